@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched straightest-geodesic exponential map on GB300.
+
+One step = one pass of the whole path over one batch resident in HBM:
+  sg_exp_map (start-face sort + persistent walk, FP64-escalated classification)
+  sg_exp_map_backward EP  (grad_v)
+  sg_exp_map_backward GFD (grad_v, grad_p, grad_bary) with grad_V (vertex positions)
+on the noisy icosphere s6 workload (81,920 faces, 1,048,576 queries, L ~ U[0.1, 1]).
+
+Prints one JSON line (metric: geodesics/s fwd+bwd; face-crossings/s and the roofline of
+the dominant kernel alongside).  `--impl reference` times the FP64 CPU oracle on the
+host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "face-crossings/sec and geodesics/sec fwd+bwd at 1M queries; frac of L2/HBM peak"
+WORKLOAD_INDEX = 2
+EPS = 1e-4
+L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
+RECORD_BYTES = 32
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0])); mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_workload(scale=1.0):
+    import meshgen
+    wl = meshgen.workload(WORKLOAD_INDEX, scale=scale)
+    X, F = wl.single
+    return wl, np.ascontiguousarray(X, np.float32), F
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(n_sample: int, threads: int):
+    """Time the FP64 oracle (forward + EP + GFD, as it stands) on the first n_sample queries."""
+    import oracle
+    wl, X32, F = load_workload(n_sample / 1048576)
+    q = wl.queries
+    om = oracle.Mesh(X32.astype(np.float64), F)
+    b = q.bary.astype(np.float32).astype(np.float64)
+    v = q.v.astype(np.float32).astype(np.float64)
+    g = q.g_pos.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    out = oracle.exp_map(om, q.face, b, v, threads=threads)
+    oracle.ep_backward(om, q.face, b, v, g, threads=threads)
+    oracle.gfd_backward(om, q.face, b, v, g, EPS, EPS, threads=threads)
+    dt = time.perf_counter() - t0
+    return len(q), dt, int(out["ncross"].sum())
+
+
+def run_reference(args):
+    threads = os.cpu_count() or 1
+    n = args.ref_sample
+    per = []
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample(min(n, 4096), threads)
+    crossings = 0
+    for _ in range(args.steps):
+        nq, dt, nc = oracle_sample(n, threads)
+        per.append(dt)
+        crossings = nc
+    t = float(np.sum(per))
+    value = args.steps * n / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "geodesics/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "icosphere-s6-noisy 81920F, queries L~U[0.1,1]; oracle sample "
+                       f"of {n} queries per step", "global_batch": n},
+            "crossings_per_s": crossings * args.steps / t,
+            "cpu_baseline": {"value": value, "unit": "geodesics/s", "cores": threads, "kind": "oracle",
+                             "sample": f"first {n} of the 1,048,576 workload queries, fwd+EP+GFD"},
+            "e2e": {"value": value, "unit": "geodesics/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=262144)
+    ap.add_argument("--cpu-sample", type=int, default=1048576)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", type=int, default=2)
+    ap.add_argument("--sort", type=int, default=1)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--fp64", type=int, default=1)
+    ap.add_argument("--json-out", default=None)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2603_15780_gb300 as sg
+    if args.warmup < 3:
+        args.warmup = 3
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    wl, X32, F = load_workload()
+    q = wl.queries
+    nq = len(q)
+    mesh = sg.Mesh(X32, F)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32), device=dev)
+    face = torch.tensor(q.face, device=dev)
+    bary, v, g = f32(q.bary), f32(q.v), f32(q.g_pos)
+    opts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
+                           block=args.block if args.block > 0 else None)
+    ws = torch.empty(sg.workspace_size(mesh, nq, opts), dtype=torch.uint8, device=dev)
+    out = {"face": torch.empty(nq, dtype=torch.int32, device=dev), "bary": torch.empty(nq, 3, device=dev),
+           "pos": torch.empty(nq, 3, device=dev), "dir": torch.empty(nq, 3, device=dev),
+           "status": torch.empty(nq, dtype=torch.int32, device=dev),
+           "ncross": torch.empty(nq, dtype=torch.int32, device=dev)}
+    gV = torch.zeros(mesh.n_vertices, 3, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        sg.exp_map(mesh, face, bary, v, out=out, workspace=ws, opts=opts)
+        if ev is not None:
+            ev[1].record(stream)
+        sg.exp_map_backward(mesh, "ep", face, bary, v, out["face"], out["dir"], out["status"], g)
+        if ev is not None:
+            ev[2].record(stream)
+        gV.zero_()
+        if ev is not None:
+            ev[3].record(stream)
+        r = sg.exp_map_backward(mesh, "gfd", face, bary, v, out["face"], out["dir"], out["status"], g,
+                                eps_v=EPS, eps_p=EPS, grad_V=gV)
+        if ev is not None:
+            ev[4].record(stream)
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ncross = int(out["ncross"].sum().item())
+    st = out["status"].cpu().numpy().astype(np.uint32)
+
+    clk = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")) if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else Clocks(local, f"/tmp/clocks_r{rank}.csv")
+    times = np.zeros((args.steps, 4))
+    for k in range(args.steps):
+        flush.zero_()                    # evict L2 between timed iterations (not timed)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        step(ev)
+        torch.cuda.synchronize()
+        times[k] = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                    ev[3].elapsed_time(ev[4])]
+    clocks = clk.stop()
+    total_ms = float(times.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_step = total_ms / args.steps
+    value = world * nq / (ms_step * 1e-3)
+    fwd_ms, ep_ms, gfd_ms = times[:, 0].mean(), times[:, 1].mean(), times[:, 3].mean()
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hb = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
+              {"face": q.face, "bary": q.bary.astype(np.float32), "v": q.v.astype(np.float32),
+               "g": q.g_pos.astype(np.float32)}.items()}
+        host_out = {"grad_v": torch.empty(nq, 3).pin_memory(), "grad_p": torch.empty(nq, 3).pin_memory(),
+                    "pos": torch.empty(nq, 3).pin_memory()}
+        h2d = sum(t.numel() * t.element_size() for t in hb.values())
+        d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+        e_ms = []
+        for k in range(args.steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fd = hb["face"].to(dev, non_blocking=True)
+            bd = hb["bary"].to(dev, non_blocking=True)
+            vd = hb["v"].to(dev, non_blocking=True)
+            gd = hb["g"].to(dev, non_blocking=True)
+            o = sg.exp_map(mesh, fd, bd, vd, workspace=ws, opts=opts)
+            sg.exp_map_backward(mesh, "ep", fd, bd, vd, o["face"], o["dir"], o["status"], gd)
+            gV.zero_()
+            r = sg.exp_map_backward(mesh, "gfd", fd, bd, vd, o["face"], o["dir"], o["status"], gd,
+                                    eps_v=EPS, eps_p=EPS, grad_V=gV)
+            host_out["grad_v"].copy_(r["grad_v"], non_blocking=True)
+            host_out["grad_p"].copy_(r["grad_p"], non_blocking=True)
+            host_out["pos"].copy_(o["pos"], non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k > 0:
+                e_ms.append(e0.elapsed_time(e1))
+        e2e = {"value": nq / (np.mean(e_ms) * 1e-3), "unit": "geodesics/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel (the GFD re-walk with vertex gradients)
+    peak, peak_kind = peaks()
+    # algorithmic bytes per launch: per crossing one 32-B record + the face's vertex ids and
+    # 3 vertices (16 B each) for the vertex-gradient adjoint + 2 x 12 B atomic adds; per query
+    # inputs (face, bary, v, g: 40 B), forward outputs read (face, dir, status: 20 B), start/end
+    # frames (2 x 64 B) and outputs (grad_v, grad_p, grad_bary, status: 40 B)
+    gfd_bytes = ncross * (RECORD_BYTES + 64 + 24) + nq * (40 + 20 + 128 + 40)
+    fwd_bytes = ncross * RECORD_BYTES + nq * (28 + 48 + 128)
+    kern = {"fwd_walk": (fwd_bytes, fwd_ms), "gfd_rewalk": (gfd_bytes, gfd_ms)}
+    dom = max(kern, key=lambda k: kern[k][1])
+    achieved = kern[dom][0] / (kern[dom][1] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes": int(kern[dom][0])}
+
+    line = {"metric": METRIC, "value": value, "unit": "geodesics/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "icosphere-s6-noisy 81920F 1Mq fwd+EP+GFD+gradV", "global_batch": world * nq,
+                       "faces": int(len(F)), "queries_per_gpu": nq, "l2": "flushed between steps (512 MB write)",
+                       "kernel": "persistent" if args.kernel == 2 else "plain", "sort": bool(args.sort),
+                       "fp64_classification": bool(args.fp64)},
+            "crossings_per_s": world * ncross / (fwd_ms * 1e-3),
+            "fwd_geodesics_per_s": world * nq / (fwd_ms * 1e-3),
+            "phase_ms": {"fwd": fwd_ms, "ep_bwd": ep_ms, "gfd_bwd_gradV": gfd_ms},
+            "crossings_per_query": ncross / nq,
+            "flag_fraction": {"near_vertex": float(((st & 4) != 0).mean()), "near_edge": float(((st & 8) != 0).mean()),
+                              "fp64": float(((st & 32) != 0).mean())},
+            "gpu_launches": args.steps * 8,  # per step: 5 sort/scan + walk + EP + GFD re-walk
+            "roofline": roofline, "clocks": clocks, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        n, dt, _ = oracle_sample(args.cpu_sample, threads)
+        line["cpu_baseline"] = {"value": n / dt, "unit": "geodesics/s", "cores": threads, "kind": "oracle",
+                                "sample": f"first {n} of the 1,048,576 queries, fwd+EP+GFD, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.json_out:
+            open(args.json_out, "w").write(json.dumps(line) + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

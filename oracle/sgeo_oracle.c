@@ -547,7 +547,7 @@ static void om_query(const om_mesh *m, int64_t f, const double *b, const double 
         if (f < 0 || f >= m->nF) s->f = 0;
         return;
     }
-    om_walk(m, s, nw, w, o, r);
+    if (s->L > 0.0) om_walk(m, s, nw, w, o, r);  /* Exp_p(0) = p: nothing to walk */
     if (r->margin < o->tau_near) r->status |= OST_NEAR_VERTEX;
 }
 

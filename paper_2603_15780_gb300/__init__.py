@@ -1,0 +1,323 @@
+"""GB300-native batched straightest-geodesic exponential map (Python binding).
+
+Thin ctypes binding over ``libsgeo.so`` (declared in ``include/sgeo.h``): argument
+marshalling only.  Every step of the exponential map, the parallel transport and the
+backward estimators runs in the library's CUDA kernels; PyTorch only provides device
+memory, streams and ``torch.autograd.Function``.  There is no CPU fallback: if the
+library cannot be loaded, or no CUDA device is present, calls raise.
+
+    mesh = Mesh(V, F)                       # numpy float32 [N,3], int32 [F,3]
+    out = exp_map(mesh, face, bary, v, w)   # torch CUDA tensors
+    pos = ExpMap.apply(mesh, face, bary, v, "gfd")   # differentiable in v, bary (and V)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Mesh", "exp_map", "exp_map_backward", "ExpMap", "Opts", "lib", "status_names",
+           "ST_BOUNDARY", "ST_MAX_STEPS", "ST_NEAR_VERTEX", "ST_NEAR_EDGE", "ST_VERTEX_HIT", "ST_FP64",
+           "ST_START_ON_EDGE", "ST_INVALID", "ST_GFD_SPLIT", "ST_FLIPPED", "ST_NO_GRADV",
+           "KERNEL_AUTO", "KERNEL_PLAIN", "KERNEL_PERSISTENT", "EST_EP", "EST_GFD", "SgError"]
+
+ST_BOUNDARY, ST_MAX_STEPS, ST_NEAR_VERTEX, ST_NEAR_EDGE = 1, 2, 4, 8
+ST_VERTEX_HIT, ST_FP64, ST_START_ON_EDGE, ST_INVALID = 16, 32, 64, 128
+ST_GFD_SPLIT, ST_FLIPPED, ST_NO_GRADV = 256, 512, 1024
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT = 0, 1, 2
+EST_EP, EST_GFD = 0, 1
+
+EXPORTED = ["sg_opts_default", "sg_status_string", "sg_mesh_create", "sg_mesh_create_batched",
+            "sg_mesh_destroy", "sg_mesh_get_info", "sg_exp_map_workspace_size", "sg_exp_map",
+            "sg_exp_map_backward", "sg_version"]
+
+
+def status_names(st: int) -> list[str]:
+    names = {ST_BOUNDARY: "BOUNDARY", ST_MAX_STEPS: "MAX_STEPS", ST_NEAR_VERTEX: "NEAR_VERTEX",
+             ST_NEAR_EDGE: "NEAR_EDGE", ST_VERTEX_HIT: "VERTEX_HIT", ST_FP64: "FP64",
+             ST_START_ON_EDGE: "START_ON_EDGE", ST_INVALID: "INVALID", ST_GFD_SPLIT: "GFD_SPLIT",
+             ST_FLIPPED: "FLIPPED", ST_NO_GRADV: "NO_GRADV"}
+    return [n for b, n in names.items() if st & b]
+
+
+class SgError(RuntimeError):
+    pass
+
+
+class Opts(C.Structure):
+    """Mirror of sg_opts (include/sgeo.h)."""
+    _fields_ = [("max_steps", C.c_int32), ("kernel", C.c_int32), ("sort", C.c_int32),
+                ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("fp64_escalate", C.c_int32),
+                ("tau_near", C.c_float), ("tau_snap", C.c_float), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("n_faces", C.c_int64), ("n_mesh", C.c_int32),
+                ("record_bytes", C.c_int32), ("device_bytes", C.c_int64), ("l_ref_mean", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libsgeo.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path) or os.environ.get("SGEO_REBUILD"):
+                path = _build.build()
+            L = C.CDLL(path)
+            P = C.c_void_p
+            L.sg_opts_default.argtypes = [C.POINTER(Opts)]
+            L.sg_status_string.argtypes = [C.c_int]
+            L.sg_status_string.restype = C.c_char_p
+            L.sg_version.restype = C.c_char_p
+            L.sg_mesh_create.argtypes = [P, C.c_int64, P, C.c_int64, C.POINTER(P)]
+            L.sg_mesh_create_batched.argtypes = [P, P, P, P, C.c_int32, C.POINTER(P)]
+            L.sg_mesh_destroy.argtypes = [P]
+            L.sg_mesh_get_info.argtypes = [P, C.POINTER(MeshInfo)]
+            L.sg_exp_map_workspace_size.argtypes = [P, C.c_int64, C.POINTER(Opts), C.POINTER(C.c_size_t)]
+            L.sg_exp_map.argtypes = [P, C.c_int64, P, P, P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P,
+                                     C.POINTER(Opts), P]
+            L.sg_exp_map_backward.argtypes = [P, C.c_int32, C.c_float, C.c_float, C.c_int64, P, P, P, P,
+                                              P, P, P, P, P, P, P, P, P, P, C.POINTER(Opts), P]
+            for f in EXPORTED:
+                if f not in ("sg_opts_default",):
+                    getattr(L, f).restype = getattr(L, f).restype or C.c_int
+            L.sg_opts_default.restype = None
+            _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != 0:
+        msg = lib().sg_status_string(rc).decode()
+        raise SgError(f"{what}: {msg} (status {rc})")
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().sg_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise SgError("a CUDA device is required (the library has no CPU path)")
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, shape=None):
+    torch = _torch()
+    if t is None:
+        return None
+    t = torch.as_tensor(t)
+    if t.device.type != "cuda":
+        t = t.to("cuda", non_blocking=True)
+    t = t.to(dtype).contiguous()
+    if shape is not None:
+        t = t.reshape(shape)
+    return t
+
+
+class Mesh:
+    """One mesh, or several meshes batched with CSR offsets (pass a list of (V, F)).
+    Vertex positions float32 [N,3] and faces int32 [F,3] on the host; built synchronously
+    on the current CUDA device by sg_mesh_create / sg_mesh_create_batched."""
+
+    def __init__(self, V, F=None):
+        _torch()
+        h = C.c_void_p()
+        if F is not None:
+            V = np.ascontiguousarray(V, dtype=np.float32).reshape(-1, 3)
+            F = np.ascontiguousarray(F, dtype=np.int32).reshape(-1, 3)
+            _check(lib().sg_mesh_create(V.ctypes.data_as(C.c_void_p), len(V), F.ctypes.data_as(C.c_void_p),
+                                        len(F), C.byref(h)), "sg_mesh_create")
+            self.n_mesh = 1
+            self.v_off = np.array([0, len(V)], np.int64)
+            self.f_off = np.array([0, len(F)], np.int64)
+            self.V = V
+            self.F = F
+        else:
+            meshes = list(V)
+            Vs = [np.ascontiguousarray(m[0], dtype=np.float32).reshape(-1, 3) for m in meshes]
+            Fs = [np.ascontiguousarray(m[1], dtype=np.int32).reshape(-1, 3) for m in meshes]
+            self.v_off = np.concatenate([[0], np.cumsum([len(x) for x in Vs])]).astype(np.int64)
+            self.f_off = np.concatenate([[0], np.cumsum([len(x) for x in Fs])]).astype(np.int64)
+            self.V = np.ascontiguousarray(np.concatenate(Vs))
+            self.F = np.ascontiguousarray(np.concatenate(Fs))
+            self.n_mesh = len(meshes)
+            _check(lib().sg_mesh_create_batched(self.V.ctypes.data_as(C.c_void_p),
+                                                self.v_off.ctypes.data_as(C.c_void_p),
+                                                self.F.ctypes.data_as(C.c_void_p),
+                                                self.f_off.ctypes.data_as(C.c_void_p), self.n_mesh,
+                                                C.byref(h)), "sg_mesh_create_batched")
+        self._h = h
+        self.n_vertices = int(self.v_off[-1])
+        self.n_faces = int(self.f_off[-1])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> MeshInfo:
+        i = MeshInfo()
+        _check(lib().sg_mesh_get_info(self._h, C.byref(i)), "sg_mesh_get_info")
+        return i
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value and _lib is not None:
+            _lib.sg_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def workspace_size(mesh: Mesh, nq: int, opts: Opts | None = None) -> int:
+    n = C.c_size_t()
+    _check(lib().sg_exp_map_workspace_size(mesh.handle, nq, C.byref(opts or default_opts()), C.byref(n)),
+           "sg_exp_map_workspace_size")
+    return n.value
+
+
+def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, mesh_id=None, *, want_hash=False,
+            want_ncross=True, opts: Opts | None = None, workspace=None, out=None, stream=None, **opt_kw):
+    """sg_exp_map on torch CUDA tensors.  Returns dict(face, bary, pos, dir, w, status,
+    ncross, hash).  `opts` (or keyword overrides such as kernel=KERNEL_PLAIN, sort=0,
+    fp64_escalate=0, block=128) map to sg_opts."""
+    torch = _torch()
+    face = _dev(face, torch.int32)
+    nq = face.numel()
+    bary = _dev(bary, torch.float32, (nq, 3))
+    v = _dev(v, torch.float32, (nq, 3))
+    nw = 0
+    if w is not None:
+        w = _dev(w, torch.float32)
+        nw = w.shape[1] if w.dim() == 3 else (w.numel() // (3 * max(nq, 1)))
+        w = w.reshape(nq, nw, 3) if nw else None
+    length = _dev(length, torch.float32, (nq,))
+    mesh_id = _dev(mesh_id, torch.int32, (nq,))
+    o = opts if opts is not None else default_opts(**opt_kw)
+    if out is None:
+        dev = face.device
+        out = {"face": torch.empty(nq, dtype=torch.int32, device=dev),
+               "bary": torch.empty(nq, 3, device=dev), "pos": torch.empty(nq, 3, device=dev),
+               "dir": torch.empty(nq, 3, device=dev),
+               "status": torch.empty(nq, dtype=torch.int32, device=dev)}
+        if nw:
+            out["w"] = torch.empty(nq, nw, 3, device=dev)
+        if want_ncross:
+            out["ncross"] = torch.empty(nq, dtype=torch.int32, device=dev)
+        if want_hash:
+            out["hash"] = torch.empty(nq, dtype=torch.int64, device=dev)
+    if workspace is None and o.kernel != KERNEL_PLAIN:
+        nb = workspace_size(mesh, nq, o)
+        workspace = torch.empty(nb, dtype=torch.uint8, device=face.device)
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().sg_exp_map(mesh.handle, nq, _ptr(mesh_id), _ptr(face), _ptr(bary), _ptr(v), _ptr(length), nw,
+                          _ptr(w), _ptr(out["face"]), _ptr(out["bary"]), _ptr(out["pos"]), _ptr(out["dir"]),
+                          _ptr(out.get("w")), _ptr(out["status"]), _ptr(out.get("ncross")),
+                          _ptr(out.get("hash")), C.byref(o), C.c_void_p(s.cuda_stream))
+    _check(rc, "sg_exp_map")
+    out["_workspace"] = workspace
+    return out
+
+
+def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_dir, end_status, g_pos,
+                     mesh_id=None, end_bary=None, *, eps_v=1e-4, eps_p=1e-4, want_grad_V=False,
+                     grad_V=None, opts: Opts | None = None, stream=None):
+    """sg_exp_map_backward.  estimator: "ep"/"gfd" or EST_*.  Returns dict(grad_v, grad_p,
+    grad_bary, grad_V (if requested; accumulated into `grad_V` when given), status)."""
+    torch = _torch()
+    est = {"ep": EST_EP, "gfd": EST_GFD}.get(estimator, estimator)
+    face = _dev(face, torch.int32)
+    nq = face.numel()
+    bary = _dev(bary, torch.float32, (nq, 3))
+    v = _dev(v, torch.float32, (nq, 3))
+    end_face = _dev(end_face, torch.int32, (nq,))
+    end_dir = _dev(end_dir, torch.float32, (nq, 3))
+    end_status = _dev(end_status, torch.int32, (nq,))
+    end_bary = _dev(end_bary, torch.float32, (nq, 3))
+    g_pos = _dev(g_pos, torch.float32, (nq, 3))
+    mesh_id = _dev(mesh_id, torch.int32, (nq,))
+    dev = face.device
+    res = {"grad_v": torch.empty(nq, 3, device=dev), "grad_p": torch.empty(nq, 3, device=dev),
+           "grad_bary": torch.empty(nq, 3, device=dev),
+           "status": torch.empty(nq, dtype=torch.int32, device=dev)}
+    if want_grad_V or grad_V is not None:
+        if grad_V is None:
+            grad_V = torch.zeros(mesh.n_vertices, 3, device=dev)
+        res["grad_V"] = grad_V
+    o = opts if opts is not None else default_opts()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().sg_exp_map_backward(mesh.handle, est, eps_v, eps_p, nq, _ptr(mesh_id), _ptr(face), _ptr(bary),
+                                   _ptr(v), _ptr(end_face), _ptr(end_bary), _ptr(end_dir), _ptr(end_status),
+                                   _ptr(g_pos), _ptr(res["grad_v"]), _ptr(res["grad_p"]),
+                                   _ptr(res["grad_bary"]), _ptr(res.get("grad_V")), _ptr(res["status"]),
+                                   C.byref(o), C.c_void_p(s.cuda_stream))
+    _check(rc, "sg_exp_map_backward")
+    return res
+
+
+def _autograd_function():
+    import torch
+
+    class ExpMap(torch.autograd.Function):
+        """pos = Exp_p(v) with p = (face, bary) on `mesh`; differentiable in v, bary and
+        (through `V`, the mesh's vertex tensor, if it requires grad) the vertex positions.
+        estimator: "ep" (Eq. proxy_func, grad for bary is zero) or "gfd" (Eqs. jv, jp)."""
+
+        @staticmethod
+        def forward(ctx, mesh, face, bary, v, estimator="gfd", V=None, mesh_id=None, eps=1e-4):
+            out = exp_map(mesh, face, bary.detach(), v.detach(), mesh_id=mesh_id)
+            ctx.mesh, ctx.estimator, ctx.eps = mesh, estimator, eps
+            ctx.save_for_backward(face, bary.detach(), v.detach(), out["face"], out["dir"], out["status"],
+                                  mesh_id if mesh_id is not None else torch.empty(0))
+            ctx.has_V = V is not None
+            ctx.mark_non_differentiable(out["face"], out["status"])
+            return out["pos"], out["face"], out["bary"], out["dir"], out["status"]
+
+        @staticmethod
+        def backward(ctx, g_pos, _gf, _gb, _gd, _gs):
+            face, bary, v, ef, ed, es, mid = ctx.saved_tensors
+            r = exp_map_backward(ctx.mesh, ctx.estimator, face, bary, v, ef, ed, es, g_pos.contiguous(),
+                                 mesh_id=mid if mid.numel() else None, eps_v=ctx.eps, eps_p=ctx.eps,
+                                 want_grad_V=ctx.needs_input_grad[5] and ctx.has_V)
+            gV = r.get("grad_V")
+            return None, None, r["grad_bary"], r["grad_v"], None, gV, None, None
+
+    return ExpMap
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _Lazy._cls is None:
+            _Lazy._cls = _autograd_function()
+        return getattr(_Lazy._cls, name)
+
+
+ExpMap = _Lazy()

@@ -1,0 +1,453 @@
+// exp_map.cu -- forward exponential map kernels, start-face sort, mesh upload and C ABI.
+//
+// Alg. "Parallel Geodesic Tracing CUDA Kernel" gives one thread per geodesic.  Two launch
+// shapes are provided:
+//   k_walk_plain       exactly that shape (grid = ceil(nq / block)), FP32 only;
+//   k_walk_persistent  an SM-filling grid whose lanes pull query indices from an atomic
+//                      counter as soon as their current walk ends, so lanes do not idle
+//                      behind the longest walk of their warp (the long tail of path
+//                      lengths the paper leaves to idle threads).  Queries can be taken in
+//                      start-face order (counting sort by global face id) so neighbouring
+//                      lanes gather the same records.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sgeo_internal.h"
+#include "walk.cuh"
+
+#define SG_MAX_W 4
+
+struct FwdArgs {
+    WalkParams P;
+    QueryIn in;
+    int64_t nq;
+    int32_t nF_total;
+    int32_t *out_face;
+    float *out_bary, *out_pos, *out_dir, *out_w;
+    uint32_t *out_status;
+    int32_t *out_ncross;
+    uint64_t *out_hash;
+    const int32_t *__restrict__ perm;  // queue position -> query index (NULL: identity)
+    int32_t *counter;                  // persistent work counter
+};
+
+template <int NW>
+__device__ void walker_finish(const FwdArgs &a, int64_t q, const Walker &w, const Carry<NW> &cw) {
+    const FaceRec &R = w.R;
+    float b2 = w.py / R.x2y;
+    float b1 = (w.px - b2 * R.x2x) / R.l01;
+    float b0 = 1.f - b1 - b2;
+    Frame3 F = face_frame(a.P, w.f);
+    a.out_face[q] = w.f - w.foff;
+    a.out_bary[3 * q] = b0; a.out_bary[3 * q + 1] = b1; a.out_bary[3 * q + 2] = b2;
+    a.out_pos[3 * q] = b0 * F.ox + b1 * F.x1x + b2 * F.x2x;
+    a.out_pos[3 * q + 1] = b0 * F.oy + b1 * F.x1y + b2 * F.x2y;
+    a.out_pos[3 * q + 2] = b0 * F.oz + b1 * F.x1z + b2 * F.x2z;
+    a.out_dir[3 * q] = w.dx * F.e1x + w.dy * F.e2x;
+    a.out_dir[3 * q + 1] = w.dx * F.e1y + w.dy * F.e2y;
+    a.out_dir[3 * q + 2] = w.dx * F.e1z + w.dy * F.e2z;
+    if (NW > 0 && a.out_w) {
+        const float sg = (w.st & SG_PARITY_BIT) ? -1.f : 1.f;
+        for (int k = 0; k < NW; ++k) {
+            float c = cw.c[k], s = sg * cw.s[k];
+            float u1 = c * w.dx - s * w.dy, u2 = c * w.dy + s * w.dx;
+            float *o = a.out_w + (3 * NW) * q + 3 * k;
+            o[0] = u1 * F.e1x + u2 * F.e2x;
+            o[1] = u1 * F.e1y + u2 * F.e2y;
+            o[2] = u1 * F.e1z + u2 * F.e2z;
+        }
+    }
+    a.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u);
+    if (a.out_ncross) a.out_ncross[q] = w.ncross;
+    if (a.out_hash) a.out_hash[q] = w.hash;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(256) k_walk_plain(FwdArgs a) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.nq) return;
+    Walker w;
+    Carry<NW> cw;
+    if (walker_init<NW>(a.P, a.in, q, w, cw)) {
+        while (!walker_step<false>(w, a.P)) {
+        }
+    }
+    walker_finish<NW>(a, q, w, cw);
+}
+
+// warp-aggregated ticket: the calling lanes get consecutive queue positions
+__device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int rank = __popc(mask & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return (int64_t)base + rank;
+}
+
+template <int NW, bool ESC>
+__global__ void __launch_bounds__(256) k_walk_persistent(FwdArgs a) {
+    Walker w;
+    Carry<NW> cw;
+    int64_t q = -1;
+    bool live = false;
+    while (true) {
+        if (!live) {
+            int64_t t = fetch_ticket(a.counter);
+            if (t >= a.nq) break;
+            q = a.perm ? (int64_t)__ldg(a.perm + t) : t;
+            live = walker_init<NW>(a.P, a.in, q, w, cw);
+            if (!live) {
+                walker_finish<NW>(a, q, w, cw);
+                continue;
+            }
+        }
+        if (walker_step<ESC>(w, a.P)) {
+            walker_finish<NW>(a, q, w, cw);
+            live = false;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ start-face counting sort
+__global__ void k_sort_keys_hist(int64_t nq, const int32_t *__restrict__ mesh_id, const int32_t *__restrict__ face,
+                                 const int32_t *__restrict__ face_off, int32_t n_mesh, int32_t nF,
+                                 int32_t *__restrict__ counts) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        int m = mesh_id ? mesh_id[i] : 0;
+        int key = nF;  // invalid queries go last
+        if (m >= 0 && m < n_mesh) {
+            int lo = face_off[m], hi = face_off[m + 1];
+            int f = face[i];
+            if (f >= 0 && f < hi - lo) key = lo + f;
+        }
+        atomicAdd(counts + key, 1);
+    }
+}
+
+__global__ void k_sort_scatter(int64_t nq, const int32_t *__restrict__ mesh_id, const int32_t *__restrict__ face,
+                               const int32_t *__restrict__ face_off, int32_t n_mesh, int32_t nF,
+                               int32_t *__restrict__ offsets, int32_t *__restrict__ perm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        int m = mesh_id ? mesh_id[i] : 0;
+        int key = nF;
+        if (m >= 0 && m < n_mesh) {
+            int lo = face_off[m], hi = face_off[m + 1];
+            int f = face[i];
+            if (f >= 0 && f < hi - lo) key = lo + f;
+        }
+        int pos = atomicAdd(offsets + key, 1);
+        perm[pos] = (int32_t)i;
+    }
+}
+
+#define SCAN_BLOCK 1024
+#define SCAN_ITEMS 4
+#define SCAN_TILE (SCAN_BLOCK * SCAN_ITEMS)
+
+// block-wide exclusive scan of one tile in place; writes the tile total
+__device__ int block_scan_tile(int32_t *data, int64_t n, int64_t base, int32_t carry_in) {
+    __shared__ int32_t warp_sums[SCAN_BLOCK / 32];
+    int tid = threadIdx.x;
+    int32_t v[SCAN_ITEMS];
+    int32_t local = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + (int64_t)tid * SCAN_ITEMS + k;
+        v[k] = i < n ? data[i] : 0;
+        local += v[k];
+    }
+    int lane = tid & 31, wid = tid >> 5;
+    int32_t x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t s = lane < SCAN_BLOCK / 32 ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SCAN_BLOCK / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int32_t excl = x - local + (wid > 0 ? warp_sums[wid - 1] : 0) + carry_in;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + (int64_t)tid * SCAN_ITEMS + k;
+        if (i < n) data[i] = excl;
+        excl += v[k];
+    }
+    int32_t total = warp_sums[SCAN_BLOCK / 32 - 1];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_tiles(int32_t *data, int64_t n, int32_t *tile_sums) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int32_t tot = block_scan_tile(data, n, base, 0);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_sums(int32_t *sums, int64_t n) {
+    int32_t carry = 0;
+    for (int64_t base = 0; base < n; base += SCAN_TILE) carry += block_scan_tile(sums, n, base, carry);
+}
+
+__global__ void k_scan_add(int32_t *data, int64_t n, const int32_t *tile_sums) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) data[i] += tile_sums[i / SCAN_TILE];
+}
+
+// ------------------------------------------------------------------ host helpers
+namespace {
+
+thread_local char g_err[256];
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct WsLayout {
+    size_t counter, counts, sums, perm, total;
+};
+
+WsLayout ws_layout(int64_t nF, int64_t nq, bool sort) {
+    WsLayout L{};
+    size_t o = 0;
+    L.counter = o; o = align_up(o + 64, 256);
+    if (sort) {
+        int64_t nk = nF + 1;
+        int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
+        L.counts = o; o = align_up(o + sizeof(int32_t) * nk, 256);
+        L.sums = o; o = align_up(o + sizeof(int32_t) * ntiles, 256);
+        L.perm = o; o = align_up(o + sizeof(int32_t) * std::max<int64_t>(nq, 1), 256);
+    }
+    L.total = o;
+    return L;
+}
+
+sg_opts resolve(const sg_opts *o) {
+    sg_opts r;
+    sg_opts_default(&r);
+    if (o) r = *o;
+    if (r.max_steps <= 0) r.max_steps = 1 << 20;
+    if (r.block <= 0) r.block = 256;
+    if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
+    if (r.tau_snap <= 0.f) r.tau_snap = 1e-6f;
+    if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
+    if (r.sort < 0) r.sort = 1;
+    if (r.kernel == SG_KERNEL_PLAIN) { r.sort = 0; r.fp64_escalate = 0; }
+    return r;
+}
+
+template <int NW>
+cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
+    if (o.kernel == SG_KERNEL_PLAIN) {
+        int64_t grid = (a.nq + o.block - 1) / o.block;
+        k_walk_plain<NW><<<(unsigned)grid, o.block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    int dev = 0, sms = 0, per = o.blocks_per_sm;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per <= 0) {
+        if (o.fp64_escalate)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk_persistent<NW, true>, o.block, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk_persistent<NW, false>, o.block, 0);
+        per = std::max(per, 1);
+    }
+    int64_t need = (a.nq + o.block - 1) / o.block;
+    int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(need, 1));
+    if (o.fp64_escalate)
+        k_walk_persistent<NW, true><<<(unsigned)grid, o.block, 0, s>>>(a);
+    else
+        k_walk_persistent<NW, false><<<(unsigned)grid, o.block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void sg_opts_default(sg_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->max_steps = 1 << 20;
+    o->kernel = SG_KERNEL_AUTO;
+    o->sort = -1;
+    o->block = 256;
+    o->blocks_per_sm = 0;
+    o->fp64_escalate = 1;
+    o->tau_near = 1e-4f;
+    o->tau_snap = 1e-6f;
+    o->workspace = nullptr;
+    o->workspace_bytes = 0;
+}
+
+const char *sg_status_string(sg_status s) {
+    switch (s) {
+        case SG_OK: return "ok";
+        case SG_ERR_INVALID_ARG: return "invalid argument";
+        case SG_ERR_NONMANIFOLD: return "non-manifold mesh";
+        case SG_ERR_DEGENERATE: return "degenerate face";
+        case SG_ERR_CUDA: return "CUDA error";
+        case SG_ERR_OOM: return "out of device memory";
+        case SG_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown";
+}
+
+const char *sg_version(void) { return "sgeo 0.1 (sm_103a)"; }
+
+sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int32_t *F, const int64_t *f_off,
+                                 int32_t n_mesh, sg_mesh **out) {
+    if (!out) return SG_ERR_INVALID_ARG;
+    *out = nullptr;
+    sg_host_mesh H;
+    sg_status st = sg_build_host_mesh(V, v_off, F, f_off, n_mesh, &H);
+    if (st != SG_OK) return st;
+    sg_mesh *m = new (std::nothrow) sg_mesh();
+    if (!m) return SG_ERR_OOM;
+    m->nV = v_off[n_mesh];
+    m->nF = f_off[n_mesh];
+    m->n_mesh = n_mesh;
+    cudaGetDevice(&m->device);
+    m->face_off = H.face_off64;
+    m->vert_off = H.vert_off64;
+    m->lref = H.lref64;
+    auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
+        if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+        m->device_bytes += (int64_t)bytes;
+        return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = up((void **)&m->d_rec, H.rec.data(), sizeof(int4) * H.rec.size()) &&
+              up((void **)&m->d_fv, H.fv.data(), sizeof(int4) * H.fv.size()) &&
+              up((void **)&m->d_V, H.V.data(), sizeof(float4) * H.V.size()) &&
+              up((void **)&m->d_face_off, H.face_off.data(), sizeof(int32_t) * H.face_off.size()) &&
+              up((void **)&m->d_lref, H.lref.data(), sizeof(float) * H.lref.size());
+    if (!ok) {
+        cudaGetLastError();
+        sg_mesh_destroy(m);
+        return SG_ERR_OOM;
+    }
+    *out = m;
+    return SG_OK;
+}
+
+sg_status sg_mesh_create(const float *V, int64_t nV, const int32_t *F, int64_t nF, sg_mesh **out) {
+    if (nV <= 0 || nF <= 0) return SG_ERR_INVALID_ARG;
+    int64_t vo[2] = {0, nV}, fo[2] = {0, nF};
+    return sg_mesh_create_batched(V, vo, F, fo, 1, out);
+}
+
+sg_status sg_mesh_destroy(sg_mesh *m) {
+    if (!m) return SG_OK;
+    cudaFree(m->d_rec);
+    cudaFree(m->d_fv);
+    cudaFree(m->d_V);
+    cudaFree(m->d_face_off);
+    cudaFree(m->d_lref);
+    delete m;
+    return SG_OK;
+}
+
+sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info) {
+    if (!m || !info) return SG_ERR_INVALID_ARG;
+    info->n_vertices = m->nV;
+    info->n_faces = m->nF;
+    info->n_mesh = m->n_mesh;
+    info->record_bytes = 32;
+    info->device_bytes = m->device_bytes;
+    info->l_ref_mean = m->lref.empty() ? 0.0 : m->lref[0];
+    return SG_OK;
+}
+
+sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts *o, size_t *bytes) {
+    if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
+    sg_opts r = resolve(o);
+    *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT && r.sort).total;
+    return SG_OK;
+}
+
+sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const float *bary,
+                     const float *v, const float *length, int32_t n_w, const float *w, int32_t *out_face,
+                     float *out_bary, float *out_pos, float *out_dir, float *out_w, uint32_t *out_status,
+                     int32_t *out_ncross, uint64_t *out_hash, const sg_opts *o, void *stream) {
+    if (!m || nq < 0 || n_w < 0 || n_w > SG_MAX_W) return SG_ERR_INVALID_ARG;
+    if (nq == 0) return SG_OK;
+    if (nq > (int64_t)INT32_MAX - 1024) return SG_ERR_INVALID_ARG;
+    if (!face || !bary || !v || !out_face || !out_bary || !out_pos || !out_dir || !out_status) return SG_ERR_INVALID_ARG;
+    if (n_w > 0 && !w) return SG_ERR_INVALID_ARG;
+    sg_opts r = resolve(o);
+    if (r.kernel != SG_KERNEL_PLAIN && r.kernel != SG_KERNEL_PERSISTENT) return SG_ERR_INVALID_ARG;
+    if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    FwdArgs a{};
+    a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
+    a.P.max_steps = r.max_steps; a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
+    a.P.want_hash = out_hash != nullptr;
+    a.nq = nq; a.in.n_mesh = m->n_mesh; a.nF_total = (int32_t)m->nF;
+    a.in.mesh_id = mesh_id; a.in.face = face; a.in.bary = bary; a.in.v = v; a.in.length = length; a.in.w = w;
+    a.out_face = out_face; a.out_bary = out_bary; a.out_pos = out_pos; a.out_dir = out_dir;
+    a.out_w = out_w; a.out_status = out_status; a.out_ncross = out_ncross; a.out_hash = out_hash;
+
+    const bool persistent = r.kernel == SG_KERNEL_PERSISTENT;
+    const bool sort = persistent && r.sort;
+    void *ws = nullptr;
+    bool own_ws = false;
+    if (persistent) {
+        WsLayout L = ws_layout(m->nF, nq, sort);
+        if (r.workspace) {
+            if (r.workspace_bytes < L.total) return SG_ERR_OOM;
+            ws = r.workspace;
+        } else {
+            if (cudaMallocAsync(&ws, L.total, s) != cudaSuccess) { cudaGetLastError(); return SG_ERR_OOM; }
+            own_ws = true;
+        }
+        char *base = (char *)ws;
+        a.counter = (int32_t *)(base + L.counter);
+        if (cudaMemsetAsync(a.counter, 0, 64, s) != cudaSuccess) return SG_ERR_CUDA;
+        if (sort) {
+            int32_t *counts = (int32_t *)(base + L.counts);
+            int32_t *sums = (int32_t *)(base + L.sums);
+            int32_t *perm = (int32_t *)(base + L.perm);
+            int64_t nk = m->nF + 1;
+            int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
+            cudaMemsetAsync(counts, 0, sizeof(int32_t) * nk, s);
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            int g = (int)std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 8);
+            k_sort_keys_hist<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts);
+            k_scan_tiles<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(counts, nk, sums);
+            k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums, ntiles);
+            k_scan_add<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(counts, nk, sums);
+            k_sort_scatter<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts, perm);
+            a.perm = perm;
+        }
+    }
+    cudaError_t e;
+    switch (n_w) {
+        case 0: e = launch_walk<0>(a, r, s); break;
+        case 1: e = launch_walk<1>(a, r, s); break;
+        case 2: e = launch_walk<2>(a, r, s); break;
+        case 3: e = launch_walk<3>(a, r, s); break;
+        default: e = launch_walk<4>(a, r, s); break;
+    }
+    if (own_ws) cudaFreeAsync(ws, s);
+    if (e != cudaSuccess) {
+        std::snprintf(g_err, sizeof g_err, "%s", cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+    }
+    return SG_OK;
+}
+
+}  // extern "C"

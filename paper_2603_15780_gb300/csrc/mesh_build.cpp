@@ -1,0 +1,188 @@
+// mesh_build.cpp -- host construction of the packed walk records (FP64 arithmetic).
+//
+// Sec. 4: a mesh M = {X, F} is manifold when each edge has one or two faces and the
+// faces around each vertex form one fan; points are (face, barycentric) pairs; the
+// total angle theta(x) at a vertex is the sum of incident corner angles.  App. "Main
+// differences with SotA implementation": only triangle adjacencies are stored (no
+// half-edges), so non-orientable meshes are accepted; the orientation of each
+// adjacency is kept as one "flip" bit so the intrinsic walk can unfold consistently.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include <cuda_runtime.h>
+
+#include "sgeo_internal.h"
+
+namespace {
+
+struct D3 {
+    double x, y, z;
+};
+inline D3 sub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline double dot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline D3 cross(D3 a, D3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+inline double norm(D3 a) { return std::sqrt(dot(a, a)); }
+inline D3 scale(D3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+
+inline int bits(float f) {
+    int i;
+    std::memcpy(&i, &f, 4);
+    return i;
+}
+
+struct EdgeKey {
+    int32_t a, b;  // a < b, local vertex ids
+    int32_t f;     // local face
+    int8_t k;      // local edge: corner k -> corner k+1
+};
+
+}  // namespace
+
+sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t *F, const int64_t *f_off,
+                             int32_t n_mesh, sg_host_mesh *out) {
+    if (!V || !v_off || !F || !f_off || n_mesh <= 0) return SG_ERR_INVALID_ARG;
+    if (v_off[0] != 0 || f_off[0] != 0) return SG_ERR_INVALID_ARG;
+    for (int m = 0; m < n_mesh; ++m)
+        if (v_off[m + 1] <= v_off[m] || f_off[m + 1] <= f_off[m]) return SG_ERR_INVALID_ARG;
+    const int64_t nV = v_off[n_mesh], nF = f_off[n_mesh];
+    if (nF >= SG_MAX_FACES || nV >= (1LL << 31)) return SG_ERR_INVALID_ARG;
+
+    out->rec.assign(2 * nF, int4{0, 0, 0, 0});
+    out->fv.assign(nF, int4{0, 0, 0, 0});
+    out->V.assign(nV, float4{0, 0, 0, 0});
+    out->face_off.assign(n_mesh + 1, 0);
+    out->lref.assign(n_mesh, 0.f);
+    out->lref64.assign(n_mesh, 0.0);
+    out->face_off64.assign(f_off, f_off + n_mesh + 1);
+    out->vert_off64.assign(v_off, v_off + n_mesh + 1);
+    for (int m = 0; m <= n_mesh; ++m) out->face_off[m] = (int32_t)f_off[m];
+
+    std::vector<double> theta(nV, 0.0);
+    std::vector<uint8_t> boundary(nV, 0);
+
+    for (int m = 0; m < n_mesh; ++m) {
+        const int64_t v0 = v_off[m], nv = v_off[m + 1] - v0;
+        const int64_t f0 = f_off[m], nf = f_off[m + 1] - f0;
+        auto X = [&](int32_t lv) { const float *p = V + 3 * (v0 + lv); return D3{p[0], p[1], p[2]}; };
+        const int32_t *Fm = F + 3 * f0;
+        for (int64_t i = 0; i < 3 * nf; ++i)
+            if (Fm[i] < 0 || Fm[i] >= nv) return SG_ERR_INVALID_ARG;
+
+        // ---- per-face intrinsic shape in the face's own 2-D frame
+        for (int64_t f = 0; f < nf; ++f) {
+            const int32_t *t = Fm + 3 * f;
+            if (t[0] == t[1] || t[1] == t[2] || t[0] == t[2]) return SG_ERR_DEGENERATE;
+            D3 x0 = X(t[0]), x1 = X(t[1]), x2 = X(t[2]);
+            D3 e1 = sub(x1, x0), e2 = sub(x2, x0);
+            D3 n = cross(e1, e2);
+            double l01 = norm(e1), nn = norm(n);
+            if (!(nn > 1e-14 * std::max(dot(e1, e1), dot(e2, e2)))) return SG_ERR_DEGENERATE;
+            D3 u = scale(e1, 1.0 / l01);
+            D3 nh = scale(n, 1.0 / nn);
+            D3 w = cross(nh, u);
+            double x2x = dot(e2, u), x2y = dot(e2, w);
+            double l12 = norm(sub(x2, x1)), l20 = norm(e2);
+            int4 &r1 = out->rec[2 * (f0 + f) + 1];
+            r1.x = bits((float)x2x);
+            r1.y = bits((float)x2y);
+            r1.z = bits((float)(1.0 / l12));
+            r1.w = bits((float)(1.0 / l20));
+            out->rec[2 * (f0 + f)].w = bits((float)l01);
+            out->fv[f0 + f] = int4{(int)(v0 + t[0]), (int)(v0 + t[1]), (int)(v0 + t[2]), m};
+            // corner angles -> theta
+            for (int k = 0; k < 3; ++k) {
+                D3 a = sub(X(t[(k + 1) % 3]), X(t[k])), b = sub(X(t[(k + 2) % 3]), X(t[k]));
+                theta[v0 + t[k]] += std::atan2(norm(cross(a, b)), dot(a, b));
+            }
+        }
+
+        // ---- edge matching: sort the 3 nf half-edges by (min, max) vertex
+        std::vector<EdgeKey> E(3 * nf);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int k = 0; k < 3; ++k) {
+                int32_t a = Fm[3 * f + k], b = Fm[3 * f + (k + 1) % 3];
+                E[3 * f + k] = EdgeKey{std::min(a, b), std::max(a, b), (int32_t)f, (int8_t)k};
+            }
+        std::sort(E.begin(), E.end(), [](const EdgeKey &p, const EdgeKey &q) {
+            if (p.a != q.a) return p.a < q.a;
+            if (p.b != q.b) return p.b < q.b;
+            if (p.f != q.f) return p.f < q.f;
+            return p.k < q.k;
+        });
+        double lsum = 0.0;
+        int64_t ne = 0;
+        std::vector<int32_t> nbr(3 * nf, -1);
+        for (size_t i = 0; i < E.size();) {
+            size_t j = i + 1;
+            while (j < E.size() && E[j].a == E[i].a && E[j].b == E[i].b) ++j;
+            if (j - i > 2) return SG_ERR_NONMANIFOLD;
+            lsum += norm(sub(X(E[i].a), X(E[i].b)));
+            ++ne;
+            if (j - i == 2) {
+                const EdgeKey &p = E[i], &q = E[i + 1];
+                if (p.f == q.f) return SG_ERR_NONMANIFOLD;
+                // same direction in both faces -> inconsistent orientation across this edge
+                int32_t pa = Fm[3 * p.f + p.k], qa = Fm[3 * q.f + q.k];
+                int flip = (pa == qa) ? 1 : 0;
+                int64_t gq = f0 + q.f, gp = f0 + p.f;
+                nbr[3 * p.f + p.k] = (int32_t)((gq << 3) | (flip << 2) | q.k);
+                nbr[3 * q.f + q.k] = (int32_t)((gp << 3) | (flip << 2) | p.k);
+            } else {
+                boundary[v0 + E[i].a] = 1;
+                boundary[v0 + E[i].b] = 1;
+            }
+            i = j;
+        }
+        for (int64_t f = 0; f < nf; ++f) {
+            int4 &r0 = out->rec[2 * (f0 + f)];
+            r0.x = nbr[3 * f];
+            r0.y = nbr[3 * f + 1];
+            r0.z = nbr[3 * f + 2];
+        }
+        out->lref64[m] = lsum / (double)ne;
+        out->lref[m] = (float)out->lref64[m];
+
+        // ---- single-fan check: walking around each vertex through the adjacency must
+        //      reach all of its incident faces
+        std::vector<int32_t> deg(nv, 0), any(nv, -1);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int k = 0; k < 3; ++k) {
+                deg[Fm[3 * f + k]]++;
+                any[Fm[3 * f + k]] = (int32_t)f;
+            }
+        for (int64_t v = 0; v < nv; ++v) {
+            if (deg[v] == 0) continue;
+            int64_t seen = 1;
+            for (int dir = 0; dir < 2; ++dir) {
+                int64_t f = any[v];
+                const int32_t *t = Fm + 3 * f;
+                int c = t[0] == v ? 0 : t[1] == v ? 1 : 2;
+                // edges at corner c: local edge c (c -> c+1) and local edge c+2 (c+2 -> c)
+                int e = dir == 0 ? c : (c + 2) % 3;
+                for (int guard = 0; guard <= deg[v]; ++guard) {
+                    int32_t nb = nbr[3 * f + e];
+                    if (nb < 0) break;
+                    int64_t g = (nb >> 3) - f0;
+                    if (g == any[v]) break;
+                    ++seen;
+                    int kp = nb & 3;
+                    const int32_t *tg = Fm + 3 * g;
+                    int cg = tg[0] == v ? 0 : tg[1] == v ? 1 : 2;
+                    // the other edge of g at corner cg
+                    e = (kp == cg) ? (cg + 2) % 3 : cg;
+                    f = g;
+                }
+                if (!boundary[v0 + v]) break;
+            }
+            if (seen != deg[v]) return SG_ERR_NONMANIFOLD;
+        }
+    }
+    for (int64_t v = 0; v < nV; ++v) {
+        const float *p = V + 3 * v;
+        float th = (float)theta[v];
+        out->V[v] = float4{p[0], p[1], p[2], boundary[v] ? -th : th};
+    }
+    return SG_OK;
+}

@@ -1,0 +1,55 @@
+// sgeo_internal.h -- data layout shared by the host mesh builder and the CUDA kernels.
+//
+// Device layout of a mesh (all arrays indexed by GLOBAL ids: meshes are concatenated):
+//
+//   rec   int4[2*nF]   32-byte walk record per face = exactly one L2 sector:
+//                      rec[2f]   = { nbr0, nbr1, nbr2, bits(l01) }
+//                      rec[2f+1] = { bits(x2x), bits(x2y), bits(il1), bits(il2) }
+//                      nbr_k = (g << 3) | (flip << 2) | k'  : face g lies across local edge k
+//                      (edge k runs from corner k to corner k+1); in g that edge is local
+//                      edge k'; flip = 1 when g lists the edge in the same direction as f
+//                      (inconsistent orientation, e.g. a Moebius strip); -1 on the boundary.
+//                      Intrinsic 2-D shape in the face's own frame (corner 0 at the origin,
+//                      corner 1 on +x, corner 2 in the upper half plane):
+//                      P0 = (0,0), P1 = (l01,0), P2 = (x2x,x2y); il1 = 1/|P2-P1|, il2 = 1/|P2|.
+//   fv    int4[nF]     global vertex ids of the face corners, .w = mesh index
+//   V     float4[nV]   vertex position (x,y,z); .w = total angle theta(x), negated for boundary
+//                      vertices (Sec. 4: theta = sum of incident corner angles)
+//   face_off int32[n_mesh+1], lref float[n_mesh] (mean edge length per mesh)
+//
+// The walk of a query touches one record per edge crossing (one dependent 32-B gather);
+// fv/V are read only at the start, at vertex hits and at the end.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "../../include/sgeo.h"
+
+#define SG_MAX_FACES (1LL << 28)
+
+struct sg_mesh {
+    int64_t nV = 0, nF = 0;
+    int32_t n_mesh = 0;
+    int device = 0;
+    int4 *d_rec = nullptr;
+    int4 *d_fv = nullptr;
+    float4 *d_V = nullptr;
+    int32_t *d_face_off = nullptr;
+    float *d_lref = nullptr;
+    std::vector<int64_t> face_off, vert_off;
+    std::vector<double> lref;
+    int64_t device_bytes = 0;
+};
+
+// host-side builder (mesh_build.cpp); fills the host arrays, returns SG_OK or an error
+struct sg_host_mesh {
+    std::vector<int4> rec, fv;
+    std::vector<float4> V;
+    std::vector<int32_t> face_off;
+    std::vector<float> lref;
+    std::vector<double> lref64;
+    std::vector<int64_t> face_off64, vert_off64;
+};
+
+sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t *F, const int64_t *f_off,
+                             int32_t n_mesh, sg_host_mesh *out);

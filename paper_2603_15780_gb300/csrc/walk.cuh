@@ -1,0 +1,451 @@
+// walk.cuh -- device-side straightest-geodesic walker (intrinsic 2-D formulation).
+//
+// The paper walks in 3-D (Alg. geodesic_step, transport_over_edge, transport_over_vertex,
+// App. "Implementation of the Geodesic Step").  Here each face carries its own 2-D frame
+// (corner 0 at the origin, corner 1 on +x); a crossing maps the walker rigidly from the
+// frame of f to the frame of its neighbour g through the shared edge, which is the
+// unfolding isometry of Sec. 4 ("the neighbourhood of a point on an edge is isometric to a
+// plane").  Per crossing the walker reads ONE 32-byte record (the face it enters).
+//
+// Decisions are orientation tests sigma_i = cross(d, P_i - p) = signed distance from the ray
+// line to corner i: the exit edge is the one whose endpoints have sigma of opposite sign, and
+// a vertex is hit when |sigma| <= tau_snap * l_ref.  When |sigma| < tau_near * l_ref the tests
+// are re-evaluated in FP64 (ESC = true) and the query is flagged NEAR_VERTEX.
+//
+// Carried tangent vectors are kept as their (cos, sin) components relative to the walking
+// direction: parallel transport holds the angle to the curve tangent constant (Sec. 4
+// "Parallel Transport"), so they are rebuilt only at the end.  A parity bit records crossings
+// of inconsistently oriented edges (non-orientable meshes) where the signed angle flips.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgeo_internal.h"
+
+#define SG_PARITY_BIT 0x80000000u
+#define SG_FNV_OFFSET 0xcbf29ce484222325ULL
+#define SG_FNV_PRIME 0x100000001b3ULL
+
+struct FaceRec {
+    int n0, n1, n2;
+    float l01, x2x, x2y, il1, il2;
+};
+
+__device__ __forceinline__ FaceRec load_rec(const int4 *__restrict__ rec, int f) {
+    int4 a = __ldg(rec + 2 * f);
+    int4 b = __ldg(rec + 2 * f + 1);
+    FaceRec r;
+    r.n0 = a.x; r.n1 = a.y; r.n2 = a.z;
+    r.l01 = __int_as_float(a.w);
+    r.x2x = __int_as_float(b.x); r.x2y = __int_as_float(b.y);
+    r.il1 = __int_as_float(b.z); r.il2 = __int_as_float(b.w);
+    return r;
+}
+
+template <class T>
+__device__ __forceinline__ T sel3(int k, T a, T b, T c) { return k == 0 ? a : (k == 1 ? b : c); }
+__device__ __forceinline__ int nbr_of(const FaceRec &r, int k) { return sel3(k, r.n0, r.n1, r.n2); }
+__device__ __forceinline__ float corner_x(const FaceRec &r, int k) { return sel3(k, 0.f, r.l01, r.x2x); }
+__device__ __forceinline__ float corner_y(const FaceRec &r, int k) { return sel3(k, 0.f, 0.f, r.x2y); }
+__device__ __forceinline__ float inv_len(const FaceRec &r, int k) { return sel3(k, __frcp_rn(r.l01), r.il1, r.il2); }
+__device__ __forceinline__ int nxt(int k) { return k == 2 ? 0 : k + 1; }
+__device__ __forceinline__ int prv(int k) { return k == 0 ? 2 : k - 1; }
+
+struct WalkParams {
+    const int4 *__restrict__ rec;
+    const int4 *__restrict__ fv;
+    const float4 *__restrict__ V;
+    const int32_t *__restrict__ face_off;
+    const float *__restrict__ lref;
+    int max_steps;
+    float tau_near, tau_snap;
+    int want_hash;
+};
+
+// Walker state (all registers).  mode: 0..2 entered through local edge `mode`;
+// 3..5 sitting on corner mode-3 after a vertex transport; 6 free start.
+struct Walker {
+    int f, mode, steps, ncross;
+    float px, py, dx, dy;
+    float Lh, Ll;        // remaining length as an unevaluated sum (compensated subtraction)
+    uint32_t st;         // SG_ST_* | parity
+    int foff;            // face offset of the query's mesh (hash uses local ids)
+    float lref;
+    uint64_t hash;
+    FaceRec R;
+};
+
+__device__ __forceinline__ float sigma32(float dx, float dy, float cx, float cy, float px, float py) {
+    // cross(d, C - p): signed distance of corner C from the ray line (d is unit)
+    return fmaf(dx, cy - py, -dy * (cx - px));
+}
+__device__ __forceinline__ double sigma64(float dx, float dy, float cx, float cy, float px, float py) {
+    return (double)dx * ((double)cy - (double)py) - (double)dy * ((double)cx - (double)px);
+}
+
+// FP64 -> FP32 keeping the sign of tiny values (a sign decides the exit edge)
+__device__ __forceinline__ float f32_keep_sign(double x) {
+    float f = (float)x;
+    if (f == 0.f && x != 0.0) f = x > 0.0 ? 1.17549435e-38f : -1.17549435e-38f;
+    return f;
+}
+
+__device__ __forceinline__ void walker_hash(Walker &w, int f, int want) {
+    if (want) {
+        w.hash ^= (uint64_t)(uint32_t)(f - w.foff);
+        w.hash *= SG_FNV_PRIME;
+    }
+}
+
+__device__ __forceinline__ void renorm(float &x, float &y) {
+    float n2 = fmaf(x, x, y * y);
+    float r = rsqrtf(n2);
+    r = r * fmaf(-0.5f * n2 * r, r, 1.5f);  // one Newton step
+    x *= r; y *= r;
+}
+
+// Vertex transport: the walker reached corner c of face w.f with direction d.
+// Straightest rule (Sec. 4, Alg. transport_over_vertex): leave along the ray that splits the
+// total angle theta(x) in two equal halves with the reversed incoming ray.  The fan is walked
+// from -d through the faces around x until the accumulated corner angles pass theta/2; the
+// outgoing ray lies in that face at the excess angle from the shared edge.
+// Returns false if the walk must stop (boundary vertex).
+__device__ __forceinline__ bool vertex_transport(Walker &w, int c, const WalkParams &P) {
+    int4 fvv = __ldg(P.fv + w.f);
+    int vid = sel3(c, fvv.x, fvv.y, fvv.z);
+    float th = __ldg(&P.V[vid].w);
+    w.st |= SG_ST_VERTEX_HIT;
+    float cx = corner_x(w.R, c), cy = corner_y(w.R, c);
+    w.px = cx; w.py = cy;
+    if (th < 0.f) {  // boundary vertex: original rule stops here (Sec. 4)
+        w.st |= SG_ST_BOUNDARY;
+        return false;
+    }
+    const float half = 0.5f * th;
+    float rx = -w.dx, ry = -w.dy;
+    // first edge: local edge prv(c) runs from corner prv(c) to corner c = x
+    int e = prv(c);
+    float ex = corner_x(w.R, prv(c)) - cx, ey = corner_y(w.R, prv(c)) - cy;
+    float A = atan2f(fabsf(rx * ey - ry * ex), rx * ex + ry * ey);
+    if (A >= half) {
+        // rotate r toward the edge by theta/2 inside this face
+        float hx = ex - (ex * rx + ey * ry) * rx, hy = ey - (ex * rx + ey * ry) * ry;
+        renorm(hx, hy);
+        float sh, ch;
+        sincosf(half, &sh, &ch);
+        w.dx = ch * rx + sh * hx;
+        w.dy = ch * ry + sh * hy;
+        renorm(w.dx, w.dy);
+        w.mode = 3 + c;
+        walker_hash(w, w.f, P.want_hash);
+        return true;
+    }
+    int cur_c = c;
+    FaceRec Rc = w.R;
+    for (int guard = 0; guard < 4096; ++guard) {
+        int nb = nbr_of(Rc, e);
+        if (nb < 0) {  // open fan reached although theta says interior: stop (inconsistent input)
+            w.st |= SG_ST_BOUNDARY;
+            return false;
+        }
+        int g = nb >> 3, kp = nb & 3, fl = (nb >> 2) & 1;
+        if (fl) w.st ^= SG_PARITY_BIT;
+        FaceRec Rg = load_rec(P.rec, g);
+        bool x_end_cur = (cur_c == nxt(e));
+        bool x_start_g = (x_end_cur != (bool)fl);
+        int cg = x_start_g ? kp : nxt(kp);
+        int yg = x_start_g ? nxt(kp) : kp;
+        int zg = 3 - cg - yg;
+        float gx = corner_x(Rg, cg), gy = corner_y(Rg, cg);
+        float ux = corner_x(Rg, yg) - gx, uy = corner_y(Rg, yg) - gy;
+        float zx = corner_x(Rg, zg) - gx, zy = corner_y(Rg, zg) - gy;
+        float gam = atan2f(fabsf(ux * zy - uy * zx), ux * zx + uy * zy);
+        if (A + gam >= half) {
+            float beta = half - A;
+            renorm(ux, uy);
+            float hx = zx - (zx * ux + zy * uy) * ux, hy = zy - (zx * ux + zy * uy) * uy;
+            renorm(hx, hy);
+            float sb, cb;
+            sincosf(beta, &sb, &cb);
+            w.dx = cb * ux + sb * hx;
+            w.dy = cb * uy + sb * hy;
+            renorm(w.dx, w.dy);
+            w.f = g;
+            w.R = Rg;
+            w.px = gx; w.py = gy;
+            w.mode = 3 + cg;
+            walker_hash(w, g, P.want_hash);
+            return true;
+        }
+        A += gam;
+        e = (nxt(cg) == zg) ? cg : zg;  // the other edge of g at x
+        cur_c = cg;
+        Rc = Rg;
+    }
+    w.st |= SG_ST_MAX_STEPS;
+    return false;
+}
+
+// Observer of a walk (the backward pass hooks into the same step code as the forward).
+struct NoHook {
+    // after the exit classification of a face: sigma of the three corners (FP64-refined
+    // when escalated), the mode the face was entered in and the snapped corner (or -1)
+    __device__ __forceinline__ void on_face(const Walker &, float, float, float, int, int) {}
+    // at an edge crossing (walker still in the old face, length already reduced): exit edge
+    // j, crossing point q (old frame), remaining length, the new face/record, its edge kp,
+    // flip, and the new direction
+    __device__ __forceinline__ void on_cross(const Walker &, int, float, float, float, int, const FaceRec &, int,
+                                             int, float, float) {}
+    // before a vertex transport at corner `hit` of the current face
+    __device__ __forceinline__ void on_vertex(const Walker &, int) {}
+};
+
+// One step of Alg. geodesic_step.  Returns true when the walk is finished.
+template <bool ESC, class Hook = NoHook>
+__device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook &&hook = Hook()) {
+    if (w.steps >= P.max_steps) {
+        w.st |= SG_ST_MAX_STEPS;
+        return true;
+    }
+    w.steps++;
+    const FaceRec &R = w.R;
+    const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
+    float s0 = sigma32(w.dx, w.dy, 0.f, 0.f, w.px, w.py);
+    float s1 = sigma32(w.dx, w.dy, R.l01, 0.f, w.px, w.py);
+    float s2 = sigma32(w.dx, w.dy, R.x2x, R.x2y, w.px, w.py);
+    int j;          // exit edge (corner j -> corner j+1)
+    int hit = -1;   // corner hit, or -1
+    const int mode = w.mode;
+    // corners relevant to the decision: apex (entered through an edge), the two far corners
+    // (sitting on a corner), or all three (free start)
+    float mrel = mode < 3 ? fabsf(sel3(prv(mode), s0, s1, s2))
+               : mode < 6 ? fminf(fabsf(sel3(nxt(mode - 3), s0, s1, s2)), fabsf(sel3(prv(mode - 3), s0, s1, s2)))
+                          : fminf(fminf(fabsf(s0), fabsf(s1)), fabsf(s2));
+    if (ESC && mrel < near) {
+        // FP64 re-evaluation of the classification (exact products of the FP32 state)
+        w.st |= SG_ST_FP64;
+        s0 = f32_keep_sign(sigma64(w.dx, w.dy, 0.f, 0.f, w.px, w.py));
+        s1 = f32_keep_sign(sigma64(w.dx, w.dy, R.l01, 0.f, w.px, w.py));
+        s2 = f32_keep_sign(sigma64(w.dx, w.dy, R.x2x, R.x2y, w.px, w.py));
+    }
+    float mflag;    // near-vertex margin, excluding a snapped corner
+    if (mode < 3) {
+        const int k = mode, a = prv(k);  // apex = corner k+2
+        float sa = sel3(a, s0, s1, s2);
+        mflag = fabsf(sa);
+        if (mflag <= snap) { hit = a; mflag = 3.0e38f; }
+        j = sa > 0.f ? nxt(k) : prv(k);
+    } else if (mode < 6) {
+        const int c = mode - 3, a = nxt(c), b = prv(c);
+        j = a;
+        float fa = fabsf(sel3(a, s0, s1, s2)), fb = fabsf(sel3(b, s0, s1, s2));
+        mflag = fminf(fa, fb);
+        if (mflag <= snap) { hit = fa <= fb ? a : b; mflag = fmaxf(fa, fb); }
+    } else {
+        // forward exit edge: sigma(start corner) < 0 <= sigma(end corner), CCW frame
+        if (s0 < 0.f && s1 >= 0.f) j = 0;
+        else if (s1 < 0.f && s2 >= 0.f) j = 1;
+        else if (s2 < 0.f && s0 >= 0.f) j = 2;
+        else { w.st |= SG_ST_INVALID; return true; }
+        float fa = fabsf(sel3(j, s0, s1, s2)), fb = fabsf(sel3(nxt(j), s0, s1, s2)), fo = fabsf(sel3(prv(j), s0, s1, s2));
+        mflag = fminf(fminf(fa, fb), fo);
+        if (fminf(fa, fb) <= snap) { hit = fa <= fb ? j : nxt(j); mflag = fminf(fmaxf(fa, fb), fo); }
+    }
+    if (mflag < near) w.st |= SG_ST_NEAR_VERTEX;
+    hook.on_face(w, s0, s1, s2, mode, hit);
+    // exit point on edge j: A = P_j, B = P_{j+1}; s = sigma_A / (sigma_A - sigma_B)
+    const int jb = nxt(j);
+    float ax = corner_x(R, j), ay = corner_y(R, j);
+    float bx = corner_x(R, jb), by = corner_y(R, jb);
+    float qx, qy, s;
+    if (hit >= 0) {
+        qx = corner_x(R, hit); qy = corner_y(R, hit);
+        s = (hit == j) ? 0.f : 1.f;
+    } else {
+        float sa = sel3(j, s0, s1, s2), sb = sel3(jb, s0, s1, s2);
+        float den = sa - sb;
+        s = den != 0.f ? sa / den : 0.5f;
+        s = fminf(fmaxf(s, 0.f), 1.f);
+        qx = fmaf(s, bx - ax, ax);
+        qy = fmaf(s, by - ay, ay);
+    }
+    float t = fmaxf(fmaf(qx - w.px, w.dx, (qy - w.py) * w.dy), 0.f);
+    float L = w.Lh + w.Ll;
+    if (t >= L) {
+        // final truncated in-face segment (reading: stop once the length is used up)
+        w.px = fmaf(L, w.dx, w.px);
+        w.py = fmaf(L, w.dy, w.py);
+        w.Lh = 0.f; w.Ll = 0.f;
+        // NEAR_EDGE: end point within tau_near*l_ref of an edge line of its face
+        float d0 = fabsf(w.py);                                                   // edge 0 (y = 0)
+        float d1 = fabsf((R.x2x - R.l01) * (w.py) - R.x2y * (w.px - R.l01)) * R.il1;  // edge 1
+        float d2 = fabsf(R.x2x * w.py - R.x2y * w.px) * R.il2;                     // edge 2
+        if (fminf(fminf(d0, d1), d2) <= near) w.st |= SG_ST_NEAR_EDGE;
+        return true;
+    }
+    {   // compensated L -= t
+        float a = w.Lh, b = -t;
+        float sum = a + b;
+        float bb = sum - a;
+        float err = (a - (sum - bb)) + (b - bb);
+        w.Lh = sum;
+        w.Ll += err;
+    }
+    if (hit >= 0) {
+        hook.on_vertex(w, hit);
+        if (!vertex_transport(w, hit, P)) return true;
+        return false;
+    }
+    const int nb = nbr_of(R, j);
+    if (nb < 0) {  // boundary edge: original rule stops (Sec. 4)
+        w.px = qx; w.py = qy;
+        w.st |= SG_ST_BOUNDARY;
+        return true;
+    }
+    const int g = nb >> 3, kp = nb & 3, fl = (nb >> 2) & 1;
+    // direction in the edge basis of f: along-edge a, outward-normal c
+    float il = inv_len(R, j);
+    float ex = (bx - ax) * il, ey = (by - ay) * il;
+    float da = fmaf(w.dx, ex, w.dy * ey);
+    float dc = fmaf(w.dx, ey, -w.dy * ex);  // d . (ey, -ex)
+    FaceRec G = load_rec(P.rec, g);
+    const int kb = nxt(kp);
+    float gax = corner_x(G, kp), gay = corner_y(G, kp);
+    float gbx = corner_x(G, kb), gby = corner_y(G, kb);
+    float gil = inv_len(G, kp);
+    float fx = (gbx - gax) * gil, fy = (gby - gay) * gil;
+    // d' = (+-a) e' - c n'_out, n'_out = (fy, -fx)
+    float sa_ = fl ? da : -da;
+    float ndx = fmaf(sa_, fx, -dc * fy);
+    float ndy = fmaf(sa_, fy, dc * fx);
+    renorm(ndx, ndy);
+    hook.on_cross(w, j, qx, qy, w.Lh + w.Ll, g, G, kp, fl, ndx, ndy);
+    float sp = fl ? s : 1.f - s;
+    w.px = fmaf(sp, gbx - gax, gax);
+    w.py = fmaf(sp, gby - gay, gay);
+    w.dx = ndx; w.dy = ndy;
+    w.f = g;
+    w.R = G;
+    w.mode = kp;
+    if (fl) w.st ^= SG_PARITY_BIT;
+    w.ncross++;
+    walker_hash(w, g, P.want_hash);
+    return false;
+}
+
+// query inputs (device pointers; mesh_id/length/w may be NULL)
+struct QueryIn {
+    int32_t n_mesh;
+    const int32_t *__restrict__ mesh_id;
+    const int32_t *__restrict__ face;
+    const float *__restrict__ bary;
+    const float *__restrict__ v;
+    const float *__restrict__ length;
+    const float *__restrict__ w;
+};
+
+struct Frame3 {
+    float ox, oy, oz;  // corner 0
+    float e1x, e1y, e1z, e2x, e2y, e2z;
+    float x1x, x1y, x1z, x2x, x2y, x2z;  // corners 1, 2
+};
+
+// 3-D frame of a face from the vertex positions: e1 along x1-x0, e2 = n x e1.  This is the
+// frame in which the intrinsic record was expressed by the mesh builder.
+__device__ __forceinline__ Frame3 face_frame(const WalkParams &P, int gf) {
+    int4 t = __ldg(P.fv + gf);
+    float4 a = __ldg(P.V + t.x), b = __ldg(P.V + t.y), c = __ldg(P.V + t.z);
+    Frame3 F;
+    F.ox = a.x; F.oy = a.y; F.oz = a.z;
+    F.x1x = b.x; F.x1y = b.y; F.x1z = b.z;
+    F.x2x = c.x; F.x2y = c.y; F.x2z = c.z;
+    float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+    float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    float rn = rsqrtf(nx * nx + ny * ny + nz * nz);
+    nx *= rn; ny *= rn; nz *= rn;
+    float ru = rsqrtf(ux * ux + uy * uy + uz * uz);
+    ux *= ru; uy *= ru; uz *= ru;
+    F.e1x = ux; F.e1y = uy; F.e1z = uz;
+    F.e2x = ny * uz - nz * uy; F.e2y = nz * ux - nx * uz; F.e2z = nx * uy - ny * ux;
+    return F;
+}
+
+template <int NW>
+struct Carry {
+    float c[NW > 0 ? NW : 1], s[NW > 0 ? NW : 1];
+};
+
+// initialise_trace (Alg. gpu_parallel): start face, barycentric point, tangent projection,
+// length.  Returns false if the query finishes immediately (invalid, zero length).
+template <int NW>
+__device__ bool walker_init(const WalkParams &P, const QueryIn &a, int64_t q, Walker &w, Carry<NW> &cw) {
+    int m = a.mesh_id ? __ldg(a.mesh_id + q) : 0;
+    int lf = __ldg(a.face + q);
+    w.st = 0; w.steps = 0; w.ncross = 0; w.hash = SG_FNV_OFFSET;
+    w.mode = 6; w.Ll = 0.f;
+    bool bad = (m < 0 || m >= a.n_mesh);
+    int foff = bad ? 0 : __ldg(P.face_off + m);
+    int nfm = bad ? 1 : __ldg(P.face_off + m + 1) - foff;
+    bad = bad || lf < 0 || lf >= nfm;
+    w.foff = foff;
+    w.f = bad ? foff : foff + lf;
+    w.lref = bad ? 1.f : __ldg(P.lref + m);
+    w.R = load_rec(P.rec, w.f);
+    float b0 = __ldg(a.bary + 3 * q), b1 = __ldg(a.bary + 3 * q + 1), b2 = __ldg(a.bary + 3 * q + 2);
+    float sb = b0 + b1 + b2;
+    if (!(fabsf(sb - 1.f) <= 1e-6f) || b0 < -1e-7f || b1 < -1e-7f || b2 < -1e-7f) bad = true;
+    if (bad) {
+        w.st |= SG_ST_INVALID;
+        w.px = w.py = 0.f; w.dx = w.dy = 0.f;
+        w.Lh = 0.f;
+        for (int k = 0; k < NW; ++k) { cw.c[k] = 0.f; cw.s[k] = 0.f; }
+        return false;
+    }
+    float rs = 1.f / sb;
+    b0 = fmaxf(b0, 0.f) * rs; b1 = fmaxf(b1, 0.f) * rs; b2 = fmaxf(b2, 0.f) * rs;
+    w.px = fmaf(b1, w.R.l01, b2 * w.R.x2x);
+    w.py = b2 * w.R.x2y;
+    Frame3 F = face_frame(P, w.f);
+    float vx = __ldg(a.v + 3 * q), vy = __ldg(a.v + 3 * q + 1), vz = __ldg(a.v + 3 * q + 2);
+    float v1 = vx * F.e1x + vy * F.e1y + vz * F.e1z;
+    float v2 = vx * F.e2x + vy * F.e2y + vz * F.e2z;
+    float Lv = sqrtf(v1 * v1 + v2 * v2);
+    float L = a.length ? __ldg(a.length + q) : Lv;
+    if (!(L >= 0.f) || (Lv == 0.f && L > 0.f)) {
+        w.st |= SG_ST_INVALID;
+        w.dx = w.dy = 0.f; w.Lh = 0.f;
+        for (int k = 0; k < NW; ++k) { cw.c[k] = 0.f; cw.s[k] = 0.f; }
+        return false;
+    }
+    if (Lv > 0.f) { w.dx = v1 / Lv; w.dy = v2 / Lv; } else { w.dx = w.dy = 0.f; }
+    w.Lh = L;
+    for (int k = 0; k < NW; ++k) {
+        const float *wp = a.w + (3 * NW) * q + 3 * k;
+        float wx = __ldg(wp), wy = __ldg(wp + 1), wz = __ldg(wp + 2);
+        float w1 = wx * F.e1x + wy * F.e1y + wz * F.e1z;
+        float w2 = wx * F.e2x + wy * F.e2y + wz * F.e2z;
+        cw.c[k] = w1 * w.dx + w2 * w.dy;   // component along d
+        cw.s[k] = w.dx * w2 - w.dy * w1;   // component along perp(d) = (-dy, dx)
+    }
+    int zeros = (b0 == 0.f) + (b1 == 0.f) + (b2 == 0.f);
+    if (zeros) w.st |= SG_ST_START_ON_EDGE;
+    if (zeros == 2 && L > 0.f) {
+        // start on a vertex: the direction must point into this face's corner (reading)
+        int c = b0 == 1.f ? 0 : (b1 == 1.f ? 1 : 2);
+        float cx = corner_x(w.R, c), cy = corner_y(w.R, c);
+        float ax = corner_x(w.R, nxt(c)) - cx, ay = corner_y(w.R, nxt(c)) - cy;
+        float bx = corner_x(w.R, prv(c)) - cx, by = corner_y(w.R, prv(c)) - cy;
+        if (!(ax * w.dy - ay * w.dx > 0.f && w.dx * by - w.dy * bx > 0.f)) {
+            w.st |= SG_ST_INVALID;
+            w.Lh = 0.f;
+            return false;
+        }
+        w.px = cx; w.py = cy;
+        w.mode = 3 + c;
+    }
+    // the face sequence starts with the start face of every query that walks (L > 0)
+    if (L > 0.f) walker_hash(w, w.f, P.want_hash);
+    return L > 0.f;
+}
+
