@@ -156,6 +156,30 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
                      float *out_dir, float *out_w, uint32_t *out_status, int32_t *out_ncross,
                      uint64_t *out_hash, const sg_opts *o, void *stream);
 
+/*
+ * sg_exp_map_noalloc -- sg_exp_map for callers that cannot allocate device memory when they
+ * call in: for example code running inside a framework that owns all device memory through
+ * its own pool, or a latency-critical loop where a cudaMalloc/cudaFree (which can
+ * synchronise the device) is not allowed.  The paper has no counterpart; it is an interface
+ * convenience of this library.
+ * Same arguments, outputs and errors as sg_exp_map; o->workspace is ignored.  The scratch
+ * (work-queue counter and start-face sort) lives in one fixed 32 MiB device array inside the
+ * library, which every GPU that loads the library holds until the process exits.  Batches
+ * whose scratch (sg_exp_map_workspace_size with the same options) exceeds 32 MiB are rejected
+ * with SG_ERR_OOM and nothing is launched; with o->sort = 0 the scratch is 64 bytes and any
+ * batch size fits.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls share the one
+ * array: the library clears what must start at zero on every call, but calls whose GPU work
+ * overlaps in time (concurrent streams, several host threads) race on it and must be
+ * serialised by the caller.
+ */
+sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
+                             const float *bary, const float *v, const float *length, int32_t n_w,
+                             const float *w, int32_t *out_face, float *out_bary, float *out_pos,
+                             float *out_dir, float *out_w, uint32_t *out_status, int32_t *out_ncross,
+                             uint64_t *out_hash, const sg_opts *o, void *stream);
+
 /* backward estimators */
 #define SG_EST_EP 0   /* Eq. proxy_func: J^v = R, J^p zeroed */
 #define SG_EST_GFD 1  /* Eqs. jv, jp: geodesic finite differences */

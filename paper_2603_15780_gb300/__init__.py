@@ -33,7 +33,7 @@ EST_EP, EST_GFD = 0, 1
 
 EXPORTED = ["sg_opts_default", "sg_status_string", "sg_mesh_create", "sg_mesh_create_batched",
             "sg_mesh_destroy", "sg_mesh_get_info", "sg_exp_map_workspace_size", "sg_exp_map",
-            "sg_exp_map_backward", "sg_version"]
+            "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc"]
 
 
 def status_names(st: int) -> list[str]:
@@ -86,6 +86,7 @@ def lib():
             L.sg_exp_map_workspace_size.argtypes = [P, C.c_int64, C.POINTER(Opts), C.POINTER(C.c_size_t)]
             L.sg_exp_map.argtypes = [P, C.c_int64, P, P, P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P,
                                      C.POINTER(Opts), P]
+            L.sg_exp_map_noalloc.argtypes = list(L.sg_exp_map.argtypes)
             L.sg_exp_map_backward.argtypes = [P, C.c_int32, C.c_float, C.c_float, C.c_int64, P, P, P, P,
                                               P, P, P, P, P, P, P, P, P, P, C.POINTER(Opts), P]
             for f in EXPORTED:

@@ -451,3 +451,54 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free variant
+// Scratch for sg_exp_map_noalloc: a fixed, file-scope device array (every GPU that loads the
+// library holds it until the process exits).  Host code must not use the array's name as a
+// device address; the address is looked up once per device with cudaGetSymbolAddress.
+#include <mutex>
+
+#define SG_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define SG_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_sg_noalloc_scratch[SG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[SG_NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+extern "C" sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
+                                        const float *bary, const float *v, const float *length, int32_t n_w,
+                                        const float *w, int32_t *out_face, float *out_bary, float *out_pos,
+                                        float *out_dir, float *out_w, uint32_t *out_status, int32_t *out_ncross,
+                                        uint64_t *out_hash, const sg_opts *o, void *stream) {
+    if (!m) return SG_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SG_ERR_CUDA; }
+    if (dev < 0 || dev >= SG_NOALLOC_MAX_DEVICES) return SG_ERR_UNSUPPORTED;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_sg_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return SG_ERR_CUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    sg_opts r;
+    sg_opts_default(&r);
+    if (o) r = *o;
+    size_t need = 0;
+    sg_status st = sg_exp_map_workspace_size(m, nq, &r, &need);
+    if (st != SG_OK) return st;
+    if (need > SG_NOALLOC_SCRATCH_BYTES) return SG_ERR_OOM;
+    r.workspace = scratch;
+    r.workspace_bytes = SG_NOALLOC_SCRATCH_BYTES;
+    return sg_exp_map(m, nq, mesh_id, face, bary, v, length, n_w, w, out_face, out_bary, out_pos, out_dir, out_w,
+                      out_status, out_ncross, out_hash, &r, stream);
+}
