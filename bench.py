@@ -195,13 +195,13 @@ def main():
         sg.exp_map(mesh, face, bary, v, out=out, workspace=ws, opts=opts)
         if ev is not None:
             ev[1].record(stream)
-        sg.exp_map_backward(mesh, "ep", face, bary, v, out["face"], out["dir"], out["status"], g)
+        sg.exp_map_backward(mesh, "ep", face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g)
         if ev is not None:
             ev[2].record(stream)
         gV.zero_()
         if ev is not None:
             ev[3].record(stream)
-        r = sg.exp_map_backward(mesh, "gfd", face, bary, v, out["face"], out["dir"], out["status"], g,
+        r = sg.exp_map_backward(mesh, "gfd", face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g,
                                 eps_v=EPS, eps_p=EPS, grad_V=gV)
         if ev is not None:
             ev[4].record(stream)
@@ -258,9 +258,9 @@ def main():
             vd = hb["v"].to(dev, non_blocking=True)
             gd = hb["g"].to(dev, non_blocking=True)
             o = sg.exp_map(mesh, fd, bd, vd, workspace=ws, opts=opts)
-            sg.exp_map_backward(mesh, "ep", fd, bd, vd, o["face"], o["dir"], o["status"], gd)
+            sg.exp_map_backward(mesh, "ep", fd, bd, vd, o["face"], o["bary"], o["dir"], o["status"], gd)
             gV.zero_()
-            r = sg.exp_map_backward(mesh, "gfd", fd, bd, vd, o["face"], o["dir"], o["status"], gd,
+            r = sg.exp_map_backward(mesh, "gfd", fd, bd, vd, o["face"], o["bary"], o["dir"], o["status"], gd,
                                     eps_v=EPS, eps_p=EPS, grad_V=gV)
             host_out["grad_v"].copy_(r["grad_v"], non_blocking=True)
             host_out["grad_p"].copy_(r["grad_p"], non_blocking=True)

@@ -209,6 +209,16 @@ sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, 
                               float *grad_v, float *grad_p, float *grad_bary, float *grad_V,
                               uint32_t *out_status, const sg_opts *o, void *stream);
 
+/*
+ * sg_exp_map_backward_workspace_size -- bytes of device scratch sg_exp_map_backward needs for
+ * nq queries with `estimator` (SG_EST_*) and, if want_grad_V != 0, the vertex gradient: the
+ * GFD column table (16 B per query) and swept-perturbation task list (12 B per query), and
+ * a float4 accumulator per vertex for grad_V.  Pass it as o->workspace; without it the
+ * library allocates stream-ordered scratch itself.
+ */
+sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_t estimator, int64_t nq,
+                                             int32_t want_grad_V, size_t *bytes);
+
 /* Library version string. */
 const char *sg_version(void);
 

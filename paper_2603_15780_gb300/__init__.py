@@ -33,7 +33,7 @@ EST_EP, EST_GFD = 0, 1
 
 EXPORTED = ["sg_opts_default", "sg_status_string", "sg_mesh_create", "sg_mesh_create_batched",
             "sg_mesh_destroy", "sg_mesh_get_info", "sg_exp_map_workspace_size", "sg_exp_map",
-            "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc"]
+            "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc", "sg_exp_map_backward_workspace_size"]
 
 
 def status_names(st: int) -> list[str]:
@@ -87,6 +87,8 @@ def lib():
             L.sg_exp_map.argtypes = [P, C.c_int64, P, P, P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P,
                                      C.POINTER(Opts), P]
             L.sg_exp_map_noalloc.argtypes = list(L.sg_exp_map.argtypes)
+            L.sg_exp_map_backward_workspace_size.argtypes = [P, C.c_int32, C.c_int64, C.c_int32,
+                                                             C.POINTER(C.c_size_t)]
             L.sg_exp_map_backward.argtypes = [P, C.c_int32, C.c_float, C.c_float, C.c_int64, P, P, P, P,
                                               P, P, P, P, P, P, P, P, P, P, C.POINTER(Opts), P]
             for f in EXPORTED:
@@ -246,9 +248,17 @@ def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, mesh_id=None, *, wan
     return out
 
 
-def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_dir, end_status, g_pos,
-                     mesh_id=None, end_bary=None, *, eps_v=1e-4, eps_p=1e-4, want_grad_V=False,
-                     grad_V=None, opts: Opts | None = None, stream=None):
+def backward_workspace_size(mesh: Mesh, estimator, nq: int, want_grad_V: bool) -> int:
+    est = {"ep": EST_EP, "gfd": EST_GFD}.get(estimator, estimator)
+    n = C.c_size_t()
+    _check(lib().sg_exp_map_backward_workspace_size(mesh.handle, est, nq, int(bool(want_grad_V)), C.byref(n)),
+           "sg_exp_map_backward_workspace_size")
+    return n.value
+
+
+def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_bary, end_dir, end_status, g_pos,
+                     mesh_id=None, *, eps_v=1e-4, eps_p=1e-4, want_grad_V=False,
+                     grad_V=None, opts: Opts | None = None, workspace=None, stream=None):
     """sg_exp_map_backward.  estimator: "ep"/"gfd" or EST_*.  Returns dict(grad_v, grad_p,
     grad_bary, grad_V (if requested; accumulated into `grad_V` when given), status)."""
     torch = _torch()
@@ -272,6 +282,11 @@ def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_dir, en
             grad_V = torch.zeros(mesh.n_vertices, 3, device=dev)
         res["grad_V"] = grad_V
     o = opts if opts is not None else default_opts()
+    if workspace is None:
+        workspace = torch.empty(backward_workspace_size(mesh, est, nq, "grad_V" in res), dtype=torch.uint8,
+                                device=dev)
+    o.workspace = workspace.data_ptr()
+    o.workspace_bytes = workspace.numel()
     s = stream if stream is not None else torch.cuda.current_stream()
     rc = lib().sg_exp_map_backward(mesh.handle, est, eps_v, eps_p, nq, _ptr(mesh_id), _ptr(face), _ptr(bary),
                                    _ptr(v), _ptr(end_face), _ptr(end_bary), _ptr(end_dir), _ptr(end_status),
@@ -294,16 +309,16 @@ def _autograd_function():
         def forward(ctx, mesh, face, bary, v, estimator="gfd", V=None, mesh_id=None, eps=1e-4):
             out = exp_map(mesh, face, bary.detach(), v.detach(), mesh_id=mesh_id)
             ctx.mesh, ctx.estimator, ctx.eps = mesh, estimator, eps
-            ctx.save_for_backward(face, bary.detach(), v.detach(), out["face"], out["dir"], out["status"],
-                                  mesh_id if mesh_id is not None else torch.empty(0))
+            ctx.save_for_backward(face, bary.detach(), v.detach(), out["face"], out["bary"], out["dir"],
+                                  out["status"], mesh_id if mesh_id is not None else torch.empty(0))
             ctx.has_V = V is not None
             ctx.mark_non_differentiable(out["face"], out["status"])
             return out["pos"], out["face"], out["bary"], out["dir"], out["status"]
 
         @staticmethod
         def backward(ctx, g_pos, _gf, _gb, _gd, _gs):
-            face, bary, v, ef, ed, es, mid = ctx.saved_tensors
-            r = exp_map_backward(ctx.mesh, ctx.estimator, face, bary, v, ef, ed, es, g_pos.contiguous(),
+            face, bary, v, ef, eb, ed, es, mid = ctx.saved_tensors
+            r = exp_map_backward(ctx.mesh, ctx.estimator, face, bary, v, ef, eb, ed, es, g_pos.contiguous(),
                                  mesh_id=mid if mid.numel() else None, eps_v=ctx.eps, eps_p=ctx.eps,
                                  want_grad_V=ctx.needs_input_grad[5] and ctx.has_V)
             gV = r.get("grad_V")

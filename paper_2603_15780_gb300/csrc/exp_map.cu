@@ -91,26 +91,48 @@ __device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
     return (int64_t)base + rank;
 }
 
+// Lanes whose walk has ended keep their final state in registers until enough lanes of the
+// warp are idle (SG_REFILL_LANES), then all idle lanes write their outputs, take new tickets
+// and initialise together, so the long init/finish code runs with many lanes active instead
+// of stalling the warp for one lane every few steps.  Once the queue is exhausted, lanes
+// write as soon as they finish and the warp leaves when all its lanes are idle.
+#define SG_REFILL_LANES 8
+
 template <int NW, bool ESC>
-__global__ void __launch_bounds__(256) k_walk_persistent(FwdArgs a) {
+__global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
     Walker w;
     Carry<NW> cw;
     int64_t q = -1;
-    bool live = false;
+    bool live = false, pending = false, exhausted = false;
+    const unsigned FULL = 0xffffffffu;
     while (true) {
-        if (!live) {
-            int64_t t = fetch_ticket(a.counter);
-            if (t >= a.nq) break;
-            q = a.perm ? (int64_t)__ldg(a.perm + t) : t;
-            live = walker_init<NW>(a.P, a.in, q, w, cw);
+        unsigned idle = __ballot_sync(FULL, !live);
+        if (exhausted && idle == FULL) break;
+        if (!exhausted && __popc(idle) >= SG_REFILL_LANES) {
+            bool dry = false;
             if (!live) {
-                walker_finish<NW>(a, q, w, cw);
-                continue;
+                if (pending) {
+                    walker_finish<NW>(a, q, w, cw);
+                    pending = false;
+                }
+                int64_t t = fetch_ticket(a.counter);
+                if (t >= a.nq) {
+                    dry = true;
+                } else {
+                    q = a.perm ? (int64_t)__ldg(a.perm + t) : t;
+                    live = walker_init<NW>(a.P, a.in, q, w, cw);
+                    if (!live) walker_finish<NW>(a, q, w, cw);
+                }
             }
+            exhausted = __any_sync(FULL, dry);
         }
-        if (walker_step<ESC>(w, a.P)) {
-            walker_finish<NW>(a, q, w, cw);
+        if (live && walker_step<ESC>(w, a.P)) {
             live = false;
+            pending = true;
+        }
+        if (exhausted && pending) {
+            walker_finish<NW>(a, q, w, cw);
+            pending = false;
         }
     }
 }
@@ -330,6 +352,7 @@ sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int
     };
     bool ok = up((void **)&m->d_rec, H.rec.data(), sizeof(int4) * H.rec.size()) &&
               up((void **)&m->d_fv, H.fv.data(), sizeof(int4) * H.fv.size()) &&
+              up((void **)&m->d_frm, H.frm.data(), sizeof(float4) * H.frm.size()) &&
               up((void **)&m->d_V, H.V.data(), sizeof(float4) * H.V.size()) &&
               up((void **)&m->d_face_off, H.face_off.data(), sizeof(int32_t) * H.face_off.size()) &&
               up((void **)&m->d_lref, H.lref.data(), sizeof(float) * H.lref.size());
@@ -352,6 +375,7 @@ sg_status sg_mesh_destroy(sg_mesh *m) {
     if (!m) return SG_OK;
     cudaFree(m->d_rec);
     cudaFree(m->d_fv);
+    cudaFree(m->d_frm);
     cudaFree(m->d_V);
     cudaFree(m->d_face_off);
     cudaFree(m->d_lref);
@@ -391,7 +415,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a{};
-    a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
+    a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.frm = m->d_frm; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
     a.P.max_steps = r.max_steps; a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
     a.P.want_hash = out_hash != nullptr;
     a.nq = nq; a.in.n_mesh = m->n_mesh; a.nF_total = (int32_t)m->nF;

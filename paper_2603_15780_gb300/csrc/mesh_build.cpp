@@ -51,6 +51,7 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
 
     out->rec.assign(2 * nF, int4{0, 0, 0, 0});
     out->fv.assign(nF, int4{0, 0, 0, 0});
+    out->frm.assign(2 * nF, float4{0, 0, 0, 0});
     out->V.assign(nV, float4{0, 0, 0, 0});
     out->face_off.assign(n_mesh + 1, 0);
     out->lref.assign(n_mesh, 0.f);
@@ -91,6 +92,8 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
             r1.w = bits((float)(1.0 / l20));
             out->rec[2 * (f0 + f)].w = bits((float)l01);
             out->fv[f0 + f] = int4{(int)(v0 + t[0]), (int)(v0 + t[1]), (int)(v0 + t[2]), m};
+            out->frm[2 * (f0 + f)] = float4{(float)u.x, (float)u.y, (float)u.z, (float)w.x};
+            out->frm[2 * (f0 + f) + 1] = float4{(float)w.y, (float)w.z, 0.f, 0.f};
             // corner angles -> theta
             for (int k = 0; k < 3; ++k) {
                 D3 a = sub(X(t[(k + 1) % 3]), X(t[k])), b = sub(X(t[(k + 2) % 3]), X(t[k]));

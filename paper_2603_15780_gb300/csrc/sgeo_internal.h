@@ -13,6 +13,9 @@
 //                      corner 1 on +x, corner 2 in the upper half plane):
 //                      P0 = (0,0), P1 = (l01,0), P2 = (x2x,x2y); il1 = 1/|P2-P1|, il2 = 1/|P2|.
 //   fv    int4[nF]     global vertex ids of the face corners, .w = mesh index
+//   frm   float4[2*nF] the face frame in 3-D: {e1x, e1y, e1z, e2x}, {e2y, e2z, 0, 0} with
+//                      e1 = (x1-x0)/|x1-x0|, e2 = n x e1 (the axes of the 2-D record frame);
+//                      read by the backward pass (lifting 2-D adjoints, chord walks)
 //   V     float4[nV]   vertex position (x,y,z); .w = total angle theta(x), negated for boundary
 //                      vertices (Sec. 4: theta = sum of incident corner angles)
 //   face_off int32[n_mesh+1], lref float[n_mesh] (mean edge length per mesh)
@@ -33,6 +36,7 @@ struct sg_mesh {
     int device = 0;
     int4 *d_rec = nullptr;
     int4 *d_fv = nullptr;
+    float4 *d_frm = nullptr;
     float4 *d_V = nullptr;
     int32_t *d_face_off = nullptr;
     float *d_lref = nullptr;
@@ -44,6 +48,7 @@ struct sg_mesh {
 // host-side builder (mesh_build.cpp); fills the host arrays, returns SG_OK or an error
 struct sg_host_mesh {
     std::vector<int4> rec, fv;
+    std::vector<float4> frm;
     std::vector<float4> V;
     std::vector<int32_t> face_off;
     std::vector<float> lref;

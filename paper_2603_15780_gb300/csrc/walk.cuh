@@ -54,6 +54,7 @@ __device__ __forceinline__ int prv(int k) { return k == 0 ? 2 : k - 1; }
 struct WalkParams {
     const int4 *__restrict__ rec;
     const int4 *__restrict__ fv;
+    const float4 *__restrict__ frm;
     const float4 *__restrict__ V;
     const int32_t *__restrict__ face_off;
     const float *__restrict__ lref;

@@ -34,7 +34,7 @@ def forward_backward(mesh, q, estimator, eps=1e-4, grad_V=False, g=None):
     f32 = parity.as_f32
     out = S.exp_map(mesh, q.face, f32(q.bary), f32(q.v))
     gg = f32(q.g_pos if g is None else g)
-    r = S.exp_map_backward(mesh, estimator, q.face, f32(q.bary), f32(q.v), out["face"], out["dir"], out["status"],
+    r = S.exp_map_backward(mesh, estimator, q.face, f32(q.bary), f32(q.v), out["face"], out["bary"], out["dir"], out["status"],
                            gg, eps_v=eps, eps_p=eps, want_grad_V=grad_V)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in r.items()}
@@ -146,7 +146,7 @@ def test_flat_mesh_gradients_closed_form():
     clean = (st & (oracle.BOUNDARY | parity.FLAGS | oracle.VERTEX_HIT)) == 0
     g = parity.as_f32(q.g_pos) * clean[:, None]
     r = S.exp_map_backward(mesh, "ep", q.face, parity.as_f32(q.bary), parity.as_f32(q.v), out["face"],
-                           out["dir"], out["status"], g, want_grad_V=True)
+                           out["bary"], out["dir"], out["status"], g, want_grad_V=True)
     gV = r["grad_V"].cpu().numpy()
     expect = np.zeros_like(gV, dtype=np.float64)
     ef = out["face"].cpu().numpy()
