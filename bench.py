@@ -181,6 +181,20 @@ def main():
     opts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
                            block=args.block if args.block > 0 else None)
     ws = torch.empty(sg.workspace_size(mesh, nq, opts), dtype=torch.uint8, device=dev)
+    bopts = sg.default_opts()
+    bws = torch.empty(sg.backward_workspace_size(mesh, "gfd", nq, True), dtype=torch.uint8, device=dev)
+    # per-kernel events recorded by the library around its walk kernels (forward walk, GFD re-walk)
+    kev = {k: [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for k in ("walk", "rewalk")}
+    for pair in kev.values():
+        for e in pair:
+            e.record()
+    import ctypes
+    kh = {k: (ctypes.c_void_p * 2)(pair[0].cuda_event, pair[1].cuda_event) for k, pair in kev.items()}
+    popts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
+                            block=args.block if args.block > 0 else None)
+    popts.prof_events = ctypes.addressof(kh["walk"])
+    pbopts = sg.default_opts()
+    pbopts.prof_events = ctypes.addressof(kh["rewalk"])
     out = {"face": torch.empty(nq, dtype=torch.int32, device=dev), "bary": torch.empty(nq, 3, device=dev),
            "pos": torch.empty(nq, 3, device=dev), "dir": torch.empty(nq, 3, device=dev),
            "status": torch.empty(nq, dtype=torch.int32, device=dev),
@@ -192,17 +206,19 @@ def main():
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        sg.exp_map(mesh, face, bary, v, out=out, workspace=ws, opts=opts)
+        sg.exp_map(mesh, face, bary, v, out=out, workspace=ws, opts=popts if ev is not None else opts)
         if ev is not None:
             ev[1].record(stream)
-        sg.exp_map_backward(mesh, "ep", face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g)
+        sg.exp_map_backward(mesh, "ep", face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g,
+                            opts=bopts, workspace=bws)
         if ev is not None:
             ev[2].record(stream)
         gV.zero_()
         if ev is not None:
             ev[3].record(stream)
         r = sg.exp_map_backward(mesh, "gfd", face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g,
-                                eps_v=EPS, eps_p=EPS, grad_V=gV)
+                                eps_v=EPS, eps_p=EPS, grad_V=gV, opts=pbopts if ev is not None else bopts,
+                                workspace=bws)
         if ev is not None:
             ev[4].record(stream)
         return r
@@ -216,6 +232,7 @@ def main():
     clk = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")) if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else Clocks(local, f"/tmp/clocks_r{rank}.csv")
     times = np.zeros((args.steps, 4))
+    ktimes = {"walk": [], "rewalk": []}
     for k in range(args.steps):
         flush.zero_()                    # evict L2 between timed iterations (not timed)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -226,6 +243,8 @@ def main():
         torch.cuda.synchronize()
         times[k] = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
                     ev[3].elapsed_time(ev[4])]
+        for kk, pair in kev.items():
+            ktimes[kk].append(pair[0].elapsed_time(pair[1]))
     clocks = clk.stop()
     total_ms = float(times.sum())
     if world > 1:
@@ -272,20 +291,26 @@ def main():
         e2e = {"value": nq / (np.mean(e_ms) * 1e-3), "unit": "geodesics/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    # ---- roofline of the dominant kernel (the GFD re-walk with vertex gradients)
+    # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     peak, peak_kind = peaks()
-    # algorithmic bytes per launch: per crossing one 32-B record + the face's vertex ids and
-    # 3 vertices (16 B each) for the vertex-gradient adjoint + 2 x 12 B atomic adds; per query
-    # inputs (face, bary, v, g: 40 B), forward outputs read (face, dir, status: 20 B), start/end
-    # frames (2 x 64 B) and outputs (grad_v, grad_p, grad_bary, status: 40 B)
-    gfd_bytes = ncross * (RECORD_BYTES + 64 + 24) + nq * (40 + 20 + 128 + 40)
-    fwd_bytes = ncross * RECORD_BYTES + nq * (28 + 48 + 128)
-    kern = {"fwd_walk": (fwd_bytes, fwd_ms), "gfd_rewalk": (gfd_bytes, gfd_ms)}
+    # forward walk: one 32-B record per crossing; per query the inputs (face, bary, v: 28 B),
+    # the queue ticket permutation (4 B), the outputs (face, bary, pos, dir, status, ncross:
+    # 48 B) and the start and end frame gathers (vertex ids + 3 vertices: 2 x 64 B)
+    walk_bytes = ncross * RECORD_BYTES + nq * (28 + 4 + 48 + 128)
+    # GFD re-walk with vertex gradients: per crossing the record (32 B), the new face's
+    # vertex ids (16 B) and 3-D frame (32 B) and one float4 accumulator flush (16 B); per
+    # query inputs (28 B), the forward end state and upstream gradient (48 B), start/end
+    # frames and vertices (96 B), start/end atomic adds (6 x 16 B), status (4 B)
+    rewalk_bytes = ncross * (RECORD_BYTES + 16 + 32 + 16) + nq * (28 + 48 + 96 + 96 + 4)
+    kern = {"k_walk_persistent": (walk_bytes, float(np.mean(ktimes["walk"]))),
+            "k_bwd_rewalk": (rewalk_bytes, float(np.mean(ktimes["rewalk"])))}
     dom = max(kern, key=lambda k: kern[k][1])
     achieved = kern[dom][0] / (kern[dom][1] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                "algorithmic_bytes": int(kern[dom][0])}
+                "algorithmic_bytes_per_launch": int(kern[dom][0]), "launch_ms": kern[dom][1]}
+    kernels = {k: {"ms": t, "algorithmic_GBps": b / (t * 1e-3) / 1e9, "frac_of_hbm": b / (t * 1e-3) / 1e9 / peak}
+               for k, (b, t) in kern.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "geodesics/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -294,14 +319,14 @@ def main():
                        "faces": int(len(F)), "queries_per_gpu": nq, "l2": "flushed between steps (512 MB write)",
                        "kernel": "persistent" if args.kernel == 2 else "plain", "sort": bool(args.sort),
                        "fp64_classification": bool(args.fp64)},
-            "crossings_per_s": world * ncross / (fwd_ms * 1e-3),
+            "crossings_per_s": world * ncross / (float(np.mean(ktimes["walk"])) * 1e-3),
             "fwd_geodesics_per_s": world * nq / (fwd_ms * 1e-3),
             "phase_ms": {"fwd": fwd_ms, "ep_bwd": ep_ms, "gfd_bwd_gradV": gfd_ms},
             "crossings_per_query": ncross / nq,
             "flag_fraction": {"near_vertex": float(((st & 4) != 0).mean()), "near_edge": float(((st & 8) != 0).mean()),
                               "fp64": float(((st & 32) != 0).mean())},
-            "gpu_launches": args.steps * 8,  # per step: 5 sort/scan + walk + EP + GFD re-walk
-            "roofline": roofline, "clocks": clocks, "e2e": e2e}
+            "gpu_launches": args.steps * 12,  # per step: 5 sort/scan + walk, EP, re-walk + chords + literal + assemble + grad_V flush
+            "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         n, dt, _ = oracle_sample(args.cpu_sample, threads)

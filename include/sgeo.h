@@ -79,6 +79,9 @@ typedef struct sg_opts {
     void *workspace;        /* optional device scratch (see sg_exp_map_workspace_size); NULL: the
                                library allocates stream-ordered scratch itself */
     size_t workspace_bytes;
+    void *prof_events;      /* optional: pointer to two cudaEvent_t recorded on `stream` right
+                               before and after the call's walk kernel (forward walk, or the
+                               backward re-walk), for per-kernel timing; NULL: none */
 } sg_opts;
 
 /* Fills `o` with the defaults described above. */

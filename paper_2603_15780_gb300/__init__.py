@@ -53,7 +53,7 @@ class Opts(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("kernel", C.c_int32), ("sort", C.c_int32),
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("fp64_escalate", C.c_int32),
                 ("tau_near", C.c_float), ("tau_snap", C.c_float), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("prof_events", C.c_void_p)]
 
 
 class MeshInfo(C.Structure):

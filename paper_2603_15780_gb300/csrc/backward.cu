@@ -274,86 +274,103 @@ struct RewalkHook {
 
 // ------------------------------------------------------------------ kernel 1: re-walk
 template <bool GFD, bool GRADV>
-__global__ void __launch_bounds__(128) k_bwd_rewalk(BwdArgs A) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= A.nq) return;
-    const WalkParams &P = A.P;
+struct RewalkJob {
+    const BwdArgs *A;
     Walker w;
-    Carry<0> cw;
-    bool live = walker_init<0>(P, A.in, q, w, cw);
-    if (!live || (w.st & SG_ST_INVALID)) {
-        if (A.out_status) A.out_status[q] = (w.st & ~SG_PARITY_BIT) | (GRADV ? SG_ST_NO_GRADV : 0u);
-        return;
-    }
-    uint32_t st = 0;
-    uint32_t fst = A.end_status ? __ldg(A.end_status + q) : 0u;
     RewalkHook<GFD, GRADV> H;
-    H.gradv = GRADV && !(fst & (SG_ST_VERTEX_HIT | SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_INVALID));
-    if (GRADV && !H.gradv) st |= SG_ST_NO_GRADV;
-    const float L = w.Lh, d0x = w.dx, d0y = w.dy;
-    if (GFD) {
-        sincosf(atan2f(A.eps_v, L), &H.S.sphi, &H.S.cphi);
-        H.S.Ltot = L;
-        H.S.tol = P.tau_near * w.lref;
-        H.S.split = 0u;
-        float evx = w.R.x2x * w.R.il2, evy = w.R.x2y * w.R.il2;  // e_u = (1,0), e_v = P2/|P2|
-        H.S.ua = A.eps_p * d0x;  H.S.ub = -A.eps_p * d0y;
-        H.S.va = A.eps_p * (evx * d0x + evy * d0y);
-        H.S.vb = A.eps_p * (-evx * d0y + evy * d0x);
-    }
-    F3 gq = f3(0.f, 0.f, 0.f);
-    if (GRADV && H.gradv) {
-        EndAdj E = end_adjoint(A, q, w.foff);
-        gq = E.g;
-        H.G.gacc = A.gacc;
-        H.G.P = &P;
-        H.G.a = E.a;
-        H.G.bs = E.sm * E.b;
-        H.G.fvc = __ldg(P.fv + w.f);
-        H.G.Fc = load_frm(P, w.f);
-        H.G.v0 = -1; H.G.v1 = -1;
-        H.G.c0 = f3(0.f, 0.f, 0.f); H.G.c1 = f3(0.f, 0.f, 0.f);
-        // start face: p0 = sum b_k P_k -> grad x_k += b_k F0 gbar0; tilt term if v has a normal
-        // component (moving the plane changes the projection of v)
-        const float g0x = E.a * d0x - E.sm * E.b * d0y, g0y = E.a * d0y + E.sm * E.b * d0x;
-        float b2 = w.py / w.R.x2y, b1 = (w.px - b2 * w.R.x2x) / w.R.l01, b0 = 1.f - b1 - b2;
-        F3 G0 = lift(H.G.Fc, g0x, g0y);
-        F3 n0 = nrm_of(H.G.Fc);
-        float vn = dot3(ld3(A.in.v, q), n0);
-        F3 x0 = vpos(P, H.G.fvc.x), u = vpos(P, H.G.fvc.y) - x0, ww = vpos(P, H.G.fvc.z) - x0;
-        F3 m = cross3(u, ww);
-        F3 h = (-vn * rsqrtf(dot3(m, m))) * G0;
-        F3 t1 = cross3(ww, h), t2 = cross3(h, u);
-        atomic_add3(A.gacc, H.G.fvc.x, b0 * G0 - (t1 + t2));
-        atomic_add3(A.gacc, H.G.fvc.y, b1 * G0 + t1);
-        atomic_add3(A.gacc, H.G.fvc.z, b2 * G0 + t2);
-    }
-    while (!walker_step<true>(w, P, H)) {
-    }
-    st |= w.st & ~SG_PARITY_BIT;
-    if (GRADV && H.gradv) {
-        H.G.flush(H.G.v0, H.G.c0);
-        H.G.flush(H.G.v1, H.G.c1);
-        // end face: grad x_j += b'_j (g . n) n
-        const FaceRec &R = w.R;
-        float b2 = w.py / R.x2y, b1 = (w.px - b2 * R.x2x) / R.l01, b0 = 1.f - b1 - b2;
-        F3 n = nrm_of(H.G.Fc);
-        F3 gn = dot3(gq, n) * n;
-        atomic_add3(A.gacc, H.G.fvc.x, b0 * gn);
-        atomic_add3(A.gacc, H.G.fvc.y, b1 * gn);
-        atomic_add3(A.gacc, H.G.fvc.z, b2 * gn);
-    }
-    if (GFD) {
-        unsigned split = H.S.split;
-        if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) split = 7u;
-        if (split) {
-            st |= SG_ST_GFD_SPLIT;
-            int base = atomicAdd(A.ntask, __popc(split));
-            for (int k = 0; k < 3; ++k)
-                if (split & (1u << k)) A.tasks[base++] = (int32_t)((q << 2) | (k + 1));
+    int64_t q;
+    uint32_t st;
+    bool valid;
+    F3 gq;
+
+    __device__ __forceinline__ bool init(int64_t t) {
+        q = t;
+        const WalkParams &P = A->P;
+        Carry<0> cw;
+        bool live = walker_init<0>(P, A->in, q, w, cw);
+        valid = live && !(w.st & SG_ST_INVALID);
+        st = 0;
+        if (!valid) return false;
+        uint32_t fst = A->end_status ? __ldg(A->end_status + q) : 0u;
+        H.gradv = GRADV && !(fst & (SG_ST_VERTEX_HIT | SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_INVALID));
+        if (GRADV && !H.gradv) st |= SG_ST_NO_GRADV;
+        const float L = w.Lh, d0x = w.dx, d0y = w.dy;
+        if (GFD) {
+            sincosf(atan2f(A->eps_v, L), &H.S.sphi, &H.S.cphi);
+            H.S.Ltot = L;
+            H.S.tol = P.tau_near * w.lref;
+            H.S.split = 0u;
+            float evx = w.R.x2x * w.R.il2, evy = w.R.x2y * w.R.il2;  // e_u = (1,0), e_v = P2/|P2|
+            H.S.ua = A->eps_p * d0x;  H.S.ub = -A->eps_p * d0y;
+            H.S.va = A->eps_p * (evx * d0x + evy * d0y);
+            H.S.vb = A->eps_p * (-evx * d0y + evy * d0x);
         }
+        if (GRADV && H.gradv) {
+            EndAdj E = end_adjoint(*A, q, w.foff);
+            gq = E.g;
+            H.G.gacc = A->gacc;
+            H.G.P = &A->P;
+            H.G.a = E.a;
+            H.G.bs = E.sm * E.b;
+            H.G.fvc = __ldg(P.fv + w.f);
+            H.G.Fc = load_frm(P, w.f);
+            H.G.v0 = -1; H.G.v1 = -1;
+            H.G.c0 = f3(0.f, 0.f, 0.f); H.G.c1 = f3(0.f, 0.f, 0.f);
+            // start face: p0 = sum b_k P_k -> grad x_k += b_k F0 gbar0; tilt term if v has a
+            // normal component (moving the plane changes the projection of v)
+            const float g0x = E.a * d0x - E.sm * E.b * d0y, g0y = E.a * d0y + E.sm * E.b * d0x;
+            float b2 = w.py / w.R.x2y, b1 = (w.px - b2 * w.R.x2x) / w.R.l01, b0 = 1.f - b1 - b2;
+            F3 G0 = lift(H.G.Fc, g0x, g0y);
+            F3 n0 = nrm_of(H.G.Fc);
+            float vn = dot3(ld3(A->in.v, q), n0);
+            F3 x0 = vpos(P, H.G.fvc.x), u = vpos(P, H.G.fvc.y) - x0, ww = vpos(P, H.G.fvc.z) - x0;
+            F3 m = cross3(u, ww);
+            F3 h = (-vn * rsqrtf(dot3(m, m))) * G0;
+            F3 t1 = cross3(ww, h), t2 = cross3(h, u);
+            atomic_add3(A->gacc, H.G.fvc.x, b0 * G0 - (t1 + t2));
+            atomic_add3(A->gacc, H.G.fvc.y, b1 * G0 + t1);
+            atomic_add3(A->gacc, H.G.fvc.z, b2 * G0 + t2);
+        }
+        return true;
     }
-    if (A.out_status) A.out_status[q] = st;
+    __device__ __forceinline__ bool step() { return walker_step<true>(w, A->P, H); }
+    __device__ __forceinline__ void finish() {
+        if (!valid) {
+            if (A->out_status) A->out_status[q] = (w.st & ~SG_PARITY_BIT) | (GRADV ? SG_ST_NO_GRADV : 0u);
+            return;
+        }
+        st |= w.st & ~SG_PARITY_BIT;
+        if (GRADV && H.gradv) {
+            H.G.flush(H.G.v0, H.G.c0);
+            H.G.flush(H.G.v1, H.G.c1);
+            // end face: grad x_j += b'_j (g . n) n
+            const FaceRec &R = w.R;
+            float b2 = w.py / R.x2y, b1 = (w.px - b2 * R.x2x) / R.l01, b0 = 1.f - b1 - b2;
+            F3 n = nrm_of(H.G.Fc);
+            F3 gn = dot3(gq, n) * n;
+            atomic_add3(A->gacc, H.G.fvc.x, b0 * gn);
+            atomic_add3(A->gacc, H.G.fvc.y, b1 * gn);
+            atomic_add3(A->gacc, H.G.fvc.z, b2 * gn);
+        }
+        if (GFD) {
+            unsigned split = H.S.split;
+            if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) split = 7u;
+            if (split) {
+                st |= SG_ST_GFD_SPLIT;
+                int base = atomicAdd(A->ntask, __popc(split));
+                for (int k = 0; k < 3; ++k)
+                    if (split & (1u << k)) A->tasks[base++] = (int32_t)((q << 2) | (k + 1));
+            }
+        }
+        if (A->out_status) A->out_status[q] = st;
+    }
+};
+
+template <bool GFD, bool GRADV>
+__global__ void __launch_bounds__(128) k_bwd_rewalk(BwdArgs A) {
+    RewalkJob<GFD, GRADV> job;
+    job.A = &A;
+    run_persistent(A.ntask + 1, A.nq, job);
 }
 
 // ------------------------------------------------------------------ chord / literal walks
@@ -446,48 +463,63 @@ __global__ void __launch_bounds__(128) k_bwd_chords(BwdArgs A) {
     *reinterpret_cast<float4 *>(A.cols + 4 * q) = col;
 }
 
-__device__ __forceinline__ void walk_to_end(const WalkParams &P, Walker &w) {
-    while (!walker_step<true>(w, P)) {
-    }
-}
+// literal walk of one swept perturbation (task = q << 2 | k): k = 1 walks Exp(p, v + eps e_perp);
+// k = 2, 3 walk p_u = Exp(p, eps e_u) carrying v, then Exp(p_u, v_u) (two phases)
+struct LiteralJob {
+    const BwdArgs *A;
+    Walker w;
+    int64_t q;
+    int k, phase;
+    float L, d0x, d0y, ux, uy;
 
-__global__ void __launch_bounds__(128) k_bwd_literal(BwdArgs A) {
-    const int ntask = *A.ntask;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
-        const int32_t task = A.tasks[t];
-        const int64_t q = task >> 2;
-        const int k = task & 3;
-        const WalkParams &P = A.P;
-        Walker w;
+    __device__ __forceinline__ bool init(int64_t t) {
+        const int32_t task = A->tasks[t];
+        q = task >> 2;
+        k = task & 3;
         Carry<0> cw;
-        walker_init<0>(P, A.in, q, w, cw);
-        const float L = w.Lh, d0x = w.dx, d0y = w.dy;
-        EndAdj E = end_adjoint(A, q, w.foff);
-        Walker we;
-        end_walker(A, q, w, E, we);
-        float eps;
+        walker_init<0>(A->P, A->in, q, w, cw);
+        L = w.Lh; d0x = w.dx; d0y = w.dy;
         if (k == 1) {
-            // Exp(p, v + eps e_perp)
-            eps = A.eps_v;
-            float vx = L * d0x - eps * d0y, vy = L * d0y + eps * d0x;
+            float vx = L * d0x - A->eps_v * d0y, vy = L * d0y + A->eps_v * d0x;
             float Lp = sqrtf(vx * vx + vy * vy);
             w.dx = vx / Lp; w.dy = vy / Lp; w.Lh = Lp; w.Ll = 0.f;
-            walk_to_end(P, w);
+            phase = 1;
         } else {
-            // p_u = Exp(p, eps e_u) carrying v, then Exp(p_u, v_u)
-            eps = A.eps_p;
-            float ux = k == 2 ? 1.f : w.R.x2x * w.R.il2, uy = k == 2 ? 0.f : w.R.x2y * w.R.il2;
-            w.dx = ux; w.dy = uy; w.Lh = eps; w.Ll = 0.f; w.mode = 6;
-            walk_to_end(P, w);
-            float vc = d0x * ux + d0y * uy, vs = ux * d0y - uy * d0x;  // v/L relative to e_u
-            float s_t = (w.st & SG_PARITY_BIT) ? -1.f : 1.f;
-            float nx = vc * w.dx - s_t * vs * w.dy, ny = vc * w.dy + s_t * vs * w.dx;
-            w.dx = nx; w.dy = ny; w.Lh = L; w.Ll = 0.f; w.mode = 6; w.steps = 0;
-            walk_to_end(P, w);
+            ux = k == 2 ? 1.f : w.R.x2x * w.R.il2;
+            uy = k == 2 ? 0.f : w.R.x2y * w.R.il2;
+            w.dx = ux; w.dy = uy; w.Lh = A->eps_p; w.Ll = 0.f; w.mode = 6;
+            phase = 0;
         }
-        A.cols[4 * q + k] = contract(pos_diff(P, w, we), E, eps);
-        if (A.out_status) atomicOr(A.out_status + q, w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_NEAR_VERTEX));
+        return true;
     }
+    __device__ __forceinline__ bool step() {
+        if (!walker_step<true>(w, A->P)) return false;
+        if (phase == 1) return true;
+        // end of p -> p_u: continue with v transported along the short walk
+        float vc = d0x * ux + d0y * uy, vs = ux * d0y - uy * d0x;  // v/L relative to e_u
+        float s_t = (w.st & SG_PARITY_BIT) ? -1.f : 1.f;
+        float nx = vc * w.dx - s_t * vs * w.dy, ny = vc * w.dy + s_t * vs * w.dx;
+        w.dx = nx; w.dy = ny; w.Lh = L; w.Ll = 0.f; w.mode = 6; w.steps = 0;
+        phase = 1;
+        return false;
+    }
+    __device__ __forceinline__ void finish() {
+        Carry<0> cw;
+        Walker w0;
+        walker_init<0>(A->P, A->in, q, w0, cw);
+        EndAdj E = end_adjoint(*A, q, w0.foff);
+        Walker we;
+        end_walker(*A, q, w0, E, we);
+        const float eps = k == 1 ? A->eps_v : A->eps_p;
+        A->cols[4 * q + k] = contract(pos_diff(A->P, w, we), E, eps);
+        if (A->out_status) atomicOr(A->out_status + q, w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_NEAR_VERTEX));
+    }
+};
+
+__global__ void __launch_bounds__(128) k_bwd_literal(BwdArgs A) {
+    LiteralJob job;
+    job.A = &A;
+    run_persistent(A.ntask + 2, (int64_t)*A.ntask, job);
 }
 
 __global__ void __launch_bounds__(256) k_bwd_assemble(BwdArgs A) {
@@ -527,6 +559,17 @@ __global__ void k_gradv_flush(int64_t nV, const float4 *__restrict__ gacc, float
 // ------------------------------------------------------------------ host
 namespace {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// SM-filling grid of 128-thread blocks for a persistent kernel over n tasks
+template <class K>
+unsigned persistent_grid(K kernel, int64_t n) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 128, 0);
+    int64_t need = (n + 127) / 128;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
+}
 struct BwdLayout {
     size_t gacc, cols, tasks, ntask, total;
 };
@@ -605,17 +648,16 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         if (grad_V) {
             BwdArgs B = A;
             B.out_status = nullptr;
-            k_bwd_rewalk<false, true><<<g128, 128, 0, s>>>(B);
+            k_bwd_rewalk<false, true><<<persistent_grid(k_bwd_rewalk<false, true>, nq), 128, 0, s>>>(B);
         }
     } else {
-        if (grad_V) k_bwd_rewalk<true, true><<<g128, 128, 0, s>>>(A);
-        else k_bwd_rewalk<true, false><<<g128, 128, 0, s>>>(A);
+        cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
+        if (pev) cudaEventRecord(pev[0], s);
+        if (grad_V) k_bwd_rewalk<true, true><<<persistent_grid(k_bwd_rewalk<true, true>, nq), 128, 0, s>>>(A);
+        else k_bwd_rewalk<true, false><<<persistent_grid(k_bwd_rewalk<true, false>, nq), 128, 0, s>>>(A);
+        if (pev) cudaEventRecord(pev[1], s);
         k_bwd_chords<<<g128, 128, 0, s>>>(A);
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        unsigned gl = (unsigned)std::max<int64_t>(1, std::min<int64_t>((3 * nq + 127) / 128, (int64_t)sms * 16));
-        k_bwd_literal<<<gl, 128, 0, s>>>(A);
+        k_bwd_literal<<<persistent_grid(k_bwd_literal, 3 * nq), 128, 0, s>>>(A);
         k_bwd_assemble<<<g256, 256, 0, s>>>(A);
     }
     if (grad_V) k_gradv_flush<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, A.gacc, grad_V);

@@ -79,62 +79,25 @@ __global__ void __launch_bounds__(256) k_walk_plain(FwdArgs a) {
     walker_finish<NW>(a, q, w, cw);
 }
 
-// warp-aggregated ticket: the calling lanes get consecutive queue positions
-__device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
-    unsigned mask = __activemask();
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(mask) - 1;
-    int rank = __popc(mask & ((1u << lane) - 1u));
-    int base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(mask));
-    base = __shfl_sync(mask, base, leader);
-    return (int64_t)base + rank;
-}
-
-// Lanes whose walk has ended keep their final state in registers until enough lanes of the
-// warp are idle (SG_REFILL_LANES), then all idle lanes write their outputs, take new tickets
-// and initialise together, so the long init/finish code runs with many lanes active instead
-// of stalling the warp for one lane every few steps.  Once the queue is exhausted, lanes
-// write as soon as they finish and the warp leaves when all its lanes are idle.
-#define SG_REFILL_LANES 8
+template <int NW, bool ESC>
+struct FwdJob {
+    const FwdArgs *a;
+    Walker w;
+    Carry<NW> cw;
+    int64_t q;
+    __device__ __forceinline__ bool init(int64_t t) {
+        q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
+        return walker_init<NW>(a->P, a->in, q, w, cw);
+    }
+    __device__ __forceinline__ bool step() { return walker_step<ESC>(w, a->P); }
+    __device__ __forceinline__ void finish() { walker_finish<NW>(*a, q, w, cw); }
+};
 
 template <int NW, bool ESC>
 __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
-    Walker w;
-    Carry<NW> cw;
-    int64_t q = -1;
-    bool live = false, pending = false, exhausted = false;
-    const unsigned FULL = 0xffffffffu;
-    while (true) {
-        unsigned idle = __ballot_sync(FULL, !live);
-        if (exhausted && idle == FULL) break;
-        if (!exhausted && __popc(idle) >= SG_REFILL_LANES) {
-            bool dry = false;
-            if (!live) {
-                if (pending) {
-                    walker_finish<NW>(a, q, w, cw);
-                    pending = false;
-                }
-                int64_t t = fetch_ticket(a.counter);
-                if (t >= a.nq) {
-                    dry = true;
-                } else {
-                    q = a.perm ? (int64_t)__ldg(a.perm + t) : t;
-                    live = walker_init<NW>(a.P, a.in, q, w, cw);
-                    if (!live) walker_finish<NW>(a, q, w, cw);
-                }
-            }
-            exhausted = __any_sync(FULL, dry);
-        }
-        if (live && walker_step<ESC>(w, a.P)) {
-            live = false;
-            pending = true;
-        }
-        if (exhausted && pending) {
-            walker_finish<NW>(a, q, w, cw);
-            pending = false;
-        }
-    }
+    FwdJob<NW, ESC> job;
+    job.a = &a;
+    run_persistent(a.counter, a.nq, job);
 }
 
 // ------------------------------------------------------------------ start-face counting sort
@@ -312,6 +275,7 @@ void sg_opts_default(sg_opts *o) {
     o->tau_snap = 1e-6f;
     o->workspace = nullptr;
     o->workspace_bytes = 0;
+    o->prof_events = nullptr;
 }
 
 const char *sg_status_string(sg_status s) {
@@ -458,6 +422,8 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
             a.perm = perm;
         }
     }
+    cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
+    if (pev) cudaEventRecord(pev[0], s);
     cudaError_t e;
     switch (n_w) {
         case 0: e = launch_walk<0>(a, r, s); break;
@@ -466,6 +432,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
         case 3: e = launch_walk<3>(a, r, s); break;
         default: e = launch_walk<4>(a, r, s); break;
     }
+    if (pev) cudaEventRecord(pev[1], s);
     if (own_ws) cudaFreeAsync(ws, s);
     if (e != cudaSuccess) {
         std::snprintf(g_err, sizeof g_err, "%s", cudaGetErrorString(e));

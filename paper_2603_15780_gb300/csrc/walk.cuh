@@ -201,6 +201,109 @@ struct NoHook {
     __device__ __forceinline__ void on_vertex(const Walker &, int) {}
 };
 
+// Step from a face entered through local edge k (the hot case): corners rotated so that
+// A -> B is the entry edge and C the apex; the exit edge is B -> C when the apex lies left of
+// the ray (sigma_C > 0), else C -> A.  The crossing maps the direction with the unnormalised
+// edge vectors e (old face) and f (new face) -- both have the edge's length, so the common
+// factor |e||f| disappears in the renormalisation.
+template <bool ESC, class Hook>
+__device__ __forceinline__ bool edge_step(Walker &w, const WalkParams &P, Hook &hook) {
+    const FaceRec &R = w.R;
+    const int k = w.mode;
+    const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
+    const float Ax = sel3(k, 0.f, R.l01, R.x2x), Ay = sel3(k, 0.f, 0.f, R.x2y);
+    const float Bx = sel3(k, R.l01, R.x2x, 0.f), By = sel3(k, 0.f, R.x2y, 0.f);
+    const float Cx = sel3(k, R.x2x, 0.f, R.l01), Cy = sel3(k, R.x2y, 0.f, 0.f);
+    float sA = sigma32(w.dx, w.dy, Ax, Ay, w.px, w.py);
+    float sB = sigma32(w.dx, w.dy, Bx, By, w.px, w.py);
+    float sC = sigma32(w.dx, w.dy, Cx, Cy, w.px, w.py);
+    if (ESC && fabsf(sC) < near) {
+        // FP64 re-evaluation of the classification (exact products of the FP32 state)
+        w.st |= SG_ST_FP64;
+        sA = f32_keep_sign(sigma64(w.dx, w.dy, Ax, Ay, w.px, w.py));
+        sB = f32_keep_sign(sigma64(w.dx, w.dy, Bx, By, w.px, w.py));
+        sC = f32_keep_sign(sigma64(w.dx, w.dy, Cx, Cy, w.px, w.py));
+    }
+    const bool hit = fabsf(sC) <= snap;  // a snapped apex is a hit, not a near miss
+    if (!hit && fabsf(sC) < near) w.st |= SG_ST_NEAR_VERTEX;
+    // sigma in corner order for observers: corner k -> A, k+1 -> B, k+2 -> C
+    hook.on_face(w, sel3(k, sA, sC, sB), sel3(k, sB, sA, sC), sel3(k, sC, sB, sA), k, hit ? prv(k) : -1);
+    const bool right = sC > 0.f;
+    const int j = right ? nxt(k) : prv(k);
+    const float x0 = right ? Bx : Cx, y0 = right ? By : Cy;
+    const float x1 = right ? Cx : Ax, y1 = right ? Cy : Ay;
+    float qx, qy, s;
+    if (hit) {
+        qx = Cx; qy = Cy;
+        s = right ? 1.f : 0.f;
+    } else {
+        const float s0 = right ? sB : sC, s1 = right ? sC : sA;
+        const float den = s0 - s1;
+        s = den != 0.f ? __fdividef(s0, den) : 0.5f;
+        s = fminf(fmaxf(s, 0.f), 1.f);
+        qx = fmaf(s, x1 - x0, x0);
+        qy = fmaf(s, y1 - y0, y0);
+    }
+    const float t = fmaxf(fmaf(qx - w.px, w.dx, (qy - w.py) * w.dy), 0.f);
+    const float L = w.Lh + w.Ll;
+    if (t >= L) {
+        // final truncated in-face segment (reading: stop once the length is used up)
+        w.px = fmaf(L, w.dx, w.px);
+        w.py = fmaf(L, w.dy, w.py);
+        w.Lh = 0.f; w.Ll = 0.f;
+        float d0 = fabsf(w.py);
+        float d1 = fabsf((R.x2x - R.l01) * (w.py) - R.x2y * (w.px - R.l01)) * R.il1;
+        float d2 = fabsf(R.x2x * w.py - R.x2y * w.px) * R.il2;
+        if (fminf(fminf(d0, d1), d2) <= near) w.st |= SG_ST_NEAR_EDGE;
+        return true;
+    }
+    {   // compensated L -= t
+        float a = w.Lh, b = -t;
+        float sum = a + b;
+        float bb = sum - a;
+        float err = (a - (sum - bb)) + (b - bb);
+        w.Lh = sum;
+        w.Ll += err;
+    }
+    if (hit) {
+        hook.on_vertex(w, prv(k));
+        return !vertex_transport(w, prv(k), P);
+    }
+    const int nb = nbr_of(R, j);
+    if (nb < 0) {  // boundary edge: original rule stops (Sec. 4)
+        w.px = qx; w.py = qy;
+        w.st |= SG_ST_BOUNDARY;
+        return true;
+    }
+    const int g = nb >> 3, kp = nb & 3, fl = (nb >> 2) & 1;
+    const float ex = x1 - x0, ey = y1 - y0;
+    const float da = fmaf(w.dx, ex, w.dy * ey);   // |e| (d . e_hat)
+    const float dc = fmaf(w.dx, ey, -w.dy * ex);  // |e| (d . n_out)
+    const FaceRec G = load_rec(P.rec, g);
+    const float gax = sel3(kp, 0.f, G.l01, G.x2x), gay = sel3(kp, 0.f, 0.f, G.x2y);
+    const float gbx = sel3(kp, G.l01, G.x2x, 0.f), gby = sel3(kp, 0.f, G.x2y, 0.f);
+    const float fx = gbx - gax, fy = gby - gay;
+    const float sa_ = fl ? da : -da;
+    float ndx = fmaf(sa_, fx, -dc * fy);
+    float ndy = fmaf(sa_, fy, dc * fx);
+    renorm(ndx, ndy);
+    hook.on_cross(w, j, qx, qy, w.Lh + w.Ll, g, G, kp, fl, ndx, ndy);
+    const float sp = fl ? s : 1.f - s;
+    w.px = fmaf(sp, fx, gax);
+    w.py = fmaf(sp, fy, gay);
+    w.dx = ndx; w.dy = ndy;
+    w.f = g;
+    w.R = G;
+    w.mode = kp;
+    if (fl) w.st ^= SG_PARITY_BIT;
+    w.ncross++;
+    walker_hash(w, g, P.want_hash);
+    return false;
+}
+
+template <bool ESC, class Hook>
+__device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hook &hook);
+
 // One step of Alg. geodesic_step.  Returns true when the walk is finished.
 template <bool ESC, class Hook = NoHook>
 __device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook &&hook = Hook()) {
@@ -209,6 +312,14 @@ __device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook
         return true;
     }
     w.steps++;
+    if (w.mode < 3) return edge_step<ESC>(w, P, hook);
+    return general_step<ESC>(w, P, hook);
+}
+
+// Step from a corner (after a vertex transport) or from a free start point; also handles
+// an entry edge, but the hot path for that case is edge_step.
+template <bool ESC, class Hook>
+__device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hook &hook) {
     const FaceRec &R = w.R;
     const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
     float s0 = sigma32(w.dx, w.dy, 0.f, 0.f, w.px, w.py);
@@ -450,3 +561,61 @@ __device__ bool walker_init(const WalkParams &P, const QueryIn &a, int64_t q, Wa
     return L > 0.f;
 }
 
+
+// ------------------------------------------------------------------ persistent driver
+// warp-aggregated ticket: the calling lanes get consecutive queue positions
+__device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int rank = __popc(mask & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return (int64_t)base + rank;
+}
+
+// Lanes pull task indices t < n from *counter.  A lane whose task has ended keeps its state
+// in registers until SG_REFILL_LANES lanes of the warp are idle; then all idle lanes finish
+// (write results), take new tickets and initialise together, so the long init/finish code
+// runs with many lanes active instead of stalling the warp for one lane every few steps.
+// Once the counter passes n, lanes finish as soon as they are done and the warp leaves when
+// all of its lanes are idle.  Every lane of the warp stays in the loop until then (the
+// ballots use the full mask).  Job: bool init(t) (true: a walk to step), bool step()
+// (true: done), void finish().
+#define SG_REFILL_LANES 8
+
+template <class Job>
+__device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job) {
+    bool live = false, pending = false, exhausted = false;
+    const unsigned FULL = 0xffffffffu;
+    while (true) {
+        unsigned idle = __ballot_sync(FULL, !live);
+        if (exhausted && idle == FULL) break;
+        if (!exhausted && __popc(idle) >= SG_REFILL_LANES) {
+            bool dry = false;
+            if (!live) {
+                if (pending) {
+                    job.finish();
+                    pending = false;
+                }
+                int64_t t = fetch_ticket(counter);
+                if (t >= n) {
+                    dry = true;
+                } else {
+                    live = job.init(t);
+                    if (!live) job.finish();
+                }
+            }
+            exhausted = __any_sync(FULL, dry);
+        }
+        if (live && job.step()) {
+            live = false;
+            pending = true;
+        }
+        if (exhausted && pending) {
+            job.finish();
+            pending = false;
+        }
+    }
+}
