@@ -161,8 +161,7 @@ struct StraddleHook {
     float ua, ub, va, vb;        // e_u / e_v offsets along and across d0 (start frame)
     float tol;
     unsigned split;
-    __device__ __forceinline__ void test(const Walker &w, float sig_loc, int k) {
-        float cx = corner_x(w.R, k), cy = corner_y(w.R, k);
+    __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy) {
         float tau = (Ltot - (w.Lh + w.Ll)) + (cx - w.px) * w.dx + (cy - w.py) * w.dy;
         float sig = (w.st & SG_PARITY_BIT) ? -sig_loc : sig_loc;
         if (tau < -tol || tau > Ltot + tol) return;
@@ -175,6 +174,9 @@ struct StraddleHook {
             float s = tau - (vb != 0.f ? sig / vb : 0.f) * va;
             if (s > -tol && s < Ltot + tol) split |= 4u;
         }
+    }
+    __device__ __forceinline__ void test(const Walker &w, float sig_loc, int k) {
+        test_at(w, sig_loc, corner_x(w.R, k), corner_y(w.R, k));
     }
     __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode) {
         if (mode < 3) {
@@ -206,45 +208,41 @@ struct GradHook {
         if (v == v0) c0 = c0 + g;
         else c1 = c1 + g;
     }
-    __device__ __forceinline__ void on_cross(const Walker &w, int j, float qx, float qy, float Lr, int g,
-                                             const FaceRec &G, int kp, int fl, float ndx, float ndy) {
-        const FaceRec &R = w.R;
-        // old frame: exit edge A = P_j, B = P_{j+1}
-        float Ax = corner_x(R, j), Ay = corner_y(R, j), Bx = corner_x(R, nxt(j)), By = corner_y(R, nxt(j));
-        float il = inv_len(R, j);
-        float ex = (Bx - Ax) * il, ey = (By - Ay) * il, nx = ey, ny = -ex;
-        float yx = fmaf(Lr, w.dx, qx), yy = fmaf(Lr, w.dy, qy);  // end point in the old frame
-        float ax_ = (yx - Ax) * ex + (yy - Ay) * ey;
-        float cc = (yx - Ax) * nx + (yy - Ay) * ny;
-        // new frame: A' = P'_kp, B' = P'_{kp+1}
-        float Apx = corner_x(G, kp), Apy = corner_y(G, kp), Bpx = corner_x(G, nxt(kp)), Bpy = corner_y(G, nxt(kp));
-        float ilp = inv_len(G, kp);
-        float fx = (Bpx - Apx) * ilp, fy = (Bpy - Apy) * ilp, mx = fy, my = -fx;
+    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &) {
+        // old frame: exit edge A -> B; new frame: A' -> B' (unit vectors from rsqrt of |e|^2)
+        const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;
+        const float il = rsqrtf(fmaf(exr, exr, eyr * eyr));
+        const float ex = exr * il, ey = eyr * il, nx = ey, ny = -ex;
+        const float yx = fmaf(c.Lr, w.dx, c.qx), yy = fmaf(c.Lr, w.dy, c.qy);  // end point, old frame
+        const float ax_ = (yx - c.x0) * ex + (yy - c.y0) * ey;
+        const float cc = (yx - c.x0) * nx + (yy - c.y0) * ny;
+        const float ilp = rsqrtf(fmaf(c.fx, c.fx, c.fy * c.fy));
+        const float fx = c.fx * ilp, fy = c.fy * ilp, mx = fy, my = -fx;
         // upstream gradient in the new frame
-        uint32_t par = (w.st & SG_PARITY_BIT) ^ (fl ? SG_PARITY_BIT : 0u);
-        float sb = par ? -bs : bs;
-        float gx = a * ndx - sb * ndy, gy = a * ndy + sb * ndx;
-        float sf = fl ? 1.f : -1.f;
-        float ge = gx * fx + gy * fy, gn = gx * mx + gy * my;
-        float K1 = sf * ge * cc + gn * ax_;
-        float K2 = sf * ax_ * gn + cc * ge;
+        const uint32_t par = (w.st & SG_PARITY_BIT) ^ (c.fl ? SG_PARITY_BIT : 0u);
+        const float sb = par ? -bs : bs;
+        const float gx = a * c.ndx - sb * c.ndy, gy = a * c.ndy + sb * c.ndx;
+        const float sf = c.fl ? 1.f : -1.f;
+        const float ge = gx * fx + gy * fy, gn = gx * mx + gy * my;
+        const float K1 = sf * ge * cc + gn * ax_;
+        const float K2 = sf * ax_ * gn + cc * ge;
         // dG/dB, dG/dA in the old frame; dG/dB', dG/dA' in the new frame
-        float dBx = nx * K1 * il, dBy = ny * K1 * il;
-        float dAx = -sf * ge * ex + gn * nx - dBx, dAy = -sf * ge * ey + gn * ny - dBy;
-        float dBpx = mx * K2 * ilp + (fl ? 0.f : gx), dBpy = my * K2 * ilp + (fl ? 0.f : gy);
-        float dApx = -mx * K2 * ilp + (fl ? gx : 0.f), dApy = -my * K2 * ilp + (fl ? gy : 0.f);
-        int4 fvg = __ldg(P->fv + g);
-        Fr2 Fg = load_frm(*P, g);
-        int vA = sel3(j, fvc.x, fvc.y, fvc.z), vB = sel3(nxt(j), fvc.x, fvc.y, fvc.z);
-        int vAp = sel3(kp, fvg.x, fvg.y, fvg.z);
+        const float dBx = nx * K1 * il, dBy = ny * K1 * il;
+        const float dAx = -sf * ge * ex + gn * nx - dBx, dAy = -sf * ge * ey + gn * ny - dBy;
+        const float dBpx = mx * K2 * ilp + (c.fl ? 0.f : gx), dBpy = my * K2 * ilp + (c.fl ? 0.f : gy);
+        const float dApx = -mx * K2 * ilp + (c.fl ? gx : 0.f), dApy = -my * K2 * ilp + (c.fl ? gy : 0.f);
+        const int4 fvg = __ldg(P->fv + c.g);
+        const Fr2 Fg = load_frm(*P, c.g);
+        const int vA = sel3(c.j, fvc.x, fvc.y, fvc.z), vB = sel3(nxt(c.j), fvc.x, fvc.y, fvc.z);
+        const int vAp = sel3(c.kp, fvg.x, fvg.y, fvg.z);
         F3 gA = lift(Fc, dAx, dAy), gB = lift(Fc, dBx, dBy);
-        F3 gAp = lift(Fg, dApx, dApy), gBp = lift(Fg, dBpx, dBpy);
+        const F3 gAp = lift(Fg, dApx, dApy), gBp = lift(Fg, dBpx, dBpy);
         if (vA == vAp) { gA = gA + gAp; gB = gB + gBp; }
         else { gA = gA + gBp; gB = gB + gAp; }
         // keep vA and vB in the cache, evicting the slot neither of them uses
-        bool inA = (vA == v0) || (vA == v1), inB = (vB == v0) || (vB == v1);
+        const bool inA = (vA == v0) || (vA == v1), inB = (vB == v0) || (vB == v1);
         if (!inA || !inB) {
-            bool keep0 = (v0 == vA) || (v0 == vB), keep1 = (v1 == vA) || (v1 == vB);
+            const bool keep0 = (v0 == vA) || (v0 == vB), keep1 = (v1 == vA) || (v1 == vB);
             if (!keep0) { flush(v0, c0); v0 = -1; }
             if (!keep1) { flush(v1, c1); v1 = -1; }
             if (!inA) { if (v0 < 0) { v0 = vA; c0 = f3(0.f, 0.f, 0.f); } else { v1 = vA; c1 = f3(0.f, 0.f, 0.f); } }
@@ -265,9 +263,11 @@ struct RewalkHook {
     __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode, int) {
         if (GFD) S.on_face(w, s0, s1, s2, mode);
     }
-    __device__ __forceinline__ void on_cross(const Walker &w, int j, float qx, float qy, float Lr, int g,
-                                             const FaceRec &R, int kp, int fl, float ndx, float ndy) {
-        if (GRADV && gradv) G.on_cross(w, j, qx, qy, Lr, g, R, kp, fl, ndx, ndy);
+    __device__ __forceinline__ void on_apex(const Walker &w, float sC, float cx, float cy) {
+        if (GFD) S.test_at(w, sC, cx, cy);
+    }
+    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &R) {
+        if (GRADV && gradv) G.on_cross(w, c, R);
     }
     __device__ __forceinline__ void on_vertex(const Walker &, int) {}
 };
@@ -379,8 +379,10 @@ struct ChordHook {
     bool moved;
     float qx, qy;
     __device__ __forceinline__ void on_face(const Walker &, float, float, float, int, int) {}
-    __device__ __forceinline__ void on_cross(const Walker &, int, float x, float y, float, int, const FaceRec &, int,
-                                             int, float, float) { moved = true; qx = x; qy = y; }
+    __device__ __forceinline__ void on_apex(const Walker &, float, float, float) {}
+    __device__ __forceinline__ void on_cross(const Walker &, const Cross &c, const FaceRec &) {
+        moved = true; qx = c.qx; qy = c.qy;
+    }
     __device__ __forceinline__ void on_vertex(const Walker &w, int hit) {
         moved = true; qx = corner_x(w.R, hit); qy = corner_y(w.R, hit);
     }

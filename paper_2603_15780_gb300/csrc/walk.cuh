@@ -187,16 +187,25 @@ __device__ __forceinline__ bool vertex_transport(Walker &w, int c, const WalkPar
     return false;
 }
 
+// An edge crossing as seen by observers: exit edge j of the old face with endpoints
+// (x0,y0) -> (x1,y1) and crossing point q in the old frame, the remaining length after the
+// crossing, the new face g entered through its local edge kp starting at (gax,gay) with edge
+// vector (fx,fy) in the new frame, the flip bit and the new direction.
+struct Cross {
+    int j;
+    float x0, y0, x1, y1, qx, qy, Lr;
+    int g, kp, fl;
+    float gax, gay, fx, fy, ndx, ndy;
+};
+
 // Observer of a walk (the backward pass hooks into the same step code as the forward).
 struct NoHook {
-    // after the exit classification of a face: sigma of the three corners (FP64-refined
-    // when escalated), the mode the face was entered in and the snapped corner (or -1)
+    // general step: sigma of the three corners after classification, entry mode, snapped corner
     __device__ __forceinline__ void on_face(const Walker &, float, float, float, int, int) {}
-    // at an edge crossing (walker still in the old face, length already reduced): exit edge
-    // j, crossing point q (old frame), remaining length, the new face/record, its edge kp,
-    // flip, and the new direction
-    __device__ __forceinline__ void on_cross(const Walker &, int, float, float, float, int, const FaceRec &, int,
-                                             int, float, float) {}
+    // edge-entry step: sigma of the apex and its position
+    __device__ __forceinline__ void on_apex(const Walker &, float, float, float) {}
+    // at an edge crossing (walker still in the old face, length already reduced)
+    __device__ __forceinline__ void on_cross(const Walker &, const Cross &, const FaceRec &) {}
     // before a vertex transport at corner `hit` of the current face
     __device__ __forceinline__ void on_vertex(const Walker &, int) {}
 };
@@ -226,8 +235,7 @@ __device__ __forceinline__ bool edge_step(Walker &w, const WalkParams &P, Hook &
     }
     const bool hit = fabsf(sC) <= snap;  // a snapped apex is a hit, not a near miss
     if (!hit && fabsf(sC) < near) w.st |= SG_ST_NEAR_VERTEX;
-    // sigma in corner order for observers: corner k -> A, k+1 -> B, k+2 -> C
-    hook.on_face(w, sel3(k, sA, sC, sB), sel3(k, sB, sA, sC), sel3(k, sC, sB, sA), k, hit ? prv(k) : -1);
+    hook.on_apex(w, sC, Cx, Cy);
     const bool right = sC > 0.f;
     const int j = right ? nxt(k) : prv(k);
     const float x0 = right ? Bx : Cx, y0 = right ? By : Cy;
@@ -287,7 +295,7 @@ __device__ __forceinline__ bool edge_step(Walker &w, const WalkParams &P, Hook &
     float ndx = fmaf(sa_, fx, -dc * fy);
     float ndy = fmaf(sa_, fy, dc * fx);
     renorm(ndx, ndy);
-    hook.on_cross(w, j, qx, qy, w.Lh + w.Ll, g, G, kp, fl, ndx, ndy);
+    hook.on_cross(w, Cross{j, x0, y0, x1, y1, qx, qy, w.Lh + w.Ll, g, kp, fl, gax, gay, fx, fy, ndx, ndy}, G);
     const float sp = fl ? s : 1.f - s;
     w.px = fmaf(sp, fx, gax);
     w.py = fmaf(sp, fy, gay);
@@ -431,7 +439,8 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
     float ndx = fmaf(sa_, fx, -dc * fy);
     float ndy = fmaf(sa_, fy, dc * fx);
     renorm(ndx, ndy);
-    hook.on_cross(w, j, qx, qy, w.Lh + w.Ll, g, G, kp, fl, ndx, ndy);
+    hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, gax, gay, gbx - gax, gby - gay, ndx, ndy},
+                  G);
     float sp = fl ? s : 1.f - s;
     w.px = fmaf(sp, gbx - gax, gax);
     w.py = fmaf(sp, gby - gay, gay);
