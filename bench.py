@@ -32,6 +32,22 @@ L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 RECORD_BYTES = 32
 
 
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
+    kernel's sources changed since that capture (profiles/ncu_traffic.json)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    files = {"k_bwd_rewalk": ["walk.cuh", "backward.cu"], "k_walk_persistent": ["walk.cuh", "exp_map.cu"]}[kernel]
+    csrc = os.path.join(ROOT, "paper_2603_15780_gb300", "csrc")
+    sha = hashlib.sha1(b"".join(open(os.path.join(csrc, f), "rb").read() for f in files)).hexdigest()
+    return rec["dram_bytes_per_launch"] if sha == rec["source_sha1"] else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -413,7 +429,7 @@ def main():
     dom = max(kern, key=lambda k: kern[k][1])
     achieved = kern[dom][0] / (kern[dom][1] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(dom),
                 "algorithmic_bytes_per_launch": int(kern[dom][0]), "launch_ms": kern[dom][1]}
     kernels = {k: {"ms": t, "algorithmic_GBps": b / (t * 1e-3) / 1e9, "frac_of_hbm": b / (t * 1e-3) / 1e9 / peak}
                for k, (b, t) in kern.items()}
