@@ -106,6 +106,27 @@ def load_workload(scale=1.0):
     return wl, np.ascontiguousarray(X, np.float32), F
 
 
+def rank_queries(wl, X, F, rank: int):
+    """Weak scaling: rank 0 takes the workload's own queries; rank r > 0 an independent batch
+    of the same size and distribution from its own PCG64 stream (seed 1000 + index, r)."""
+    if rank == 0:
+        return wl.queries
+    import meshgen
+    rng = np.random.Generator(np.random.PCG64([1000 + WORKLOAD_INDEX, rank]))
+    return meshgen.sample_queries(X.astype(np.float64), F, len(wl.queries), rng, 0.1, 1.0, 0)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (all-reduce MAX); identity for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- oracle arm
 def oracle_sample(n_sample: int, threads: int):
     """Time the FP64 oracle (forward + EP + GFD, as it stands) on the first n_sample queries."""
@@ -294,7 +315,7 @@ def main():
     dev = torch.device("cuda", local)
 
     wl, X32, F = load_workload()
-    q = wl.queries
+    q = rank_queries(wl, X32, F, rank)
     nq = len(q)
     mesh = sg.Mesh(X32, F)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32), device=dev)
@@ -368,11 +389,8 @@ def main():
         for kk, pair in kev.items():
             ktimes[kk].append(pair[0].elapsed_time(pair[1]))
     clocks = clk.stop()
-    total_ms = float(times.sum())
+    total_ms = max_over_ranks(float(times.sum()), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_step = total_ms / args.steps
     value = world * nq / (ms_step * 1e-3)

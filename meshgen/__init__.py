@@ -286,6 +286,51 @@ def cone_fan(n: int, theta: float, slant: float = 1.0, ring: bool = True):
     return X, F
 
 
+def mobius(nu: int, nv: int, R: float = 1.0, w: float = 0.4):
+    """Moebius strip: centre circle of radius R, half-width w, nu x nv grid with a half twist;
+    the seam joins column nu-1 to column 0 with the width coordinate reversed, so the faces
+    across it are oppositely wound (a non-orientable surface with one boundary loop)."""
+    X = []
+    for i in range(nu):
+        u = 2 * np.pi * i / nu
+        for j in range(nv):
+            t = -w + 2 * w * j / (nv - 1)
+            X.append([(R + t * np.cos(u / 2)) * np.cos(u), (R + t * np.cos(u / 2)) * np.sin(u),
+                      t * np.sin(u / 2)])
+    F = []
+    for i in range(nu):
+        for j in range(nv - 1):
+            a, b = i * nv + j, i * nv + j + 1
+            if i + 1 < nu:
+                c, d = (i + 1) * nv + j + 1, (i + 1) * nv + j
+            else:
+                c, d = (nv - 1 - (j + 1)), (nv - 1 - j)
+            F += [(a, d, c), (a, c, b)]
+    return np.array(X, float), np.array(F, np.int32)
+
+
+def klein_bottle(nu: int, nv: int, R: float = 2.0):
+    """Figure-8 Klein bottle immersion on an nu x nv grid: (u + 2pi, v) is identified with
+    (u, -v), so the closing column is glued with v reversed (closed, non-orientable)."""
+    X = []
+    for i in range(nu):
+        u = 2 * np.pi * i / nu
+        for j in range(nv):
+            v = 2 * np.pi * j / nv
+            r = R + np.cos(u / 2) * np.sin(v) - np.sin(u / 2) * np.sin(2 * v)
+            X.append([r * np.cos(u), r * np.sin(u), np.sin(u / 2) * np.sin(v) + np.cos(u / 2) * np.sin(2 * v)])
+    F = []
+    for i in range(nu):
+        for j in range(nv):
+            a, b = i * nv + j, i * nv + (j + 1) % nv
+            if i + 1 < nu:
+                c, d = (i + 1) * nv + (j + 1) % nv, (i + 1) * nv + j
+            else:
+                c, d = (nv - (j + 1)) % nv, (nv - j) % nv
+            F += [(a, d, c), (a, c, b)]
+    return np.array(X, float), np.array(F, np.int32)
+
+
 # --------------------------------------------------------------------------- queries
 def face_areas(X, F):
     e1 = X[F[:, 1]] - X[F[:, 0]]

@@ -504,3 +504,33 @@ def test_gfd_tracks_sphere_jacobian():
         cs_ep.append(a @ b2 / np.linalg.norm(a) / np.linalg.norm(b2))
     assert np.median(cs_gfd) > 0.97, np.median(cs_gfd)
     assert np.median(cs_ep) > 0.97, np.median(cs_ep)
+
+
+# --------------------------------------------------------------------------- non-orientable
+def test_non_orientable_meshes_gauss_bonnet_and_transport():
+    """App. 'Main differences with SotA implementation': only triangle adjacency is stored, so
+    non-orientable meshes (Moebius strip, Klein bottle) work.  Gauss-Bonnet gives
+    sum(2pi - theta) = 2 pi chi = 0 on the Klein bottle; transport keeps |w| and the unsigned
+    angle between w and the direction (the sign has no global meaning on such surfaces)."""
+    X, F = meshgen.klein_bottle(64, 32)
+    m = oracle.Mesh(X, F)
+    th, b = m.theta()
+    assert not b.any()
+    assert abs(np.sum(2 * np.pi - th)) < 1e-9
+    rng = np.random.default_rng(41)
+    q = meshgen.sample_queries(X, F, 800, rng, 1.0, 8.0, 2)
+    out = oracle.exp_map(m, q.face, q.bary, q.v, q.w)
+    ok = (out["status"] & (oracle.NEAR_VERTEX | oracle.BOUNDARY)) == 0
+    assert out["ncross"][ok].mean() > 20
+    d0 = q.v / np.linalg.norm(q.v, axis=1, keepdims=True)
+    for k in range(2):
+        assert np.abs(np.linalg.norm(out["w"][:, k], axis=1) - 1.0)[ok].max() < 1e-12
+        c0 = np.einsum("ij,ij->i", d0, q.w[:, k])
+        c1 = np.einsum("ij,ij->i", out["dir"], out["w"][:, k])
+        assert np.abs(c0 - c1)[ok].max() < 1e-10
+    # reversibility also holds across orientation flips
+    L = np.linalg.norm(q.v, axis=1)
+    bk = oracle.exp_map(m, out["face"], out["bary"], -out["dir"] * L[:, None])
+    ok &= (bk["status"] & (oracle.NEAR_VERTEX | oracle.NEAR_EDGE)) == 0
+    p0 = start_points(X, F, q.face, q.bary)
+    assert np.abs(bk["pos"] - p0)[ok].max() < 1e-9
