@@ -193,52 +193,50 @@ struct StraddleHook {
 };
 
 // Adjoint of the crossing maps, accumulated into the vertex-gradient scratch.
+// For a crossing with end point y (old frame, a = (y-A).e, c = (y-A).n), upstream gradient
+// gbar' in the new frame (ge = gbar'.e', gn = gbar'.m') and sf = +1 for a flipped adjacency,
+// -1 otherwise, the 2-D corner gradients lifted to 3-D combine per shared vertex into
+//   g_B = (K1 N_old + sf K2 N_new) / l,   g_A = (G_new - G_old) - g_B,
+//   K1 = sf ge c + gn a,  K2 = sf a gn + c ge,
+// where N_old, N_new are the 3-D in-plane unit normals of the edge pointing out of each face
+// and G_old, G_new the adjoint vector lifted into the old and the new face (it is carried
+// from one crossing to the next).  B is the exit edge's end corner in the old face.
 struct GradHook {
     float4 *gacc;
     const WalkParams *P;
     float a, bs;        // gbar_i = a d_i + bs * s_i * perp(d_i)
     int4 fvc;           // vertex ids of the current face
     Fr2 Fc;             // 3-D axes of the current face
+    F3 Gc;              // the adjoint lifted into the current face
     int v0, v1;         // two-slot register cache of per-vertex sums
     F3 c0, c1;
     __device__ __forceinline__ void flush(int v, F3 c) {
         if (v >= 0) atomic_add3(gacc, v, c);
     }
-    __device__ __forceinline__ void put(int v, F3 g) {
-        if (v == v0) c0 = c0 + g;
-        else c1 = c1 + g;
-    }
     __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &) {
-        // old frame: exit edge A -> B; new frame: A' -> B' (unit vectors from rsqrt of |e|^2)
         const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;
         const float il = rsqrtf(fmaf(exr, exr, eyr * eyr));
-        const float ex = exr * il, ey = eyr * il, nx = ey, ny = -ex;
-        const float yx = fmaf(c.Lr, w.dx, c.qx), yy = fmaf(c.Lr, w.dy, c.qy);  // end point, old frame
-        const float ax_ = (yx - c.x0) * ex + (yy - c.y0) * ey;
-        const float cc = (yx - c.x0) * nx + (yy - c.y0) * ny;
+        const float ex = exr * il, ey = eyr * il;
+        const float yx = fmaf(c.Lr, w.dx, c.qx) - c.x0, yy = fmaf(c.Lr, w.dy, c.qy) - c.y0;  // y - A
+        const float ax_ = yx * ex + yy * ey;
+        const float cc = yx * ey - yy * ex;
         const float ilp = rsqrtf(fmaf(c.fx, c.fx, c.fy * c.fy));
-        const float fx = c.fx * ilp, fy = c.fy * ilp, mx = fy, my = -fx;
+        const float fx = c.fx * ilp, fy = c.fy * ilp;
         // upstream gradient in the new frame
         const uint32_t par = (w.st & SG_PARITY_BIT) ^ (c.fl ? SG_PARITY_BIT : 0u);
         const float sb = par ? -bs : bs;
         const float gx = a * c.ndx - sb * c.ndy, gy = a * c.ndy + sb * c.ndx;
         const float sf = c.fl ? 1.f : -1.f;
-        const float ge = gx * fx + gy * fy, gn = gx * mx + gy * my;
+        const float ge = gx * fx + gy * fy, gn = gx * fy - gy * fx;
         const float K1 = sf * ge * cc + gn * ax_;
         const float K2 = sf * ax_ * gn + cc * ge;
-        // dG/dB, dG/dA in the old frame; dG/dB', dG/dA' in the new frame
-        const float dBx = nx * K1 * il, dBy = ny * K1 * il;
-        const float dAx = -sf * ge * ex + gn * nx - dBx, dAy = -sf * ge * ey + gn * ny - dBy;
-        const float dBpx = mx * K2 * ilp + (c.fl ? 0.f : gx), dBpy = my * K2 * ilp + (c.fl ? 0.f : gy);
-        const float dApx = -mx * K2 * ilp + (c.fl ? gx : 0.f), dApy = -my * K2 * ilp + (c.fl ? gy : 0.f);
         const int4 fvg = __ldg(P->fv + c.g);
         const Fr2 Fg = load_frm(*P, c.g);
+        const F3 Nold = lift(Fc, ey, -ex), Nnew = lift(Fg, fy, -fx);
+        const F3 Gn = lift(Fg, gx, gy);
+        const F3 gB = il * (K1 * Nold + (sf * K2) * Nnew);
+        const F3 gA = (Gn - Gc) - gB;
         const int vA = sel3(c.j, fvc.x, fvc.y, fvc.z), vB = sel3(nxt(c.j), fvc.x, fvc.y, fvc.z);
-        const int vAp = sel3(c.kp, fvg.x, fvg.y, fvg.z);
-        F3 gA = lift(Fc, dAx, dAy), gB = lift(Fc, dBx, dBy);
-        const F3 gAp = lift(Fg, dApx, dApy), gBp = lift(Fg, dBpx, dBpy);
-        if (vA == vAp) { gA = gA + gAp; gB = gB + gBp; }
-        else { gA = gA + gBp; gB = gB + gAp; }
         // keep vA and vB in the cache, evicting the slot neither of them uses
         const bool inA = (vA == v0) || (vA == v1), inB = (vB == v0) || (vB == v1);
         if (!inA || !inB) {
@@ -248,10 +246,12 @@ struct GradHook {
             if (!inA) { if (v0 < 0) { v0 = vA; c0 = f3(0.f, 0.f, 0.f); } else { v1 = vA; c1 = f3(0.f, 0.f, 0.f); } }
             if (!inB) { if (v0 < 0) { v0 = vB; c0 = f3(0.f, 0.f, 0.f); } else { v1 = vB; c1 = f3(0.f, 0.f, 0.f); } }
         }
-        put(vA, gA);
-        put(vB, gB);
+        const bool a0 = vA == v0;
+        c0 = c0 + (a0 ? gA : gB);
+        c1 = c1 + (a0 ? gB : gA);
         fvc = fvg;
         Fc = Fg;
+        Gc = Gn;
     }
 };
 
@@ -321,6 +321,7 @@ struct RewalkJob {
             const float g0x = E.a * d0x - E.sm * E.b * d0y, g0y = E.a * d0y + E.sm * E.b * d0x;
             float b2 = w.py / w.R.x2y, b1 = (w.px - b2 * w.R.x2x) / w.R.l01, b0 = 1.f - b1 - b2;
             F3 G0 = lift(H.G.Fc, g0x, g0y);
+            H.G.Gc = G0;
             F3 n0 = nrm_of(H.G.Fc);
             float vn = dot3(ld3(A->in.v, q), n0);
             F3 x0 = vpos(P, H.G.fvc.x), u = vpos(P, H.G.fvc.y) - x0, ww = vpos(P, H.G.fvc.z) - x0;

@@ -618,6 +618,11 @@ __device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job 
             }
             exhausted = __any_sync(FULL, dry);
         }
+        // two steps per refill check halve the loop overhead
+        if (live && job.step()) {
+            live = false;
+            pending = true;
+        }
         if (live && job.step()) {
             live = false;
             pending = true;
