@@ -161,8 +161,8 @@ struct StraddleHook {
     float ua, ub, va, vb;        // e_u / e_v offsets along and across d0 (start frame)
     float tol;
     unsigned split;
-    __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy) {
-        float tau = (Ltot - (w.Lh + w.Ll)) + (cx - w.px) * w.dx + (cy - w.py) * w.dy;
+    __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy, float px, float py) {
+        float tau = (Ltot - (w.Lh + w.Ll)) + (cx - px) * w.dx + (cy - py) * w.dy;
         float sig = (w.st & SG_PARITY_BIT) ? -sig_loc : sig_loc;
         if (tau < -tol || tau > Ltot + tol) return;
         if (sig > -tol && sig * cphi - tau * sphi < tol) split |= 1u;
@@ -176,7 +176,7 @@ struct StraddleHook {
         }
     }
     __device__ __forceinline__ void test(const Walker &w, float sig_loc, int k) {
-        test_at(w, sig_loc, corner_x(w.R, k), corner_y(w.R, k));
+        test_at(w, sig_loc, corner_x(w.R, k), corner_y(w.R, k), w.px, w.py);
     }
     __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode) {
         if (mode < 3) {
@@ -232,8 +232,10 @@ struct GradHook {
         const float K2 = sf * ax_ * gn + cc * ge;
         const int4 fvg = __ldg(P->fv + c.g);
         const Fr2 Fg = load_frm(*P, c.g);
-        const F3 Nold = lift(Fc, ey, -ex), Nnew = lift(Fg, fy, -fx);
-        const F3 Gn = lift(Fg, gx, gy);
+        // lift through each frame's rotation to its face frame
+        const F3 Nold = lift(Fc, c.ca0 * ey + c.sa0 * ex, c.sa0 * ey - c.ca0 * ex);
+        const F3 Nnew = lift(Fg, c.ca1 * fy + c.sa1 * fx, c.sa1 * fy - c.ca1 * fx);
+        const F3 Gn = lift(Fg, c.ca1 * gx - c.sa1 * gy, c.sa1 * gx + c.ca1 * gy);
         const F3 gB = il * (K1 * Nold + (sf * K2) * Nnew);
         const F3 gA = (Gn - Gc) - gB;
         const int vA = sel3(c.j, fvc.x, fvc.y, fvc.z), vB = sel3(nxt(c.j), fvc.x, fvc.y, fvc.z);
@@ -263,8 +265,8 @@ struct RewalkHook {
     __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode, int) {
         if (GFD) S.on_face(w, s0, s1, s2, mode);
     }
-    __device__ __forceinline__ void on_apex(const Walker &w, float sC, float cx, float cy) {
-        if (GFD) S.test_at(w, sC, cx, cy);
+    __device__ __forceinline__ void on_apex(const Walker &w, float sC, float cx, float cy, float px, float py) {
+        if (GFD) S.test_at(w, sC, cx, cy, px, py);
     }
     __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &R) {
         if (GRADV && gradv) G.on_cross(w, c, R);
@@ -368,45 +370,13 @@ struct RewalkJob {
 };
 
 template <bool GFD, bool GRADV>
-__global__ void __launch_bounds__(128) k_bwd_rewalk(BwdArgs A) {
+__global__ void __launch_bounds__(128, 5) k_bwd_rewalk(BwdArgs A) {
     RewalkJob<GFD, GRADV> job;
     job.A = &A;
     run_persistent(A.ntask + 1, A.nq, job);
 }
 
 // ------------------------------------------------------------------ chord / literal walks
-// records the crossing point (or the vertex reached) of one step
-struct ChordHook {
-    bool moved;
-    float qx, qy;
-    __device__ __forceinline__ void on_face(const Walker &, float, float, float, int, int) {}
-    __device__ __forceinline__ void on_apex(const Walker &, float, float, float) {}
-    __device__ __forceinline__ void on_cross(const Walker &, const Cross &c, const FaceRec &) {
-        moved = true; qx = c.qx; qy = c.qy;
-    }
-    __device__ __forceinline__ void on_vertex(const Walker &w, int hit) {
-        moved = true; qx = corner_x(w.R, hit); qy = corner_y(w.R, hit);
-    }
-};
-
-// 3-D chord of a walk of length `len` from the walker's position along unit 2-D direction u,
-// summed segment by segment in face-local coordinates
-__device__ F3 short_chord(const WalkParams &P, Walker w, float ux, float uy, float len) {
-    w.dx = ux; w.dy = uy; w.Lh = len; w.Ll = 0.f; w.mode = 6; w.steps = 0;
-    F3 c = f3(0.f, 0.f, 0.f);
-    for (int it = 0; it < 64; ++it) {
-        const int f0 = w.f;
-        const float x0 = w.px, y0 = w.py;
-        ChordHook h;
-        h.moved = false;
-        bool done = walker_step<true>(w, P, h);
-        Fr2 F = load_frm(P, f0);
-        c = c + (h.moved ? lift(F, h.qx - x0, h.qy - y0) : lift(F, w.px - x0, w.py - y0));
-        if (done) break;
-    }
-    return c;
-}
-
 // the forward end state (face, 2-D point, transported direction, parity) of query q
 __device__ __forceinline__ void end_walker(const BwdArgs &A, int64_t q, const Walker &start, const EndAdj &E,
                                            Walker &w) {
@@ -427,6 +397,16 @@ __device__ F3 pos_diff(const WalkParams &P, const Walker &a, const Walker &b) {
     int4 ta = __ldg(P.fv + a.f), tb = __ldg(P.fv + b.f);
     Fr2 Fa = load_frm(P, a.f), Fb = load_frm(P, b.f);
     return (vpos(P, ta.x) - vpos(P, tb.x)) + lift(Fa, a.px, a.py) - lift(Fb, b.px, b.py);
+}
+
+// 3-D chord of a walk of length `len` from the walker's position along unit 2-D direction u
+// (face frame), as the cancellation-free difference of the end and start positions
+__device__ F3 short_chord(const WalkParams &P, const Walker &w0, float ux, float uy, float len) {
+    Walker w = w0;
+    w.dx = ux; w.dy = uy; w.Lh = len; w.Ll = 0.f; w.mode = 6; w.steps = 0;
+    while (!walker_step<true>(w, P)) {
+    }
+    return pos_diff(P, w, w0);
 }
 
 __device__ __forceinline__ float contract(F3 c, const EndAdj &E, float eps) {
@@ -619,7 +599,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     if (r.tau_snap <= 0.f) r.tau_snap = 1e-6f;
     cudaStream_t s = (cudaStream_t)stream;
     BwdArgs A{};
-    A.P.rec = m->d_rec; A.P.fv = m->d_fv; A.P.frm = m->d_frm; A.P.V = m->d_V; A.P.face_off = m->d_face_off;
+    A.P.rec = m->d_rec; A.P.fv = m->d_fv; A.P.frm = m->d_frm; A.P.half = m->d_half; A.P.V = m->d_V; A.P.face_off = m->d_face_off;
     A.P.lref = m->d_lref;
     A.P.max_steps = r.max_steps; A.P.tau_near = r.tau_near; A.P.tau_snap = r.tau_snap; A.P.want_hash = 0;
     A.in.n_mesh = m->n_mesh; A.in.mesh_id = mesh_id; A.in.face = face; A.in.bary = bary; A.in.v = v;

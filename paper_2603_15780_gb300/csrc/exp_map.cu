@@ -317,6 +317,7 @@ sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int
     bool ok = up((void **)&m->d_rec, H.rec.data(), sizeof(int4) * H.rec.size()) &&
               up((void **)&m->d_fv, H.fv.data(), sizeof(int4) * H.fv.size()) &&
               up((void **)&m->d_frm, H.frm.data(), sizeof(float4) * H.frm.size()) &&
+              up((void **)&m->d_half, H.half.data(), sizeof(int4) * H.half.size()) &&
               up((void **)&m->d_V, H.V.data(), sizeof(float4) * H.V.size()) &&
               up((void **)&m->d_face_off, H.face_off.data(), sizeof(int32_t) * H.face_off.size()) &&
               up((void **)&m->d_lref, H.lref.data(), sizeof(float) * H.lref.size());
@@ -340,6 +341,7 @@ sg_status sg_mesh_destroy(sg_mesh *m) {
     cudaFree(m->d_rec);
     cudaFree(m->d_fv);
     cudaFree(m->d_frm);
+    cudaFree(m->d_half);
     cudaFree(m->d_V);
     cudaFree(m->d_face_off);
     cudaFree(m->d_lref);
@@ -352,7 +354,7 @@ sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info) {
     info->n_vertices = m->nV;
     info->n_faces = m->nF;
     info->n_mesh = m->n_mesh;
-    info->record_bytes = 32;
+    info->record_bytes = 32 + 3 * 32;
     info->device_bytes = m->device_bytes;
     info->l_ref_mean = m->lref.empty() ? 0.0 : m->lref[0];
     return SG_OK;
@@ -379,7 +381,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a{};
-    a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.frm = m->d_frm; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
+    a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.frm = m->d_frm; a.P.half = m->d_half; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
     a.P.max_steps = r.max_steps; a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
     a.P.want_hash = out_hash != nullptr;
     a.nq = nq; a.in.n_mesh = m->n_mesh; a.nF_total = (int32_t)m->nF;

@@ -52,6 +52,7 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
     out->rec.assign(2 * nF, int4{0, 0, 0, 0});
     out->fv.assign(nF, int4{0, 0, 0, 0});
     out->frm.assign(2 * nF, float4{0, 0, 0, 0});
+    out->half.assign(6 * nF, int4{0, 0, 0, 0});
     out->V.assign(nV, float4{0, 0, 0, 0});
     out->face_off.assign(n_mesh + 1, 0);
     out->lref.assign(n_mesh, 0.f);
@@ -143,6 +144,35 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
             r0.x = nbr[3 * f];
             r0.y = nbr[3 * f + 1];
             r0.z = nbr[3 * f + 2];
+        }
+        // ---- half-edge records: each face seen from each of its edges
+        for (int64_t f = 0; f < nf; ++f) {
+            const int32_t *t = Fm + 3 * f;
+            D3 x0 = X(t[0]), x1 = X(t[1]), x2 = X(t[2]);
+            D3 e1 = sub(x1, x0), e2 = sub(x2, x0);
+            double l01 = norm(e1);
+            D3 u = scale(e1, 1.0 / l01);
+            D3 nh = scale(cross(e1, e2), 1.0 / norm(cross(e1, e2)));
+            D3 w = cross(nh, u);
+            double Px[3] = {0.0, l01, dot(e2, u)}, Py[3] = {0.0, 0.0, dot(e2, w)};
+            for (int k = 0; k < 3; ++k) {
+                int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                double ex = Px[k1] - Px[k], ey = Py[k1] - Py[k];
+                double l = std::sqrt(ex * ex + ey * ey);
+                double ca = ex / l, sa = ey / l;
+                double rx = Px[k2] - Px[k], ry = Py[k2] - Py[k];
+                double cx = rx * ca + ry * sa, cy = -rx * sa + ry * ca;
+                auto link = [&](int edge) -> int32_t {
+                    int32_t nb = nbr[3 * f + edge];
+                    if (nb < 0) return -1;
+                    int64_t g = nb >> 3;
+                    int kp = nb & 3, fl = (nb >> 2) & 1;
+                    return (int32_t)(((3 * g + kp) << 1) | fl);
+                };
+                int64_t h = 3 * (f0 + f) + k;
+                out->half[2 * h] = int4{bits((float)l), bits((float)cx), bits((float)cy), link(k1)};
+                out->half[2 * h + 1] = int4{link(k2), bits((float)ca), bits((float)sa), 0};
+            }
         }
         out->lref64[m] = lsum / (double)ne;
         out->lref[m] = (float)out->lref64[m];

@@ -16,6 +16,14 @@
 //   frm   float4[2*nF] the face frame in 3-D: {e1x, e1y, e1z, e2x}, {e2y, e2z, 0, 0} with
 //                      e1 = (x1-x0)/|x1-x0|, e2 = n x e1 (the axes of the 2-D record frame);
 //                      read by the backward pass (lifting 2-D adjoints, chord walks)
+//   half  int4[6*nF]   32-byte half-edge record per (face f, local edge k), id h = 3f + k, in the
+//                      edge's own frame (origin at corner k, x along the edge, the face on +y):
+//                      half[2h]   = { bits(l), bits(cx), bits(cy), linkR }
+//                      half[2h+1] = { linkL, bits(ca), bits(sa), 0 }
+//                      l = |edge k|, (cx, cy) = corner k+2 (the apex), (ca, sa) = the edge's unit
+//                      direction in the face frame (edge frame -> face frame rotation); linkR /
+//                      linkL = (h' << 1) | flip for the twin half-edge across edge k+1 (apex side
+//                      B -> C) / edge k+2 (C -> A), -1 on the boundary.
 //   V     float4[nV]   vertex position (x,y,z); .w = total angle theta(x), negated for boundary
 //                      vertices (Sec. 4: theta = sum of incident corner angles)
 //   face_off int32[n_mesh+1], lref float[n_mesh] (mean edge length per mesh)
@@ -37,6 +45,7 @@ struct sg_mesh {
     int4 *d_rec = nullptr;
     int4 *d_fv = nullptr;
     float4 *d_frm = nullptr;
+    int4 *d_half = nullptr;
     float4 *d_V = nullptr;
     int32_t *d_face_off = nullptr;
     float *d_lref = nullptr;
@@ -47,7 +56,7 @@ struct sg_mesh {
 
 // host-side builder (mesh_build.cpp); fills the host arrays, returns SG_OK or an error
 struct sg_host_mesh {
-    std::vector<int4> rec, fv;
+    std::vector<int4> rec, fv, half;
     std::vector<float4> frm;
     std::vector<float4> V;
     std::vector<int32_t> face_off;

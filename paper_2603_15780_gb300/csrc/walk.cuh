@@ -48,11 +48,20 @@ __device__ __forceinline__ int nbr_of(const FaceRec &r, int k) { return sel3(k, 
 __device__ __forceinline__ float corner_x(const FaceRec &r, int k) { return sel3(k, 0.f, r.l01, r.x2x); }
 __device__ __forceinline__ float corner_y(const FaceRec &r, int k) { return sel3(k, 0.f, 0.f, r.x2y); }
 __device__ __forceinline__ float inv_len(const FaceRec &r, int k) { return sel3(k, __frcp_rn(r.l01), r.il1, r.il2); }
+// half-edge record view of the same 8 words: l, cx, cy, linkR | linkL, ca, sa, -
+__device__ __forceinline__ float hl(const FaceRec &r) { return __int_as_float(r.n0); }
+__device__ __forceinline__ float hcx(const FaceRec &r) { return __int_as_float(r.n1); }
+__device__ __forceinline__ float hcy(const FaceRec &r) { return __int_as_float(r.n2); }
+__device__ __forceinline__ int hlinkR(const FaceRec &r) { return __float_as_int(r.l01); }
+__device__ __forceinline__ int hlinkL(const FaceRec &r) { return __float_as_int(r.x2x); }
+__device__ __forceinline__ float hca(const FaceRec &r) { return r.x2y; }
+__device__ __forceinline__ float hsa(const FaceRec &r) { return r.il1; }
 __device__ __forceinline__ int nxt(int k) { return k == 2 ? 0 : k + 1; }
 __device__ __forceinline__ int prv(int k) { return k == 0 ? 2 : k - 1; }
 
 struct WalkParams {
     const int4 *__restrict__ rec;
+    const int4 *__restrict__ half;
     const int4 *__restrict__ fv;
     const float4 *__restrict__ frm;
     const float4 *__restrict__ V;
@@ -63,10 +72,14 @@ struct WalkParams {
     int want_hash;
 };
 
-// Walker state (all registers).  mode: 0..2 entered through local edge `mode`;
-// 3..5 sitting on corner mode-3 after a vertex transport; 6 free start.
+// Walker state (all registers).  mode 7: on the entry edge of half-edge h (the hot case; R
+// holds the half-edge record, (px, py) = (fraction s along the edge, 0), d in the edge
+// frame); modes 0..2 entered through local edge `mode`, 3..5 sitting on corner mode-3 after a
+// vertex transport, 6 free start -- in these R holds the face record and p, d are in the face
+// frame.  Every walk ends in a face mode.
+#define SG_MODE_HALF 7
 struct Walker {
-    int f, mode, steps, ncross;
+    int f, h, mode, steps, ncross;
     float px, py, dx, dy;
     float Lh, Ll;        // remaining length as an unevaluated sum (compensated subtraction)
     uint32_t st;         // SG_ST_* | parity
@@ -187,62 +200,77 @@ __device__ __forceinline__ bool vertex_transport(Walker &w, int c, const WalkPar
     return false;
 }
 
-// An edge crossing as seen by observers: exit edge j of the old face with endpoints
-// (x0,y0) -> (x1,y1) and crossing point q in the old frame, the remaining length after the
-// crossing, the new face g entered through its local edge kp starting at (gax,gay) with edge
-// vector (fx,fy) in the new frame, the flip bit and the new direction.
+// An edge crossing as seen by observers: exit edge j (local edge of the old face) with
+// endpoints (x0,y0) -> (x1,y1) and crossing point q in the old frame, the remaining length
+// after the crossing, the new face g entered through its local edge kp starting at (gax,gay)
+// with edge vector (fx,fy) in the new frame, the flip bit, the new direction, and the
+// rotations that take each frame's vectors to its face frame.
 struct Cross {
     int j;
     float x0, y0, x1, y1, qx, qy, Lr;
     int g, kp, fl;
     float gax, gay, fx, fy, ndx, ndy;
+    float ca0, sa0, ca1, sa1;  // rotations old frame -> old face frame, new frame -> new face frame
 };
 
 // Observer of a walk (the backward pass hooks into the same step code as the forward).
 struct NoHook {
     // general step: sigma of the three corners after classification, entry mode, snapped corner
     __device__ __forceinline__ void on_face(const Walker &, float, float, float, int, int) {}
-    // edge-entry step: sigma of the apex and its position
-    __device__ __forceinline__ void on_apex(const Walker &, float, float, float) {}
+    // half-edge step: sigma of the apex, its position and the walker position (edge frame)
+    __device__ __forceinline__ void on_apex(const Walker &, float, float, float, float, float) {}
     // at an edge crossing (walker still in the old face, length already reduced)
     __device__ __forceinline__ void on_cross(const Walker &, const Cross &, const FaceRec &) {}
     // before a vertex transport at corner `hit` of the current face
     __device__ __forceinline__ void on_vertex(const Walker &, int) {}
 };
 
-// Step from a face entered through local edge k (the hot case): corners rotated so that
-// A -> B is the entry edge and C the apex; the exit edge is B -> C when the apex lies left of
-// the ray (sigma_C > 0), else C -> A.  The crossing maps the direction with the unnormalised
-// edge vectors e (old face) and f (new face) -- both have the edge's length, so the common
-// factor |e||f| disappears in the renormalisation.
+// Leave the half-edge frame: position (xe, ye) and direction into the face frame of w.f,
+// R becomes the face record (needed at the end of a walk and before a vertex transport).
+__device__ __forceinline__ void half_to_face(Walker &w, const WalkParams &P, float xe, float ye) {
+    const float ca = hca(w.R), sa = hsa(w.R);
+    const int k = w.h - 3 * w.f;
+    const FaceRec F = load_rec(P.rec, w.f);
+    w.px = corner_x(F, k) + ca * xe - sa * ye;
+    w.py = corner_y(F, k) + sa * xe + ca * ye;
+    const float dx = ca * w.dx - sa * w.dy, dy = sa * w.dx + ca * w.dy;
+    w.dx = dx; w.dy = dy;
+    w.R = F;
+    w.mode = 6;
+}
+
+// The hot step: the walker sits on the entry edge A=(0,0) -> B=(l,0) of half-edge h at
+// x = s*l, the apex is C=(cx,cy) with cy > 0.  sigma_A = dy x, sigma_B = -dy (l - x),
+// sigma_C = dx cy - dy (cx - x).  The exit edge is B -> C when the apex lies left of the ray
+// (sigma_C > 0), else C -> A.  The twin half-edge's frame has the crossed edge as its x axis
+// (reversed unless the adjacency is flipped) and the new face on +y, so the new direction is
+// (-+ d.e, d.n_out) / |e|, renormalised; no corner lookups are needed.
 template <bool ESC, class Hook>
-__device__ __forceinline__ bool edge_step(Walker &w, const WalkParams &P, Hook &hook) {
+__device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &hook) {
     const FaceRec &R = w.R;
-    const int k = w.mode;
     const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
-    const float Ax = sel3(k, 0.f, R.l01, R.x2x), Ay = sel3(k, 0.f, 0.f, R.x2y);
-    const float Bx = sel3(k, R.l01, R.x2x, 0.f), By = sel3(k, 0.f, R.x2y, 0.f);
-    const float Cx = sel3(k, R.x2x, 0.f, R.l01), Cy = sel3(k, R.x2y, 0.f, 0.f);
-    float sA = sigma32(w.dx, w.dy, Ax, Ay, w.px, w.py);
-    float sB = sigma32(w.dx, w.dy, Bx, By, w.px, w.py);
-    float sC = sigma32(w.dx, w.dy, Cx, Cy, w.px, w.py);
+    const float L0 = hl(R), cx = hcx(R), cy = hcy(R);
+    const float x = w.px * L0;
+    float sA = w.dy * x;
+    float sB = -w.dy * (L0 - x);
+    float sC = fmaf(w.dx, cy, -w.dy * (cx - x));
     if (ESC && fabsf(sC) < near) {
         // FP64 re-evaluation of the classification (exact products of the FP32 state)
         w.st |= SG_ST_FP64;
-        sA = f32_keep_sign(sigma64(w.dx, w.dy, Ax, Ay, w.px, w.py));
-        sB = f32_keep_sign(sigma64(w.dx, w.dy, Bx, By, w.px, w.py));
-        sC = f32_keep_sign(sigma64(w.dx, w.dy, Cx, Cy, w.px, w.py));
+        const double X = (double)w.px * (double)L0;
+        sA = f32_keep_sign((double)w.dy * X);
+        sB = f32_keep_sign(-(double)w.dy * ((double)L0 - X));
+        sC = f32_keep_sign((double)w.dx * (double)cy - (double)w.dy * ((double)cx - X));
     }
     const bool hit = fabsf(sC) <= snap;  // a snapped apex is a hit, not a near miss
     if (!hit && fabsf(sC) < near) w.st |= SG_ST_NEAR_VERTEX;
-    hook.on_apex(w, sC, Cx, Cy);
+    hook.on_apex(w, sC, cx, cy, x, 0.f);
     const bool right = sC > 0.f;
-    const int j = right ? nxt(k) : prv(k);
-    const float x0 = right ? Bx : Cx, y0 = right ? By : Cy;
-    const float x1 = right ? Cx : Ax, y1 = right ? Cy : Ay;
+    const float x0 = right ? L0 : cx, y0 = right ? 0.f : cy;
+    const float x1 = right ? cx : 0.f, y1 = right ? cy : 0.f;
     float qx, qy, s;
     if (hit) {
-        qx = Cx; qy = Cy;
+        qx = cx; qy = cy;
         s = right ? 1.f : 0.f;
     } else {
         const float s0 = right ? sB : sC, s1 = right ? sC : sA;
@@ -252,16 +280,17 @@ __device__ __forceinline__ bool edge_step(Walker &w, const WalkParams &P, Hook &
         qx = fmaf(s, x1 - x0, x0);
         qy = fmaf(s, y1 - y0, y0);
     }
-    const float t = fmaxf(fmaf(qx - w.px, w.dx, (qy - w.py) * w.dy), 0.f);
+    const float t = fmaxf(fmaf(qx - x, w.dx, qy * w.dy), 0.f);
     const float L = w.Lh + w.Ll;
     if (t >= L) {
         // final truncated in-face segment (reading: stop once the length is used up)
-        w.px = fmaf(L, w.dx, w.px);
-        w.py = fmaf(L, w.dy, w.py);
+        const float xe = fmaf(L, w.dx, x), ye = L * w.dy;
         w.Lh = 0.f; w.Ll = 0.f;
+        half_to_face(w, P, xe, ye);
+        const FaceRec &F = w.R;
         float d0 = fabsf(w.py);
-        float d1 = fabsf((R.x2x - R.l01) * (w.py) - R.x2y * (w.px - R.l01)) * R.il1;
-        float d2 = fabsf(R.x2x * w.py - R.x2y * w.px) * R.il2;
+        float d1 = fabsf((F.x2x - F.l01) * (w.py) - F.x2y * (w.px - F.l01)) * F.il1;
+        float d2 = fabsf(F.x2x * w.py - F.x2y * w.px) * F.il2;
         if (fminf(fminf(d0, d1), d2) <= near) w.st |= SG_ST_NEAR_EDGE;
         return true;
     }
@@ -274,35 +303,37 @@ __device__ __forceinline__ bool edge_step(Walker &w, const WalkParams &P, Hook &
         w.Ll += err;
     }
     if (hit) {
-        hook.on_vertex(w, prv(k));
-        return !vertex_transport(w, prv(k), P);
+        const int c = prv(w.h - 3 * w.f);  // the apex is corner k+2 of the face
+        half_to_face(w, P, cx, cy);
+        hook.on_vertex(w, c);
+        return !vertex_transport(w, c, P);
     }
-    const int nb = nbr_of(R, j);
-    if (nb < 0) {  // boundary edge: original rule stops (Sec. 4)
-        w.px = qx; w.py = qy;
+    const int link = right ? hlinkR(R) : hlinkL(R);
+    if (link < 0) {  // boundary edge: original rule stops (Sec. 4)
+        half_to_face(w, P, qx, qy);
         w.st |= SG_ST_BOUNDARY;
         return true;
     }
-    const int g = nb >> 3, kp = nb & 3, fl = (nb >> 2) & 1;
+    const int hn = link >> 1, fl = link & 1;
     const float ex = x1 - x0, ey = y1 - y0;
     const float da = fmaf(w.dx, ex, w.dy * ey);   // |e| (d . e_hat)
     const float dc = fmaf(w.dx, ey, -w.dy * ex);  // |e| (d . n_out)
-    const FaceRec G = load_rec(P.rec, g);
-    const float gax = sel3(kp, 0.f, G.l01, G.x2x), gay = sel3(kp, 0.f, 0.f, G.x2y);
-    const float gbx = sel3(kp, G.l01, G.x2x, 0.f), gby = sel3(kp, 0.f, G.x2y, 0.f);
-    const float fx = gbx - gax, fy = gby - gay;
-    const float sa_ = fl ? da : -da;
-    float ndx = fmaf(sa_, fx, -dc * fy);
-    float ndy = fmaf(sa_, fy, dc * fx);
+    const FaceRec G = load_rec(P.half, hn);
+    float ndx = fl ? da : -da, ndy = dc;
     renorm(ndx, ndy);
-    hook.on_cross(w, Cross{j, x0, y0, x1, y1, qx, qy, w.Lh + w.Ll, g, kp, fl, gax, gay, fx, fy, ndx, ndy}, G);
-    const float sp = fl ? s : 1.f - s;
-    w.px = fmaf(sp, fx, gax);
-    w.py = fmaf(sp, fy, gay);
+    const int g = hn / 3;
+    {
+        const int k = w.h - 3 * w.f;
+        hook.on_cross(w, Cross{right ? nxt(k) : prv(k), x0, y0, x1, y1, qx, qy, w.Lh + w.Ll, g, hn - 3 * g, fl,
+                               0.f, 0.f, hl(G), 0.f, ndx, ndy, hca(R), hsa(R), hca(G), hsa(G)},
+                      G);
+    }
+    w.px = fl ? s : 1.f - s;
+    w.py = 0.f;
     w.dx = ndx; w.dy = ndy;
     w.f = g;
+    w.h = hn;
     w.R = G;
-    w.mode = kp;
     if (fl) w.st ^= SG_PARITY_BIT;
     w.ncross++;
     walker_hash(w, g, P.want_hash);
@@ -316,16 +347,17 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
 template <bool ESC, class Hook = NoHook>
 __device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook &&hook = Hook()) {
     if (w.steps >= P.max_steps) {
+        if (w.mode == SG_MODE_HALF) half_to_face(w, P, w.px * hl(w.R), 0.f);
         w.st |= SG_ST_MAX_STEPS;
         return true;
     }
     w.steps++;
-    if (w.mode < 3) return edge_step<ESC>(w, P, hook);
+    if (w.mode == SG_MODE_HALF) return half_step<ESC>(w, P, hook);
     return general_step<ESC>(w, P, hook);
 }
 
-// Step from a corner (after a vertex transport) or from a free start point; also handles
-// an entry edge, but the hot path for that case is edge_step.
+// Step from a corner (after a vertex transport) or from a free start point (face frame); a
+// crossing moves the walker into the half-edge frame of the face it enters.
 template <bool ESC, class Hook>
 __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hook &hook) {
     const FaceRec &R = w.R;
@@ -423,31 +455,24 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
         return true;
     }
     const int g = nb >> 3, kp = nb & 3, fl = (nb >> 2) & 1;
-    // direction in the edge basis of f: along-edge a, outward-normal c
-    float il = inv_len(R, j);
-    float ex = (bx - ax) * il, ey = (by - ay) * il;
-    float da = fmaf(w.dx, ex, w.dy * ey);
-    float dc = fmaf(w.dx, ey, -w.dy * ex);  // d . (ey, -ex)
-    FaceRec G = load_rec(P.rec, g);
-    const int kb = nxt(kp);
-    float gax = corner_x(G, kp), gay = corner_y(G, kp);
-    float gbx = corner_x(G, kb), gby = corner_y(G, kb);
-    float gil = inv_len(G, kp);
-    float fx = (gbx - gax) * gil, fy = (gby - gay) * gil;
-    // d' = (+-a) e' - c n'_out, n'_out = (fy, -fx)
-    float sa_ = fl ? da : -da;
-    float ndx = fmaf(sa_, fx, -dc * fy);
-    float ndy = fmaf(sa_, fy, dc * fx);
+    // into the half-edge frame of (g, kp): x along the crossed edge, the new face on +y
+    const float ex = bx - ax, ey = by - ay;
+    const float da = fmaf(w.dx, ex, w.dy * ey);
+    const float dc = fmaf(w.dx, ey, -w.dy * ex);  // d . (ey, -ex)
+    const int hn = 3 * g + kp;
+    const FaceRec G = load_rec(P.half, hn);
+    float ndx = fl ? da : -da, ndy = dc;
     renorm(ndx, ndy);
-    hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, gax, gay, gbx - gax, gby - gay, ndx, ndy},
+    hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, 0.f, 0.f, hl(G), 0.f, ndx, ndy,
+                           1.f, 0.f, hca(G), hsa(G)},
                   G);
-    float sp = fl ? s : 1.f - s;
-    w.px = fmaf(sp, gbx - gax, gax);
-    w.py = fmaf(sp, gby - gay, gay);
+    w.px = fl ? s : 1.f - s;
+    w.py = 0.f;
     w.dx = ndx; w.dy = ndy;
     w.f = g;
+    w.h = hn;
     w.R = G;
-    w.mode = kp;
+    w.mode = SG_MODE_HALF;
     if (fl) w.st ^= SG_PARITY_BIT;
     w.ncross++;
     walker_hash(w, g, P.want_hash);
@@ -504,7 +529,7 @@ __device__ bool walker_init(const WalkParams &P, const QueryIn &a, int64_t q, Wa
     int m = a.mesh_id ? __ldg(a.mesh_id + q) : 0;
     int lf = __ldg(a.face + q);
     w.st = 0; w.steps = 0; w.ncross = 0; w.hash = SG_FNV_OFFSET;
-    w.mode = 6; w.Ll = 0.f;
+    w.mode = 6; w.Ll = 0.f; w.h = -1;
     bool bad = (m < 0 || m >= a.n_mesh);
     int foff = bad ? 0 : __ldg(P.face_off + m);
     int nfm = bad ? 1 : __ldg(P.face_off + m + 1) - foff;
