@@ -433,15 +433,17 @@ def main():
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     peak, peak_kind = peaks()
-    # forward walk: one 32-B record per crossing; per query the inputs (face, bary, v: 28 B),
-    # the queue ticket permutation (4 B), the outputs (face, bary, pos, dir, status, ncross:
-    # 48 B) and the start and end frame gathers (vertex ids + 3 vertices: 2 x 64 B)
-    walk_bytes = ncross * RECORD_BYTES + nq * (28 + 4 + 48 + 128)
-    # GFD re-walk with vertex gradients: per crossing the record (32 B), the new face's
-    # vertex ids (16 B) and 3-D frame (32 B) and one float4 accumulator flush (16 B); per
-    # query inputs (28 B), the forward end state and upstream gradient (48 B), start/end
-    # frames and vertices (96 B), start/end atomic adds (6 x 16 B), status (4 B)
-    rewalk_bytes = ncross * (RECORD_BYTES + 16 + 32 + 16) + nq * (28 + 48 + 96 + 96 + 4)
+    # forward walk: one 32-B half-edge record per crossing; per query the inputs (face, bary,
+    # v: 28 B), the queue ticket permutation (4 B), the start face record (32 B), the start and
+    # end frame gathers (vertex ids + 3 vertices: 2 x 64 B), the end face record (32 B) and the
+    # outputs (face, bary, pos, dir, status, ncross: 48 B)
+    walk_bytes = ncross * RECORD_BYTES + nq * (28 + 4 + 32 + 128 + 32 + 48)
+    # GFD re-walk with vertex gradients: per crossing the 32-B half-edge record and two 8-B
+    # atomic adds of half-edge coefficients; per query the inputs (28 B), start face record,
+    # frame, vertex ids and vertices (128 B), forward end state and upstream gradient with the
+    # end frame (64 B), end face record (32 B), start/end vertex atomics (6 x 16 B) and
+    # end-face frame and ids (48 B), status (4 B)
+    rewalk_bytes = ncross * (RECORD_BYTES + 16) + nq * (28 + 128 + 64 + 32 + 96 + 48 + 4)
     kern = {"k_walk_persistent": (walk_bytes, float(np.mean(ktimes["walk"]))),
             "k_bwd_rewalk": (rewalk_bytes, float(np.mean(ktimes["rewalk"])))}
     dom = max(kern, key=lambda k: kern[k][1])

@@ -58,6 +58,7 @@ struct BwdArgs {
     uint32_t *out_status;
     float eps_v, eps_p;
     float4 *gacc;       // [nV] vertex-gradient accumulator (scratch)
+    float2 *hacc;       // [3 nF] per half-edge (start, end) coefficients of its edge normal (scratch)
     float *cols;        // [nq][4] column contractions: par, perp, u, v (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) swept perturbations (scratch)
     int32_t *ntask;     // task counter (scratch)
@@ -192,68 +193,34 @@ struct StraddleHook {
     }
 };
 
-// Adjoint of the crossing maps, accumulated into the vertex-gradient scratch.
-// For a crossing with end point y (old frame, a = (y-A).e, c = (y-A).n), upstream gradient
-// gbar' in the new frame (ge = gbar'.e', gn = gbar'.m') and sf = +1 for a flipped adjacency,
-// -1 otherwise, the 2-D corner gradients lifted to 3-D combine per shared vertex into
-//   g_B = (K1 N_old + sf K2 N_new) / l,   g_A = (G_new - G_old) - g_B,
-//   K1 = sf ge c + gn a,  K2 = sf a gn + c ge,
-// where N_old, N_new are the 3-D in-plane unit normals of the edge pointing out of each face
-// and G_old, G_new the adjoint vector lifted into the old and the new face (it is carried
-// from one crossing to the next).  B is the exit edge's end corner in the old face.
+// Adjoint of the crossing maps.  For a crossing of edge A -> B (the exit edge, unit e, outward
+// unit normal n in the old frame) with end point y (old frame) and upstream gradient gbar in
+// the old frame (g_e = gbar.e, g_n = gbar.n), the transition's linear part gives the same
+// scalar K = g_e ((y-A).n) - g_n ((y-A).e) for both faces' corner gradients, and the jump of
+// the lifted adjoint across the edge is -g_n (N_old + N_new).  Lifted to 3-D the two shared
+// vertices receive
+//   g_B = (K / l) (N_old + N_new),   g_A = -(g_n + K / l) (N_old + N_new),
+// N_old / N_new = the in-plane unit normals of the edge pointing out of the old / new face.
+// Both are constants of the half-edges, so the walk only accumulates the two scalar
+// coefficients per half-edge side (start corner, end corner); k_gradv_halfedges turns them
+// into vertex gradients once.  For coplanar faces N_old + N_new = 0.
 struct GradHook {
-    float4 *gacc;
-    const WalkParams *P;
+    float2 *hacc;
     float a, bs;        // gbar_i = a d_i + bs * s_i * perp(d_i)
-    int4 fvc;           // vertex ids of the current face
-    Fr2 Fc;             // 3-D axes of the current face
-    F3 Gc;              // the adjoint lifted into the current face
-    int v0, v1;         // two-slot register cache of per-vertex sums
-    F3 c0, c1;
-    __device__ __forceinline__ void flush(int v, F3 c) {
-        if (v >= 0) atomic_add3(gacc, v, c);
-    }
     __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &) {
         const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;
         const float il = rsqrtf(fmaf(exr, exr, eyr * eyr));
-        const float ex = exr * il, ey = eyr * il;
+        const float ex = exr * il, ey = eyr * il;                       // e; n = (ey, -ex)
         const float yx = fmaf(c.Lr, w.dx, c.qx) - c.x0, yy = fmaf(c.Lr, w.dy, c.qy) - c.y0;  // y - A
-        const float ax_ = yx * ex + yy * ey;
-        const float cc = yx * ey - yy * ex;
-        const float ilp = rsqrtf(fmaf(c.fx, c.fx, c.fy * c.fy));
-        const float fx = c.fx * ilp, fy = c.fy * ilp;
-        // upstream gradient in the new frame
-        const uint32_t par = (w.st & SG_PARITY_BIT) ^ (c.fl ? SG_PARITY_BIT : 0u);
-        const float sb = par ? -bs : bs;
-        const float gx = a * c.ndx - sb * c.ndy, gy = a * c.ndy + sb * c.ndx;
-        const float sf = c.fl ? 1.f : -1.f;
-        const float ge = gx * fx + gy * fy, gn = gx * fy - gy * fx;
-        const float K1 = sf * ge * cc + gn * ax_;
-        const float K2 = sf * ax_ * gn + cc * ge;
-        const int4 fvg = __ldg(P->fv + c.g);
-        const Fr2 Fg = load_frm(*P, c.g);
-        // lift through each frame's rotation to its face frame
-        const F3 Nold = lift(Fc, c.ca0 * ey + c.sa0 * ex, c.sa0 * ey - c.ca0 * ex);
-        const F3 Nnew = lift(Fg, c.ca1 * fy + c.sa1 * fx, c.sa1 * fy - c.ca1 * fx);
-        const F3 Gn = lift(Fg, c.ca1 * gx - c.sa1 * gy, c.sa1 * gx + c.ca1 * gy);
-        const F3 gB = il * (K1 * Nold + (sf * K2) * Nnew);
-        const F3 gA = (Gn - Gc) - gB;
-        const int vA = sel3(c.j, fvc.x, fvc.y, fvc.z), vB = sel3(nxt(c.j), fvc.x, fvc.y, fvc.z);
-        // keep vA and vB in the cache, evicting the slot neither of them uses
-        const bool inA = (vA == v0) || (vA == v1), inB = (vB == v0) || (vB == v1);
-        if (!inA || !inB) {
-            const bool keep0 = (v0 == vA) || (v0 == vB), keep1 = (v1 == vA) || (v1 == vB);
-            if (!keep0) { flush(v0, c0); v0 = -1; }
-            if (!keep1) { flush(v1, c1); v1 = -1; }
-            if (!inA) { if (v0 < 0) { v0 = vA; c0 = f3(0.f, 0.f, 0.f); } else { v1 = vA; c1 = f3(0.f, 0.f, 0.f); } }
-            if (!inB) { if (v0 < 0) { v0 = vB; c0 = f3(0.f, 0.f, 0.f); } else { v1 = vB; c1 = f3(0.f, 0.f, 0.f); } }
-        }
-        const bool a0 = vA == v0;
-        c0 = c0 + (a0 ? gA : gB);
-        c1 = c1 + (a0 ? gB : gA);
-        fvc = fvg;
-        Fc = Fg;
-        Gc = Gn;
+        const float ya = yx * ex + yy * ey, yc = yx * ey - yy * ex;
+        const float sb = (w.st & SG_PARITY_BIT) ? -bs : bs;             // old-frame parity
+        const float gx = a * w.dx - sb * w.dy, gy = a * w.dy + sb * w.dx;
+        const float ge = gx * ex + gy * ey, gn = gx * ey - gy * ex;
+        const float kB = il * (ge * yc - gn * ya);
+        const float kA = -(gn + kB);
+        const int hold = 3 * w.f + c.j, hnew = 3 * c.g + c.kp;
+        atomicAdd(hacc + hold, make_float2(kA, kB));
+        atomicAdd(hacc + hnew, c.fl ? make_float2(kA, kB) : make_float2(kB, kA));
     }
 };
 
@@ -310,29 +277,25 @@ struct RewalkJob {
         if (GRADV && H.gradv) {
             EndAdj E = end_adjoint(*A, q, w.foff);
             gq = E.g;
-            H.G.gacc = A->gacc;
-            H.G.P = &A->P;
+            H.G.hacc = A->hacc;
             H.G.a = E.a;
             H.G.bs = E.sm * E.b;
-            H.G.fvc = __ldg(P.fv + w.f);
-            H.G.Fc = load_frm(P, w.f);
-            H.G.v0 = -1; H.G.v1 = -1;
-            H.G.c0 = f3(0.f, 0.f, 0.f); H.G.c1 = f3(0.f, 0.f, 0.f);
             // start face: p0 = sum b_k P_k -> grad x_k += b_k F0 gbar0; tilt term if v has a
             // normal component (moving the plane changes the projection of v)
+            const int4 fv0 = __ldg(P.fv + w.f);
+            const Fr2 F0 = load_frm(P, w.f);
             const float g0x = E.a * d0x - E.sm * E.b * d0y, g0y = E.a * d0y + E.sm * E.b * d0x;
             float b2 = w.py / w.R.x2y, b1 = (w.px - b2 * w.R.x2x) / w.R.l01, b0 = 1.f - b1 - b2;
-            F3 G0 = lift(H.G.Fc, g0x, g0y);
-            H.G.Gc = G0;
-            F3 n0 = nrm_of(H.G.Fc);
+            F3 G0 = lift(F0, g0x, g0y);
+            F3 n0 = nrm_of(F0);
             float vn = dot3(ld3(A->in.v, q), n0);
-            F3 x0 = vpos(P, H.G.fvc.x), u = vpos(P, H.G.fvc.y) - x0, ww = vpos(P, H.G.fvc.z) - x0;
+            F3 x0 = vpos(P, fv0.x), u = vpos(P, fv0.y) - x0, ww = vpos(P, fv0.z) - x0;
             F3 m = cross3(u, ww);
             F3 h = (-vn * rsqrtf(dot3(m, m))) * G0;
             F3 t1 = cross3(ww, h), t2 = cross3(h, u);
-            atomic_add3(A->gacc, H.G.fvc.x, b0 * G0 - (t1 + t2));
-            atomic_add3(A->gacc, H.G.fvc.y, b1 * G0 + t1);
-            atomic_add3(A->gacc, H.G.fvc.z, b2 * G0 + t2);
+            atomic_add3(A->gacc, fv0.x, b0 * G0 - (t1 + t2));
+            atomic_add3(A->gacc, fv0.y, b1 * G0 + t1);
+            atomic_add3(A->gacc, fv0.z, b2 * G0 + t2);
         }
         return true;
     }
@@ -344,16 +307,15 @@ struct RewalkJob {
         }
         st |= w.st & ~SG_PARITY_BIT;
         if (GRADV && H.gradv) {
-            H.G.flush(H.G.v0, H.G.c0);
-            H.G.flush(H.G.v1, H.G.c1);
             // end face: grad x_j += b'_j (g . n) n
             const FaceRec &R = w.R;
+            const int4 fve = __ldg(A->P.fv + w.f);
             float b2 = w.py / R.x2y, b1 = (w.px - b2 * R.x2x) / R.l01, b0 = 1.f - b1 - b2;
-            F3 n = nrm_of(H.G.Fc);
+            F3 n = nrm_of(load_frm(A->P, w.f));
             F3 gn = dot3(gq, n) * n;
-            atomic_add3(A->gacc, H.G.fvc.x, b0 * gn);
-            atomic_add3(A->gacc, H.G.fvc.y, b1 * gn);
-            atomic_add3(A->gacc, H.G.fvc.z, b2 * gn);
+            atomic_add3(A->gacc, fve.x, b0 * gn);
+            atomic_add3(A->gacc, fve.y, b1 * gn);
+            atomic_add3(A->gacc, fve.z, b2 * gn);
         }
         if (GFD) {
             unsigned split = H.S.split;
@@ -370,7 +332,7 @@ struct RewalkJob {
 };
 
 template <bool GFD, bool GRADV>
-__global__ void __launch_bounds__(128, 5) k_bwd_rewalk(BwdArgs A) {
+__global__ void __launch_bounds__(128, 6) k_bwd_rewalk(BwdArgs A) {
     RewalkJob<GFD, GRADV> job;
     job.A = &A;
     run_persistent(A.ntask + 1, A.nq, job);
@@ -530,6 +492,21 @@ __global__ void __launch_bounds__(256) k_bwd_assemble(BwdArgs A) {
     if (A.grad_bary) st3(A.grad_bary, q, gb);
 }
 
+// per half-edge (face f, edge k): its coefficients times the edge's outward in-plane normal
+// N = F_f (sa, -ca), added to the edge's start corner k and end corner k+1
+__global__ void k_gradv_halfedges(int64_t nh, WalkParams P, const float2 *__restrict__ hacc, float4 *gacc) {
+    int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= nh) return;
+    const float2 c = hacc[h];
+    if (c.x == 0.f && c.y == 0.f) return;
+    const int f = (int)(h / 3), k = (int)(h - 3 * (int64_t)f);
+    const FaceRec H = load_rec(P.half, (int)h);
+    const F3 N = lift(load_frm(P, f), hsa(H), -hca(H));
+    const int4 t = __ldg(P.fv + f);
+    atomic_add3(gacc, sel3(k, t.x, t.y, t.z), c.x * N);
+    atomic_add3(gacc, sel3(nxt(k), t.x, t.y, t.z), c.y * N);
+}
+
 __global__ void k_gradv_flush(int64_t nV, const float4 *__restrict__ gacc, float *grad_V) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nV) return;
@@ -554,13 +531,16 @@ unsigned persistent_grid(K kernel, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
 }
 struct BwdLayout {
-    size_t gacc, cols, tasks, ntask, total;
+    size_t gacc, hacc, cols, tasks, ntask, total;
 };
-BwdLayout bwd_layout(int64_t nV, int64_t nq, int32_t estimator, bool grad_V) {
+BwdLayout bwd_layout(int64_t nV, int64_t nF, int64_t nq, int32_t estimator, bool grad_V) {
     BwdLayout L{};
     size_t o = 0;
     L.ntask = o; o = align_up(o + 64, 256);
-    if (grad_V) { L.gacc = o; o = align_up(o + sizeof(float4) * (size_t)nV, 256); }
+    if (grad_V) {
+        L.gacc = o; o = align_up(o + sizeof(float4) * (size_t)nV, 256);
+        L.hacc = o; o = align_up(o + sizeof(float2) * 3 * (size_t)nF, 256);
+    }
     if (estimator == SG_EST_GFD) {
         L.cols = o; o = align_up(o + sizeof(float) * 4 * (size_t)std::max<int64_t>(nq, 1), 256);
         L.tasks = o; o = align_up(o + sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(nq, 1), 256);
@@ -574,7 +554,7 @@ extern "C" sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_
                                                         int32_t want_grad_V, size_t *bytes) {
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
     if (estimator != SG_EST_EP && estimator != SG_EST_GFD) return SG_ERR_INVALID_ARG;
-    *bytes = bwd_layout(m->nV, nq, estimator, want_grad_V != 0).total;
+    *bytes = bwd_layout(m->nV, m->nF, nq, estimator, want_grad_V != 0).total;
     return SG_OK;
 }
 
@@ -609,7 +589,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.grad_v = grad_v; A.grad_p = grad_p; A.grad_bary = grad_bary; A.grad_V = grad_V; A.out_status = out_status;
     A.eps_v = eps_v; A.eps_p = eps_p;
 
-    BwdLayout Lw = bwd_layout(m->nV, nq, estimator, grad_V != nullptr);
+    BwdLayout Lw = bwd_layout(m->nV, m->nF, nq, estimator, grad_V != nullptr);
     void *ws = nullptr;
     bool own = false;
     if (r.workspace) {
@@ -621,10 +601,16 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     }
     char *base = (char *)ws;
     A.ntask = (int32_t *)(base + Lw.ntask);
-    if (grad_V) A.gacc = (float4 *)(base + Lw.gacc);
+    if (grad_V) {
+        A.gacc = (float4 *)(base + Lw.gacc);
+        A.hacc = (float2 *)(base + Lw.hacc);
+    }
     if (estimator == SG_EST_GFD) { A.cols = (float *)(base + Lw.cols); A.tasks = (int32_t *)(base + Lw.tasks); }
     cudaMemsetAsync(A.ntask, 0, 64, s);
-    if (grad_V) cudaMemsetAsync(A.gacc, 0, sizeof(float4) * (size_t)m->nV, s);
+    if (grad_V) {
+        cudaMemsetAsync(A.gacc, 0, sizeof(float4) * (size_t)m->nV, s);
+        cudaMemsetAsync(A.hacc, 0, sizeof(float2) * 3 * (size_t)m->nF, s);
+    }
     const unsigned g128 = (unsigned)((nq + 127) / 128), g256 = (unsigned)((nq + 255) / 256);
     if (estimator == SG_EST_EP) {
         k_ep_backward<<<g256, 256, 0, s>>>(A);
@@ -643,7 +629,10 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         k_bwd_literal<<<persistent_grid(k_bwd_literal, 3 * nq), 128, 0, s>>>(A);
         k_bwd_assemble<<<g256, 256, 0, s>>>(A);
     }
-    if (grad_V) k_gradv_flush<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, A.gacc, grad_V);
+    if (grad_V) {
+        k_gradv_halfedges<<<(unsigned)((3 * m->nF + 255) / 256), 256, 0, s>>>(3 * m->nF, A.P, A.hacc, A.gacc);
+        k_gradv_flush<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, A.gacc, grad_V);
+    }
     if (own) cudaFreeAsync(ws, s);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
