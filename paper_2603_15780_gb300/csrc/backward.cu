@@ -58,7 +58,8 @@ struct BwdArgs {
     uint32_t *out_status;
     float eps_v, eps_p;
     float4 *gacc;       // [nV] vertex-gradient accumulator (scratch)
-    float2 *hacc;       // [3 nF] per half-edge (start, end) coefficients of its edge normal (scratch)
+    float2 *eacc;       // [nE] per interior edge (start, end) coefficients, canonical orientation (scratch)
+    const int2 *edges;  // [nE] (canonical half-edge, twin)
     float *cols;        // [nq][4] column contractions: par, perp, u, v (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) swept perturbations (scratch)
     int32_t *ntask;     // task counter (scratch)
@@ -201,13 +202,14 @@ struct StraddleHook {
 // vertices receive
 //   g_B = (K / l) (N_old + N_new),   g_A = -(g_n + K / l) (N_old + N_new),
 // N_old / N_new = the in-plane unit normals of the edge pointing out of the old / new face.
-// Both are constants of the half-edges, so the walk only accumulates the two scalar
-// coefficients per half-edge side (start corner, end corner); k_gradv_halfedges turns them
-// into vertex gradients once.  For coplanar faces N_old + N_new = 0.
+// N_old + N_new is a constant of the edge, so the walk only adds the two scalar
+// coefficients to the edge's accumulator (one atomic per crossing, in the edge's canonical
+// orientation, read from the twin half-edge record that the crossing loads anyway);
+// k_gradv_edges turns them into vertex gradients once.  For coplanar faces N_old + N_new = 0.
 struct GradHook {
-    float2 *hacc;
+    float2 *eacc;
     float a, bs;        // gbar_i = a d_i + bs * s_i * perp(d_i)
-    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &) {
+    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &G) {
         const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;
         const float il = rsqrtf(fmaf(exr, exr, eyr * eyr));
         const float ex = exr * il, ey = eyr * il;                       // e; n = (ey, -ex)
@@ -218,9 +220,12 @@ struct GradHook {
         const float ge = gx * ex + gy * ey, gn = gx * ey - gy * ex;
         const float kB = il * (ge * yc - gn * ya);
         const float kA = -(gn + kB);
-        const int hold = 3 * w.f + c.j, hnew = 3 * c.g + c.kp;
-        atomicAdd(hacc + hold, make_float2(kA, kB));
-        atomicAdd(hacc + hnew, c.fl ? make_float2(kA, kB) : make_float2(kB, kA));
+        // the twin half-edge runs B -> A (A -> B when flipped); its record holds the edge id and
+        // whether it is the edge's canonical half-edge
+        const int ed = __float_as_int(G.il2);
+        // canonical orientation is A -> B unless the twin (running B -> A) is the canonical one
+        const bool same = ((ed & 1) != 0) || (c.fl != 0);
+        atomicAdd(eacc + (ed >> 1), same ? make_float2(kA, kB) : make_float2(kB, kA));
     }
 };
 
@@ -277,7 +282,7 @@ struct RewalkJob {
         if (GRADV && H.gradv) {
             EndAdj E = end_adjoint(*A, q, w.foff);
             gq = E.g;
-            H.G.hacc = A->hacc;
+            H.G.eacc = A->eacc;
             H.G.a = E.a;
             H.G.bs = E.sm * E.b;
             // start face: p0 = sum b_k P_k -> grad x_k += b_k F0 gbar0; tilt term if v has a
@@ -492,19 +497,22 @@ __global__ void __launch_bounds__(256) k_bwd_assemble(BwdArgs A) {
     if (A.grad_bary) st3(A.grad_bary, q, gb);
 }
 
-// per half-edge (face f, edge k): its coefficients times the edge's outward in-plane normal
-// N = F_f (sa, -ca), added to the edge's start corner k and end corner k+1
-__global__ void k_gradv_halfedges(int64_t nh, WalkParams P, const float2 *__restrict__ hacc, float4 *gacc) {
-    int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= nh) return;
-    const float2 c = hacc[h];
+// per interior edge: its coefficients times N_a + N_b (the outward in-plane normals of the edge
+// in its two faces, N = F_f (sa, -ca) of each half-edge), added to the canonical half-edge's
+// start and end vertices
+__global__ void k_gradv_edges(int64_t nE, WalkParams P, const int2 *__restrict__ edges, const float2 *__restrict__ eacc,
+                              float4 *gacc) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    const float2 c = eacc[e];
     if (c.x == 0.f && c.y == 0.f) return;
-    const int f = (int)(h / 3), k = (int)(h - 3 * (int64_t)f);
-    const FaceRec H = load_rec(P.half, (int)h);
-    const F3 N = lift(load_frm(P, f), hsa(H), -hca(H));
-    const int4 t = __ldg(P.fv + f);
-    atomic_add3(gacc, sel3(k, t.x, t.y, t.z), c.x * N);
-    atomic_add3(gacc, sel3(nxt(k), t.x, t.y, t.z), c.y * N);
+    const int2 hh = __ldg(edges + e);
+    const int fa = hh.x / 3, ka = hh.x - 3 * fa, fb = hh.y / 3;
+    const FaceRec Ha = load_rec(P.half, hh.x), Hb = load_rec(P.half, hh.y);
+    const F3 N = lift(load_frm(P, fa), hsa(Ha), -hca(Ha)) + lift(load_frm(P, fb), hsa(Hb), -hca(Hb));
+    const int4 t = __ldg(P.fv + fa);
+    atomic_add3(gacc, sel3(ka, t.x, t.y, t.z), c.x * N);
+    atomic_add3(gacc, sel3(nxt(ka), t.x, t.y, t.z), c.y * N);
 }
 
 __global__ void k_gradv_flush(int64_t nV, const float4 *__restrict__ gacc, float *grad_V) {
@@ -531,15 +539,15 @@ unsigned persistent_grid(K kernel, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
 }
 struct BwdLayout {
-    size_t gacc, hacc, cols, tasks, ntask, total;
+    size_t gacc, eacc, cols, tasks, ntask, total;
 };
-BwdLayout bwd_layout(int64_t nV, int64_t nF, int64_t nq, int32_t estimator, bool grad_V) {
+BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool grad_V) {
     BwdLayout L{};
     size_t o = 0;
     L.ntask = o; o = align_up(o + 64, 256);
     if (grad_V) {
         L.gacc = o; o = align_up(o + sizeof(float4) * (size_t)nV, 256);
-        L.hacc = o; o = align_up(o + sizeof(float2) * 3 * (size_t)nF, 256);
+        L.eacc = o; o = align_up(o + sizeof(float2) * (size_t)std::max<int64_t>(nE, 1), 256);
     }
     if (estimator == SG_EST_GFD) {
         L.cols = o; o = align_up(o + sizeof(float) * 4 * (size_t)std::max<int64_t>(nq, 1), 256);
@@ -554,7 +562,7 @@ extern "C" sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_
                                                         int32_t want_grad_V, size_t *bytes) {
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
     if (estimator != SG_EST_EP && estimator != SG_EST_GFD) return SG_ERR_INVALID_ARG;
-    *bytes = bwd_layout(m->nV, m->nF, nq, estimator, want_grad_V != 0).total;
+    *bytes = bwd_layout(m->nV, m->nE, nq, estimator, want_grad_V != 0).total;
     return SG_OK;
 }
 
@@ -589,7 +597,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.grad_v = grad_v; A.grad_p = grad_p; A.grad_bary = grad_bary; A.grad_V = grad_V; A.out_status = out_status;
     A.eps_v = eps_v; A.eps_p = eps_p;
 
-    BwdLayout Lw = bwd_layout(m->nV, m->nF, nq, estimator, grad_V != nullptr);
+    BwdLayout Lw = bwd_layout(m->nV, m->nE, nq, estimator, grad_V != nullptr);
     void *ws = nullptr;
     bool own = false;
     if (r.workspace) {
@@ -603,13 +611,13 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.ntask = (int32_t *)(base + Lw.ntask);
     if (grad_V) {
         A.gacc = (float4 *)(base + Lw.gacc);
-        A.hacc = (float2 *)(base + Lw.hacc);
+        A.eacc = (float2 *)(base + Lw.eacc);
     }
     if (estimator == SG_EST_GFD) { A.cols = (float *)(base + Lw.cols); A.tasks = (int32_t *)(base + Lw.tasks); }
     cudaMemsetAsync(A.ntask, 0, 64, s);
     if (grad_V) {
         cudaMemsetAsync(A.gacc, 0, sizeof(float4) * (size_t)m->nV, s);
-        cudaMemsetAsync(A.hacc, 0, sizeof(float2) * 3 * (size_t)m->nF, s);
+        cudaMemsetAsync(A.eacc, 0, sizeof(float2) * (size_t)std::max<int64_t>(m->nE, 1), s);
     }
     const unsigned g128 = (unsigned)((nq + 127) / 128), g256 = (unsigned)((nq + 255) / 256);
     if (estimator == SG_EST_EP) {
@@ -630,7 +638,8 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         k_bwd_assemble<<<g256, 256, 0, s>>>(A);
     }
     if (grad_V) {
-        k_gradv_halfedges<<<(unsigned)((3 * m->nF + 255) / 256), 256, 0, s>>>(3 * m->nF, A.P, A.hacc, A.gacc);
+        if (m->nE > 0)
+            k_gradv_edges<<<(unsigned)((m->nE + 255) / 256), 256, 0, s>>>(m->nE, A.P, m->d_edges, A.eacc, A.gacc);
         k_gradv_flush<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, A.gacc, grad_V);
     }
     if (own) cudaFreeAsync(ws, s);

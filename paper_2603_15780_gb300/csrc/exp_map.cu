@@ -307,6 +307,8 @@ sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int
     m->n_mesh = n_mesh;
     cudaGetDevice(&m->device);
     m->face_off = H.face_off64;
+    m->nE = (int64_t)H.edges.size();
+    if (H.edges.empty()) H.edges.push_back(int2{0, 0});
     m->vert_off = H.vert_off64;
     m->lref = H.lref64;
     auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
@@ -318,6 +320,7 @@ sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int
               up((void **)&m->d_fv, H.fv.data(), sizeof(int4) * H.fv.size()) &&
               up((void **)&m->d_frm, H.frm.data(), sizeof(float4) * H.frm.size()) &&
               up((void **)&m->d_half, H.half.data(), sizeof(int4) * H.half.size()) &&
+              up((void **)&m->d_edges, H.edges.data(), sizeof(int2) * std::max<size_t>(H.edges.size(), 1)) &&
               up((void **)&m->d_V, H.V.data(), sizeof(float4) * H.V.size()) &&
               up((void **)&m->d_face_off, H.face_off.data(), sizeof(int32_t) * H.face_off.size()) &&
               up((void **)&m->d_lref, H.lref.data(), sizeof(float) * H.lref.size());
@@ -342,6 +345,7 @@ sg_status sg_mesh_destroy(sg_mesh *m) {
     cudaFree(m->d_fv);
     cudaFree(m->d_frm);
     cudaFree(m->d_half);
+    cudaFree(m->d_edges);
     cudaFree(m->d_V);
     cudaFree(m->d_face_off);
     cudaFree(m->d_lref);

@@ -53,6 +53,8 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
     out->fv.assign(nF, int4{0, 0, 0, 0});
     out->frm.assign(2 * nF, float4{0, 0, 0, 0});
     out->half.assign(6 * nF, int4{0, 0, 0, 0});
+    out->edges.clear();
+    out->edges.reserve((size_t)(1.5 * nF) + 16);
     out->V.assign(nV, float4{0, 0, 0, 0});
     out->face_off.assign(n_mesh + 1, 0);
     out->lref.assign(n_mesh, 0.f);
@@ -118,6 +120,7 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
         double lsum = 0.0;
         int64_t ne = 0;
         std::vector<int32_t> nbr(3 * nf, -1);
+        std::vector<int32_t> hedge(3 * nf, -1);  // (edge id << 1) | non-canonical, per half-edge
         for (size_t i = 0; i < E.size();) {
             size_t j = i + 1;
             while (j < E.size() && E[j].a == E[i].a && E[j].b == E[i].b) ++j;
@@ -133,6 +136,11 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
                 int64_t gq = f0 + q.f, gp = f0 + p.f;
                 nbr[3 * p.f + p.k] = (int32_t)((gq << 3) | (flip << 2) | q.k);
                 nbr[3 * q.f + q.k] = (int32_t)((gp << 3) | (flip << 2) | p.k);
+                int64_t hp = 3 * gp + p.k, hq = 3 * gq + q.k;
+                int64_t eid = (int64_t)out->edges.size();
+                out->edges.push_back(int2{(int)std::min(hp, hq), (int)std::max(hp, hq)});
+                hedge[3 * p.f + p.k] = (int32_t)((eid << 1) | (hp > hq ? 1 : 0));
+                hedge[3 * q.f + q.k] = (int32_t)((eid << 1) | (hq > hp ? 1 : 0));
             } else {
                 boundary[v0 + E[i].a] = 1;
                 boundary[v0 + E[i].b] = 1;
@@ -171,7 +179,7 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
                 };
                 int64_t h = 3 * (f0 + f) + k;
                 out->half[2 * h] = int4{bits((float)l), bits((float)cx), bits((float)cy), link(k1)};
-                out->half[2 * h + 1] = int4{link(k2), bits((float)ca), bits((float)sa), 0};
+                out->half[2 * h + 1] = int4{link(k2), bits((float)ca), bits((float)sa), hedge[3 * f + k]};
             }
         }
         out->lref64[m] = lsum / (double)ne;

@@ -19,11 +19,14 @@
 //   half  int4[6*nF]   32-byte half-edge record per (face f, local edge k), id h = 3f + k, in the
 //                      edge's own frame (origin at corner k, x along the edge, the face on +y):
 //                      half[2h]   = { bits(l), bits(cx), bits(cy), linkR }
-//                      half[2h+1] = { linkL, bits(ca), bits(sa), 0 }
+//                      half[2h+1] = { linkL, bits(ca), bits(sa), edge }
 //                      l = |edge k|, (cx, cy) = corner k+2 (the apex), (ca, sa) = the edge's unit
 //                      direction in the face frame (edge frame -> face frame rotation); linkR /
 //                      linkL = (h' << 1) | flip for the twin half-edge across edge k+1 (apex side
-//                      B -> C) / edge k+2 (C -> A), -1 on the boundary.
+//                      B -> C) / edge k+2 (C -> A), -1 on the boundary; edge = (e << 1) | o for
+//                      an interior edge e (o = 1 when this half-edge is not e's canonical one,
+//                      the lower half-edge id), -1 on the boundary.
+//   edges int2[nE]     (canonical half-edge, twin half-edge) of each interior edge
 //   V     float4[nV]   vertex position (x,y,z); .w = total angle theta(x), negated for boundary
 //                      vertices (Sec. 4: theta = sum of incident corner angles)
 //   face_off int32[n_mesh+1], lref float[n_mesh] (mean edge length per mesh)
@@ -46,6 +49,8 @@ struct sg_mesh {
     int4 *d_fv = nullptr;
     float4 *d_frm = nullptr;
     int4 *d_half = nullptr;
+    int2 *d_edges = nullptr;
+    int64_t nE = 0;
     float4 *d_V = nullptr;
     int32_t *d_face_off = nullptr;
     float *d_lref = nullptr;
@@ -57,6 +62,7 @@ struct sg_mesh {
 // host-side builder (mesh_build.cpp); fills the host arrays, returns SG_OK or an error
 struct sg_host_mesh {
     std::vector<int4> rec, fv, half;
+    std::vector<int2> edges;
     std::vector<float4> frm;
     std::vector<float4> V;
     std::vector<int32_t> face_off;
