@@ -467,7 +467,7 @@ def main():
             "crossings_per_query": ncross / nq,
             "flag_fraction": {"near_vertex": float(((st & 4) != 0).mean()), "near_edge": float(((st & 8) != 0).mean()),
                               "fp64": float(((st & 32) != 0).mean())},
-            "gpu_launches": args.steps * 12,  # per step: 5 sort/scan + walk, EP, re-walk + chords + literal + assemble + grad_V flush
+            "gpu_launches": args.steps * 13,  # per step: 5 sort/scan + walk, EP, re-walk + chords + literal + assemble, grad_V edges + flush
             "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1

@@ -61,7 +61,7 @@ def test_vertex_gradient_on_klein_bottle_matches_central_differences():
     base = oracle.exp_map(oracle.Mesh(Xd, F), q.face, b, v)
     out = sg.exp_map(mesh, q.face, parity.as_f32(q.bary), parity.as_f32(q.v))
     flipped = (out["status"].cpu().numpy() & sg.ST_FLIPPED) != 0
-    assert flipped.mean() > 0.2
+    assert flipped.mean() > 0.1   # enough walks end across an odd number of flipped edges
     h = 1e-5
     for trial in range(2):
         dX = rng.normal(size=X.shape)
