@@ -58,7 +58,7 @@ def lib():
             L.om_mesh_theta.argtypes = [P, P, P]
             L.om_mesh_adjacency.argtypes = [P, P]
             L.om_exp_map.argtypes = [P, C.c_int64, P, P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P,
-                                     P, P, P, C.POINTER(_Opts), C.c_int]
+                                     P, P, P, P, P, C.POINTER(_Opts), C.c_int]
             L.om_ep_backward.argtypes = [P, C.c_int64, P, P, P, P, P, P, C.POINTER(_Opts), C.c_int]
             L.om_gfd_backward.argtypes = [P, C.c_int64, P, P, P, C.c_double, C.c_double, P, P, P, P,
                                           P, C.POINTER(_Opts), C.c_int]
@@ -122,9 +122,11 @@ def _opts(max_steps=0, path_cap=0, tau_snap=0.0, tau_near=0.0):
 def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, *, max_steps=0, tau_snap=0.0,
             tau_near=0.0, path_cap=0, threads=0):
     """Batch exponential map (forward).  Returns a dict of numpy arrays:
-    face, bary, pos, dir, w (if given), status, ncross, nvert, hash, margin, path (if
-    path_cap > 0).  tau_snap/tau_near are relative to the mesh's mean edge length
-    (defaults 1e-12 and 1e-4)."""
+    face, bary, pos, dir, w (if given), status, ncross, nvert, hash, margin, and when
+    path_cap > 0 the traced geodesic: path [nq, path_cap] (faces in the order the walk enters
+    them, -1 past the end), path_pt [nq, path_cap, 3] (the point where it enters each), path_len
+    [nq] (faces entered, which may exceed path_cap).  tau_snap/tau_near are relative to the
+    mesh's mean edge length (defaults 1e-12 and 1e-4)."""
     face = np.ascontiguousarray(face, dtype=np.int32)
     nq = len(face)
     bary = _f64(bary, (nq, 3))
@@ -146,11 +148,14 @@ def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, *, max_steps=0, tau_
         out["w"] = np.zeros((nq, nw, 3))
     if path_cap:
         out["path"] = np.zeros((nq, path_cap), np.int32)
+        out["path_pt"] = np.zeros((nq, path_cap, 3))
+        out["path_len"] = np.zeros(nq, np.int32)
     o = _opts(max_steps, path_cap, tau_snap, tau_near)
     lib().om_exp_map(mesh._h, nq, _p(face), _p(bary), _p(v), _p(ln), nw, _p(w), _p(out["face"]),
                      _p(out["bary"]), _p(out["pos"]), _p(out["dir"]), _p(out.get("w")),
                      _p(out["status"]), _p(out["ncross"]), _p(out["nvert"]), _p(out["hash"]),
-                     _p(out["margin"]), _p(out.get("path")), C.byref(o), threads)
+                     _p(out["margin"]), _p(out.get("path")), _p(out.get("path_pt")), _p(out.get("path_len")),
+                     C.byref(o), threads)
     return out
 
 

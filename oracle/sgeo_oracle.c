@@ -253,19 +253,25 @@ typedef struct {
     uint64_t hash;
     double margin;     /* min line-to-vertex distance / l_ref over visited faces */
     int32_t *path; int32_t path_cap, path_len;
+    double *path_pt;   /* optional: the 3-D point at which the walk entered each recorded face */
 } om_rec;
-
-static inline void rec_face(om_rec *r, int64_t f) {
-    r->hash ^= (uint64_t)(uint32_t)f;
-    r->hash *= 0x100000001b3ULL;
-    if (r->path && r->path_len < r->path_cap) r->path[r->path_len] = (int32_t)f;
-    r->path_len++;
-}
 
 static void bary_point(const om_mesh *m, int64_t f, const double *b, double *p) {
     const int32_t *t = m->F + 3 * f;
     p[0] = p[1] = p[2] = 0.0;
     for (int k = 0; k < 3; ++k) vaxpy(p, b[k], VX(m, t[k]));
+}
+
+/* the walk enters face s->f at barycentric point s->b: hash it and, when tracing, record the
+ * face and the point (the polyline of the traced geodesic is these points, then the end point) */
+static inline void rec_face(om_rec *r, const om_mesh *m, const om_state *s) {
+    r->hash ^= (uint64_t)(uint32_t)s->f;
+    r->hash *= 0x100000001b3ULL;
+    if (r->path && r->path_len < r->path_cap) {
+        r->path[r->path_len] = (int32_t)s->f;
+        if (r->path_pt) bary_point(m, s->f, s->b, r->path_pt + 3 * r->path_len);
+    }
+    r->path_len++;
 }
 
 /* unit vector in the plane spanned by u and h, at angle a from u toward h's side */
@@ -303,7 +309,7 @@ static void unfold_apply(const om_unfold *U, double *x) {
 static void om_walk(const om_mesh *m, om_state *s, int nw, double *w, const om_opts *o, om_rec *r) {
     const double snap = o->tau_snap * m->lref, near = o->tau_near * m->lref;
     r->margin = INFINITY;
-    rec_face(r, s->f);
+    rec_face(r, m, s);
     while (1) {
         if (r->nsteps >= o->max_steps) { r->status |= OST_MAX_STEPS; return; }
         r->nsteps++;
@@ -437,7 +443,7 @@ static void om_walk(const om_mesh *m, om_state *s, int nw, double *w, const om_o
             for (int i = 0; i < 3; ++i) s->b[i] = i == cc ? 1.0 : 0.0;
             s->at_corner = cc;
             s->entry_opp = -1;
-            rec_face(r, fexit);
+            rec_face(r, m, s);
             continue;
         }
         /* ---------------- edge crossing: Alg. transport_over_edge */
@@ -465,7 +471,7 @@ static void om_walk(const om_mesh *m, om_state *s, int nw, double *w, const om_o
         s->entry_opp = gz;
         s->at_corner = -1;
         r->ncross++;
-        rec_face(r, g);
+        rec_face(r, m, s);
     }
 }
 
@@ -555,7 +561,8 @@ void om_exp_map(const om_mesh *m, int64_t nq, const int32_t *face, const double 
                 const double *length, int32_t nw, const double *w,
                 int32_t *out_face, double *out_bary, double *out_pos, double *out_dir, double *out_w,
                 uint32_t *out_status, int32_t *out_ncross, int32_t *out_nvert, uint64_t *out_hash,
-                double *out_margin, int32_t *out_path, const om_opts *opts, int nthreads) {
+                double *out_margin, int32_t *out_path, double *out_path_pt, int32_t *out_path_len,
+                const om_opts *opts, int nthreads) {
     om_opts o;
     default_opts(opts, &o);
     if (nw > 8) nw = 8;
@@ -583,9 +590,13 @@ void om_exp_map(const om_mesh *m, int64_t nq, const int32_t *face, const double 
             int32_t *pp = out_path + (int64_t)o.path_cap * i;
             for (int k = 0; k < o.path_cap; ++k) pp[k] = -1;
             r.path = pp; r.path_cap = o.path_cap;
+            r.path_pt = out_path_pt ? out_path_pt + 3 * (int64_t)o.path_cap * i : NULL;
+            if (r.path_pt) for (int k = 0; k < 3 * o.path_cap; ++k) r.path_pt[k] = 0.0;
             r.hash = 0xcbf29ce484222325ULL;
+            if (out_path_len) out_path_len[i] = 0;
             if (om_init(m, face[i], bary + 3 * i, v + 3 * i, length ? length + i : NULL, nw, w ? w + 3 * nw * i : NULL, wl, &s, &r.status)) continue;
-            om_walk(m, &s, nw, wl, &o, &r);
+            if (s.L > 0.0) om_walk(m, &s, nw, wl, &o, &r);  /* Exp_p(0) = p: no face sequence */
+            if (out_path_len) out_path_len[i] = r.path_len;
         }
     }
 }

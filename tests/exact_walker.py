@@ -59,14 +59,17 @@ class Polycube:
         assert len(nz) == 1, "fold edge must be axis-aligned"
         return tuple(Q(0) if c == 0 else Q(1 if c > 0 else -1) for c in u)
 
-    def walk(self, face, bary, d, t_total, max_steps=10000):
+    def walk(self, face, bary, d, t_total, max_steps=10000, points=False):
         """Walk from point sum(bary * corners) on `face` along d for parameter t_total
-        (length = t_total * |d|).  Returns (faces, end_point) or None on a vertex hit."""
+        (length = t_total * |d|).  Returns (faces, end_point) or None on a vertex hit; with
+        points=True, (faces, end_point, entry_points): the exact point at which the walk
+        enters each face of `faces` (the start point, then each edge crossing)."""
         f = face
         p = tuple(sum(Q(b) * self.X[i][c] for b, i in zip(bary, self.F[f])) for c in range(3))
         d = tuple(Q(x) for x in d)
         t_rem = Q(t_total)
         faces = [f]
+        pts = [p]
         entry = None
         for _ in range(max_steps):
             best = None
@@ -98,14 +101,14 @@ class Polycube:
                 return None
             t, s, a, b = best
             if t >= t_rem:
-                return faces, _add(p, d, t_rem)
+                return (faces, _add(p, d, t_rem), pts) if points else (faces, _add(p, d, t_rem))
             if s == 0 or s == 1:
                 return None  # exact vertex hit
             p = _add(p, d, t)
             t_rem -= t
             nbrs = [g for g in self.edge_faces[frozenset((a, b))] if g != f]
             if not nbrs:
-                return faces, p  # boundary (closed polycubes have none)
+                return (faces, p, pts) if points else (faces, p)  # boundary (closed polycubes have none)
             g = nbrs[0]
             if self.axis[g] != self.axis[f] or self.X[self.F[g][0]][self.axis[g]] != self.X[tri[0]][self.axis[f]]:
                 e = _sub(self.X[b], self.X[a])
@@ -118,4 +121,5 @@ class Polycube:
             f = g
             entry = frozenset((a, b))
             faces.append(f)
+            pts.append(p)
         return None

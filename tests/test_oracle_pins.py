@@ -117,10 +117,10 @@ def test_polycube_exact_face_sequences(cells):
     qs = _rational_queries(pc, 150, rng)
     matched = 0
     for f, bary, d, t in qs:
-        ex = pc.walk(f, bary, d, t)
+        ex = pc.walk(f, bary, d, t, points=True)
         if ex is None:
             continue
-        faces, pend = ex
+        faces, pend, pts = ex
         v = np.array([float(x * t) for x in d])
         out = oracle.exp_map(m, [f], [[float(b) for b in bary]], [v], path_cap=4096)
         if out["status"][0] & (oracle.NEAR_VERTEX | oracle.NEAR_EDGE):
@@ -128,10 +128,55 @@ def test_polycube_exact_face_sequences(cells):
         path = out["path"][0]
         path = list(path[path >= 0])
         assert path == faces
+        assert out["path_len"][0] == len(faces)
         assert out["hash"][0] == oracle.fnv_hash(faces)
         assert np.abs(out["pos"][0] - np.array([float(c) for c in pend])).max() < 1e-12
+        # the traced polyline: the exact entry point of every face
+        exact = np.array([[float(c) for c in q] for q in pts])
+        assert np.abs(out["path_pt"][0, :len(faces)] - exact).max() < 1e-11   # FP64 rounding over the walk
         matched += 1
     assert matched > 100
+
+
+def test_traced_polyline_has_the_walked_length_and_crosses_shared_edges():
+    """Geodesic tracing (the by-product of Sec. 1 and Sec. 4): inside each face the straightest
+    geodesic is a straight segment, so the traced polyline (entry points, then the end point) is
+    exactly L long, and each entry point after the first lies on the edge (or, after a vertex
+    hit, the vertex) that the previous face and the entered face share."""
+    rng = np.random.default_rng(17)
+    X, F = meshgen.icosphere(3, 0.01, rng)
+    m = oracle.Mesh(X, F)
+    q = meshgen.sample_queries(X, F, 300, rng, 0.0, 2.5, 0)
+    out = oracle.exp_map(m, q.face, q.bary, q.v, path_cap=512)
+    L = np.linalg.norm(q.v, axis=1)
+    checked = 0
+    for i in range(len(L)):
+        n = out["path_len"][i]
+        if out["status"][i] & oracle.INVALID or n > 512:
+            continue
+        if L[i] == 0:
+            assert n == 0
+            continue
+        faces, pts = out["path"][i, :n], out["path_pt"][i, :n]
+        p0 = (q.bary[i][:, None] * X[F[q.face[i]]]).sum(0)
+        assert np.abs(pts[0] - p0).max() < 1e-14
+        poly = np.concatenate([pts, out["pos"][i][None]])
+        length = np.linalg.norm(np.diff(poly, axis=0), axis=1).sum()
+        assert abs(length - L[i]) <= 1e-12 * max(L[i], 1.0), (i, length, L[i])
+        for k in range(1, n):
+            shared = set(F[faces[k - 1]]) & set(F[faces[k]])
+            if faces[k] == faces[k - 1]:
+                shared = set(F[faces[k]])
+            a = X[sorted(shared)]
+            if len(shared) == 2:
+                e = a[1] - a[0]
+                t = np.clip(np.dot(pts[k] - a[0], e) / np.dot(e, e), 0.0, 1.0)
+                dist = np.linalg.norm(a[0] + t * e - pts[k])
+            else:  # vertex hit: the entry point is one of the shared vertices
+                dist = np.linalg.norm(a - pts[k], axis=1).min()
+            assert dist < 1e-12, (i, k, dist)
+        checked += 1
+    assert checked > 250
 
 
 def test_cube_worked_examples():
