@@ -166,6 +166,58 @@ def flat_grid(n: int, rng: np.random.Generator | None = None, jitter: float = 0.
     return X, F.astype(np.int32)
 
 
+def cut_hole(X, F, inside):
+    """Remove the faces whose centroid satisfies inside(centroid) (a boolean function of [k,3]
+    points) and drop unused vertices.  Returns (X, F)."""
+    return _compact(X, F[~inside(X[F].mean(1))])
+
+
+def remove_faces(X, F, frac: float, rng: np.random.Generator):
+    """Remove about frac * |F| random faces while keeping the mesh manifold in the sense of
+    Sec. 4 (every vertex keeps one connected fan): a face is removed only if, for each of its
+    vertices, the remaining incident faces still form one fan (connected through shared
+    edges at that vertex) and at least one remains.  Returns (X, F) without unused vertices."""
+    nF = len(F)
+    alive = np.ones(nF, bool)
+    inc = [[] for _ in range(len(X))]
+    for f, t in enumerate(F):
+        for v in t:
+            inc[v].append(f)
+
+    def one_fan(v, drop):
+        fs = [f for f in inc[v] if alive[f] and f != drop]
+        if not fs:
+            return False
+        # union through shared edges (v, u)
+        seen = {fs[0]}
+        stack = [fs[0]]
+        while stack:
+            f = stack.pop()
+            others = set(F[f]) - {v}
+            for g in fs:
+                if g not in seen and len(others & (set(F[g]) - {v})) == 1:
+                    seen.add(g)
+                    stack.append(g)
+        return len(seen) == len(fs)
+
+    target = int(frac * nF)
+    removed = 0
+    for f in rng.permutation(nF):
+        if removed >= target:
+            break
+        if all(one_fan(v, f) for v in F[f]):
+            alive[f] = False
+            removed += 1
+    return _compact(X, F[alive])
+
+
+def _compact(X, F):
+    used = np.unique(F)
+    remap = -np.ones(len(X), np.int64)
+    remap[used] = np.arange(len(used))
+    return X[used], remap[F].astype(np.int32)
+
+
 def folded_strip(nx: int, ny: int, width: float, height: float, folds, rng=None, jitter=0.0):
     """A planar grid strip [0,width] x [0,height] folded along vertical grid lines.
     `folds` is a list of (column index, angle) pairs: the part of the strip right of

@@ -26,6 +26,7 @@ _lib = None
 # per-query status bits (same meaning as the library's status word)
 BOUNDARY, MAX_STEPS, NEAR_VERTEX, NEAR_EDGE, VERTEX_HIT = 1, 2, 4, 8, 16
 START_ON_EDGE, INVALID = 64, 128
+HOLE = 2048          # hole avoidance traced along the boundary (boundary_mode=1)
 
 
 def build(force: bool = False) -> str:
@@ -41,7 +42,7 @@ def build(force: bool = False) -> str:
 
 class _Opts(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("path_cap", C.c_int32), ("tau_snap", C.c_double),
-                ("tau_near", C.c_double)]
+                ("tau_near", C.c_double), ("boundary_mode", C.c_int32)]
 
 
 def lib():
@@ -115,18 +116,19 @@ class Mesh:
         return a
 
 
-def _opts(max_steps=0, path_cap=0, tau_snap=0.0, tau_near=0.0):
-    return _Opts(max_steps, path_cap, tau_snap, tau_near)
+def _opts(max_steps=0, path_cap=0, tau_snap=0.0, tau_near=0.0, boundary_mode=0):
+    return _Opts(max_steps, path_cap, tau_snap, tau_near, boundary_mode)
 
 
 def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, *, max_steps=0, tau_snap=0.0,
-            tau_near=0.0, path_cap=0, threads=0):
+            tau_near=0.0, path_cap=0, boundary_mode=0, threads=0):
     """Batch exponential map (forward).  Returns a dict of numpy arrays:
     face, bary, pos, dir, w (if given), status, ncross, nvert, hash, margin, and when
     path_cap > 0 the traced geodesic: path [nq, path_cap] (faces in the order the walk enters
     them, -1 past the end), path_pt [nq, path_cap, 3] (the point where it enters each), path_len
     [nq] (faces entered, which may exceed path_cap).  tau_snap/tau_near are relative to the
-    mesh's mean edge length (defaults 1e-12 and 1e-4)."""
+    mesh's mean edge length (defaults 1e-12 and 1e-4).  boundary_mode 0 stops at the boundary
+    (Sec. 4, original rule), 1 applies hole avoidance (status HOLE when it engaged)."""
     face = np.ascontiguousarray(face, dtype=np.int32)
     nq = len(face)
     bary = _f64(bary, (nq, 3))
@@ -150,7 +152,7 @@ def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, *, max_steps=0, tau_
         out["path"] = np.zeros((nq, path_cap), np.int32)
         out["path_pt"] = np.zeros((nq, path_cap, 3))
         out["path_len"] = np.zeros(nq, np.int32)
-    o = _opts(max_steps, path_cap, tau_snap, tau_near)
+    o = _opts(max_steps, path_cap, tau_snap, tau_near, boundary_mode)
     lib().om_exp_map(mesh._h, nq, _p(face), _p(bary), _p(v), _p(ln), nw, _p(w), _p(out["face"]),
                      _p(out["bary"]), _p(out["pos"]), _p(out["dir"]), _p(out.get("w")),
                      _p(out["status"]), _p(out["ncross"]), _p(out["nvert"]), _p(out["hash"]),

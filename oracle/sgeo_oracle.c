@@ -53,6 +53,7 @@
 #define OST_VERTEX_HIT 16u
 #define OST_START_ON_EDGE 64u
 #define OST_INVALID 128u
+#define OST_HOLE 2048u     /* hole avoidance traced along the boundary */
 
 typedef struct om_mesh {
     int64_t nV, nF;
@@ -69,6 +70,7 @@ typedef struct om_opts {
     int32_t path_cap;   /* entries per query in out_path (0: none) */
     double tau_snap;    /* vertex snap radius / l_ref */
     double tau_near;    /* near-vertex / near-edge flag radius / l_ref */
+    int32_t boundary_mode; /* 0: stop at the boundary (Sec. 4, original rule); 1: hole avoidance */
 } om_opts;
 
 /* ------------------------------------------------------------------ small vector ops */
@@ -302,6 +304,176 @@ static void unfold_apply(const om_unfold *U, double *x) {
 }
 
 /*
+ * Hole avoidance (Sec. 4 "Straightest geodesics": rather than stopping at the boundary, trace
+ * along it and resume the straightest walk as soon as possible with the last straightest
+ * direction; App. transport_over_vertex / transport_over_edge, hole-avoidance branches).
+ * The walker sits on boundary vertex v0 = corner c of face s->f.  D is the direction it had
+ * when it reached the boundary (3-D, unit) and n0 the normal of the face it was in; carried
+ * vector q has signed angle phi[q] to D about n0 and length wl[q].
+ * Readings (the paper describes transport_error but does not define it):
+ *   - a face f around v0 receives D when D, projected onto f's plane, points strictly into
+ *     f's corner at v0; its error is |<D, n_f>|, the sine of D's angle to the plane; the
+ *     receiving face of least error is taken and the walk resumes from v0 inside it;
+ *   - when no face receives D, the walk follows the boundary to the next boundary vertex,
+ *     spending the edge's length, and tries again there: it keeps its sense along the
+ *     boundary (the edge it did not arrive by); at a vertex hit directly by the ray it takes
+ *     the boundary edge whose unit direction has the larger dot product with D.  If the
+ *     length runs out on an edge the walk ends there, with D projected onto that face as its
+ *     direction;
+ *   - carried vectors keep their signed angle to the direction;
+ *   - a decision closer than tau_near (a wedge sine, the difference of the two least errors,
+ *     or of the two edge cosines) is flagged NEAR_VERTEX.
+ * Returns 1 when the walk resumes (s on the corner of the receiving face), 0 when it ended.
+ */
+static int om_hole(const om_mesh *m, om_state *s, int c, int32_t came_from, int nw, double *w,
+                   const double *phi, const double *wl, const double *D, const om_opts *o, om_rec *r) {
+    const double tau = o->tau_near;
+    int flip_ref = 0;   /* orientation of s->f relative to the face the boundary was reached in */
+    r->status |= OST_HOLE;
+    while (1) {
+        const int64_t f0 = s->f;
+        const int32_t v0 = m->F[3 * f0 + c];
+        const double *x0 = VX(m, v0);
+        int64_t fan[512];
+        int fflip[512], nf = 0;
+        int64_t bface[2];
+        int32_t bvert[2];
+        int bflip[2], nb = 0;
+        fan[nf] = f0; fflip[nf] = 0; nf++;
+        for (int dir = 0; dir < 2; ++dir) {
+            int64_t cur = f0;
+            int cc = c, fl = 0;
+            int opp = dir == 0 ? (cc + 2) % 3 : (cc + 1) % 3;  /* the edge (v0, corner 3-cc-opp) */
+            for (int guard = 0; guard < 512; ++guard) {
+                const int32_t vs = m->F[3 * cur + (3 - cc - opp)];
+                const int64_t g = m->adj[3 * cur + opp];
+                if (g < 0) {
+                    if (nb < 2) { bface[nb] = cur; bvert[nb] = vs; bflip[nb] = fl; nb++; }
+                    break;
+                }
+                if (g == f0 || nf >= 512) break;
+                const int cg = corner_of(m, g, v0), sg = corner_of(m, g, vs), cs = corner_of(m, cur, vs);
+                /* a consistent orientation lists the shared edge in opposite directions */
+                if ((((cc + 1) % 3) == cs) == (((cg + 1) % 3) == sg)) fl ^= 1;
+                fan[nf] = g; fflip[nf] = fl; nf++;
+                cur = g; cc = cg; opp = sg;
+            }
+        }
+        /* the receiving face of least error */
+        int best = -1;
+        double best_err = INFINITY, second = INFINITY, bu[3] = {0, 0, 0};
+        for (int i = 0; i < nf; ++i) {
+            const int64_t g = fan[i];
+            const int cg = corner_of(m, g, v0);
+            double ng[3], u[3], ea[3], eb[3], t[3];
+            face_normal(m, g, ng);
+            vcopy(u, D);
+            vaxpy(u, -vdot(D, ng), ng);
+            const double lu = vnorm(u);
+            if (!(lu > 1e-12)) continue;
+            vscale(u, 1.0 / lu);
+            vsub(VX(m, m->F[3 * g + (cg + 1) % 3]), x0, ea);
+            vsub(VX(m, m->F[3 * g + (cg + 2) % 3]), x0, eb);
+            vcross(ea, u, t);
+            const double sa = vdot(t, ng) / vnorm(ea);
+            vcross(u, eb, t);
+            const double sb = vdot(t, ng) / vnorm(eb);
+            const double mg = fmin(sa, sb);
+            if (fabs(mg) < tau) r->status |= OST_NEAR_VERTEX;
+            if (!(mg > 0.0)) continue;
+            const double err = fabs(vdot(D, ng));
+            if (err < best_err) { second = best_err; best_err = err; best = i; vcopy(bu, u); }
+            else if (err < second) second = err;
+        }
+        if (best >= 0) {
+            if (second - best_err < tau) r->status |= OST_NEAR_VERTEX;
+            const int64_t g = fan[best];
+            const int cg = corner_of(m, g, v0);
+            double ng[3], cu[3];
+            face_normal(m, g, ng);
+            if (flip_ref ^ fflip[best]) vscale(ng, -1.0);
+            vcross(ng, bu, cu);
+            for (int q = 0; q < nw; ++q)
+                for (int i = 0; i < 3; ++i) w[3 * q + i] = wl[q] * (cos(phi[q]) * bu[i] + sin(phi[q]) * cu[i]);
+            s->f = g;
+            for (int i = 0; i < 3; ++i) s->b[i] = i == cg ? 1.0 : 0.0;
+            vcopy(s->d, bu);
+            s->at_corner = cg;
+            s->entry_opp = -1;
+            rec_face(r, m, s);
+            return 1;
+        }
+        /* no face receives D: follow the boundary edge that agrees best with D */
+        if (nb == 0) { r->status |= OST_BOUNDARY; return 0; }
+        int k = 0;
+        double dk[2] = {-INFINITY, -INFINITY};
+        for (int i = 0; i < nb; ++i) {
+            double e[3];
+            vsub(VX(m, bvert[i]), x0, e);
+            dk[i] = vdot(D, e) / vnorm(e);
+        }
+        if (nb == 2) {
+            if (came_from >= 0) {
+                k = bvert[0] == came_from ? 1 : 0;
+            } else {
+                k = dk[1] > dk[0] ? 1 : 0;
+                if (fabs(dk[1] - dk[0]) < tau) r->status |= OST_NEAR_VERTEX;
+            }
+        }
+        const int64_t fb = bface[k];
+        const int cb = corner_of(m, fb, v0), co = corner_of(m, fb, bvert[k]);
+        flip_ref ^= bflip[k];
+        if (fb != s->f) {
+            s->f = fb;
+            for (int i = 0; i < 3; ++i) s->b[i] = i == cb ? 1.0 : 0.0;
+            rec_face(r, m, s);
+        }
+        if (r->nsteps >= o->max_steps) {
+            r->status |= OST_MAX_STEPS;
+            for (int i = 0; i < 3; ++i) s->b[i] = i == cb ? 1.0 : 0.0;
+            return 0;
+        }
+        r->nsteps++;
+        double e[3];
+        vsub(VX(m, bvert[k]), x0, e);
+        const double le = vnorm(e);
+        if (s->L <= le) {
+            const double t = s->L / le;
+            for (int i = 0; i < 3; ++i) s->b[i] = i == cb ? 1.0 - t : i == co ? t : 0.0;
+            s->L = 0.0;
+            double nbv[3], u[3], cu[3];
+            face_normal(m, fb, nbv);
+            vcopy(u, D);
+            vaxpy(u, -vdot(D, nbv), nbv);
+            if (vnorm(u) > 1e-12) vnormalize(u); else { vcopy(u, e); vscale(u, 1.0 / le); }
+            vcopy(s->d, u);
+            if (flip_ref) vscale(nbv, -1.0);
+            vcross(nbv, u, cu);
+            for (int q = 0; q < nw; ++q)
+                for (int i = 0; i < 3; ++i) w[3 * q + i] = wl[q] * (cos(phi[q]) * u[i] + sin(phi[q]) * cu[i]);
+            s->at_corner = -1;
+            s->entry_opp = -1;
+            return 0;
+        }
+        s->L -= le;
+        for (int i = 0; i < 3; ++i) s->b[i] = i == co ? 1.0 : 0.0;
+        c = co;
+        came_from = v0;
+    }
+}
+
+/* signed angles (about the normal n of the current face) and lengths of the carried vectors
+ * relative to the direction, kept through a hole-avoidance detour */
+static void carried_angles(const om_state *s, const double *n, int nw, const double *w, double *phi, double *wl) {
+    for (int q = 0; q < nw; ++q) {
+        double c[3];
+        vcross(s->d, w + 3 * q, c);
+        phi[q] = atan2(vdot(c, n), vdot(s->d, w + 3 * q));
+        wl[q] = vnorm(w + 3 * q);
+    }
+}
+
+/*
  * One query: Alg. "Parallel Geodesic Tracing CUDA Kernel" body with Alg. geodesic_step,
  * transport_over_edge and transport_over_vertex (black lines), FP64.
  * w (nw carried vectors, 3-D) is transported alongside.
@@ -377,8 +549,12 @@ static void om_walk(const om_mesh *m, om_state *s, int nw, double *w, const om_o
             r->status |= OST_VERTEX_HIT;
             r->nvert++;
             if (m->bnd[v0]) {
-                r->status |= OST_BOUNDARY;
                 for (int i = 0; i < 3; ++i) s->b[i] = i == hit ? 1.0 : 0.0;
+                if (!o->boundary_mode) { r->status |= OST_BOUNDARY; return; }
+                double phi[8], wl[8], D[3];
+                carried_angles(s, n, nw, w, phi, wl);
+                vcopy(D, s->d);
+                if (om_hole(m, s, hit, -1, nw, w, phi, wl, D, o, r)) continue;
                 return;
             }
             double half = 0.5 * m->theta[v0];
@@ -454,8 +630,30 @@ static void om_walk(const om_mesh *m, om_state *s, int nw, double *w, const om_o
         sj /= ss; sk /= ss;
         int64_t g = m->adj[3 * s->f + istar];
         if (g < 0) {
-            r->status |= OST_BOUNDARY;
             s->b[istar] = 0.0; s->b[j] = sj; s->b[k2] = sk;
+            if (!o->boundary_mode) { r->status |= OST_BOUNDARY; return; }
+            /* hole avoidance, edge branch: slide along the boundary edge toward the endpoint
+             * the direction points to (corner k2 when <d, x_k2 - x_j> >= 0, else corner j) */
+            double e[3];
+            vsub(x[k2], x[j], e);
+            const double le = vnorm(e), de = vdot(s->d, e) / le;
+            if (fabs(de) < o->tau_near) r->status |= OST_NEAR_VERTEX;
+            const int tgt = de >= 0.0 ? k2 : j;
+            const double dist = (tgt == k2 ? sj : sk) * le;   /* distance from the hit point to the target */
+            r->status |= OST_HOLE;
+            if (s->L <= dist) {
+                const double tmv = s->L / le;
+                if (tgt == k2) { s->b[k2] += tmv; s->b[j] -= tmv; } else { s->b[j] += tmv; s->b[k2] -= tmv; }
+                s->L = 0.0;
+                return;
+            }
+            s->L -= dist;
+            r->nsteps++;
+            for (int i = 0; i < 3; ++i) s->b[i] = i == tgt ? 1.0 : 0.0;
+            double phi[8], wl[8], D[3];
+            carried_angles(s, n, nw, w, phi, wl);
+            vcopy(D, s->d);
+            if (om_hole(m, s, tgt, t[tgt == k2 ? j : k2], nw, w, phi, wl, D, o, r)) continue;
             return;
         }
         int32_t vj = t[j], vk = t[k2];
@@ -540,6 +738,7 @@ static void default_opts(const om_opts *o, om_opts *out) {
     out->path_cap = o ? o->path_cap : 0;
     out->tau_snap = (o && o->tau_snap > 0) ? o->tau_snap : 1e-12;
     out->tau_near = (o && o->tau_near > 0) ? o->tau_near : 1e-4;
+    out->boundary_mode = o ? o->boundary_mode : 0;
 }
 
 /* single walk from a fully specified start; used by the batch entry and by GFD */

@@ -179,6 +179,107 @@ def test_traced_polyline_has_the_walked_length_and_crosses_shared_edges():
     assert checked > 250
 
 
+def _square_with_hole():
+    X, F = meshgen.flat_grid(21)
+    return meshgen.cut_hole(X, F, lambda c: (np.abs(c[:, 0] - 0.5) < 0.1) & (np.abs(c[:, 1] - 0.5) < 0.1))
+
+
+def test_hole_avoidance_closed_forms_on_a_square_with_a_hole():
+    """Hole avoidance (Sec. 4: trace along the boundary, resume with the last straightest
+    direction), on the unit square with the hole [0.4, 0.6]^2, where every case has a closed form:
+      - a ray into the hole's left side slides up that side to the corner (0.4, 0.6) and resumes
+        there with its own direction: end = c + (L - |q - p| - |c - q|) d;
+      - a ray that misses the hole is a straight line;
+      - a ray leaving through the right side of the square slides up to the corner (1, 1), where
+        no face receives it, keeps its sense along the boundary and slides left along the top:
+        end = (1 - r, 1) with r the length left at the corner;
+      - with boundary_mode 0 the same rays stop where they reach the boundary."""
+    X, F = _square_with_hole()
+    m = oracle.Mesh(X, F)
+    rng = np.random.default_rng(71)
+    n = 200
+    a = rng.uniform(0.1, 1.0, n)
+    d = np.stack([np.cos(a), np.sin(a), np.zeros(n)], 1)
+    p = np.stack([np.full(n, 0.2), rng.uniform(0.42, 0.58, n), np.zeros(n)], 1)
+    qy = p[:, 1] + 0.2 * np.tan(a)
+    L = np.full(n, 0.5)
+    # start faces and barycentrics of p
+    face, bary = _locate(X, F, p)
+    out = oracle.exp_map(m, face, bary, d * L[:, None], boundary_mode=1)
+    into = qy < 0.6
+    q = np.stack([np.full(n, 0.4), qy, np.zeros(n)], 1)
+    rem = L - np.linalg.norm(q - p, axis=1) - (0.6 - qy)
+    expect = np.where(into[:, None], np.array([0.4, 0.6, 0.0]) + rem[:, None] * d, p + L[:, None] * d)
+    ok = (out["status"] & (oracle.NEAR_VERTEX | oracle.NEAR_EDGE)) == 0
+    assert ok.mean() > 0.9 and into[ok].mean() > 0.3
+    assert np.abs(out["pos"] - expect)[ok].max() < 1e-12
+    assert np.all(((out["status"] & oracle.HOLE) != 0)[ok] == into[ok])
+    assert np.all((out["status"] & oracle.BOUNDARY) == 0)
+    stop = oracle.exp_map(m, face, bary, d * L[:, None])
+    assert np.all(((stop["status"] & oracle.BOUNDARY) != 0)[ok] == into[ok])
+    assert np.abs(stop["pos"] - np.where(into[:, None], q, expect))[ok].max() < 1e-12
+    # out through the right side of the square, around the corner (1, 1)
+    p2 = np.stack([np.full(n, 0.8), rng.uniform(0.7, 0.8, n), np.zeros(n)], 1)
+    a2 = rng.uniform(0.1, 0.6, n)
+    d2 = np.stack([np.cos(a2), np.sin(a2), np.zeros(n)], 1)
+    q2y = p2[:, 1] + 0.2 * np.tan(a2)
+    L2 = np.full(n, 0.8)
+    f2, b2 = _locate(X, F, p2)
+    o2 = oracle.exp_map(m, f2, b2, d2 * L2[:, None], boundary_mode=1)
+    r2 = L2 - np.linalg.norm(np.stack([np.full(n, 1.0), q2y, np.zeros(n)], 1) - p2, axis=1) - (1.0 - q2y)
+    use = (q2y < 1.0) & (r2 > 0) & (r2 < 1.0) & ((o2["status"] & (oracle.NEAR_VERTEX | oracle.NEAR_EDGE)) == 0)
+    assert use.mean() > 0.5
+    e2 = np.stack([1.0 - r2, np.ones(n), np.zeros(n)], 1)
+    assert np.abs(o2["pos"] - e2)[use].max() < 1e-12
+
+
+def _locate(X, F, p):
+    """Face and barycentrics of planar points p (z = 0) on a planar mesh, by brute force."""
+    A, B, C = X[F[:, 0], :2], X[F[:, 1], :2], X[F[:, 2], :2]
+    face = np.zeros(len(p), np.int32)
+    bary = np.zeros((len(p), 3))
+    for i, x in enumerate(p[:, :2]):
+        v0, v1, v2 = B - A, C - A, x - A
+        d00 = (v0 * v0).sum(1); d01 = (v0 * v1).sum(1); d11 = (v1 * v1).sum(1)
+        d20 = (v2 * v0).sum(1); d21 = (v2 * v1).sum(1)
+        den = d00 * d11 - d01 * d01
+        bv = (d11 * d20 - d01 * d21) / den
+        bw = (d00 * d21 - d01 * d20) / den
+        bu = 1 - bv - bw
+        k = np.nonzero((bu >= 0) & (bv >= 0) & (bw >= 0))[0][0]
+        face[i] = k
+        bary[i] = (bu[k], bv[k], bw[k])
+    return face, bary
+
+
+def test_hole_avoidance_on_a_sphere_with_holes():
+    """A sphere with 8% of its faces removed (every vertex keeps one fan, Sec. 4): with hole
+    avoidance no walk stops at the boundary, walks that never touch it are unchanged, and a walk
+    that does follows the same faces as the stopping walk up to the boundary."""
+    rng = np.random.default_rng(72)
+    X, F = meshgen.icosphere(3, 0.003, rng)
+    X, F = meshgen.remove_faces(X, F, 0.08, rng)
+    m = oracle.Mesh(X, F)
+    q = meshgen.sample_queries(X, F, 600, rng, 0.1, 3.0, 1)
+    stop = oracle.exp_map(m, q.face, q.bary, q.v, q.w, path_cap=512)
+    hole = oracle.exp_map(m, q.face, q.bary, q.v, q.w, path_cap=512, boundary_mode=1)
+    hit = (stop["status"] & oracle.BOUNDARY) != 0
+    assert hit.mean() > 0.2
+    assert not np.any(hole["status"] & oracle.BOUNDARY)
+    assert np.all(((hole["status"] & oracle.HOLE) != 0) == hit)
+    same = ~hit
+    for k in ("face", "pos", "dir", "w", "hash"):
+        assert np.array_equal(stop[k][same], hole[k][same]), k
+    for i in np.nonzero(hit)[0]:
+        n = min(stop["path_len"][i], 512)
+        assert np.array_equal(stop["path"][i, :n], hole["path"][i, :n])
+    # carried vectors stay unit and keep their angle to the direction
+    cw = np.einsum("ij,ij->i", hole["w"][:, 0], hole["dir"])
+    c0 = np.einsum("ij,ij->i", q.w[:, 0], q.v / np.linalg.norm(q.v, axis=1, keepdims=True))
+    assert np.abs(np.linalg.norm(hole["w"][:, 0], axis=1) - 1).max() < 1e-9
+    assert np.abs(cw - c0).max() < 1e-9
+
+
 def test_cube_worked_examples():
     """Hand-worked examples (tests/golden/cube_worked_examples.txt): one edge-crossing walk and
     two vertex hits at a cube corner, where theta = 3pi/2 and the straightest rule of Sec. 4
