@@ -61,6 +61,7 @@ typedef enum sg_status {
                                     (odd number of inconsistently oriented edges crossed) */
 #define SG_ST_NO_GRADV 1024u     /* (backward) no vertex-position gradient for this query (vertex
                                     hit or boundary stop: the map is not differentiable there) */
+#define SG_ST_HOLE 2048u         /* hole avoidance (boundary_mode 1) traced along the boundary */
 
 /* kernels */
 #define SG_KERNEL_AUTO 0
@@ -75,13 +76,27 @@ typedef struct sg_opts {
     int32_t blocks_per_sm;  /* persistent kernel residency; <= 0: as many as fit */
     int32_t fp64_escalate;  /* 1: re-evaluate near-vertex classification in FP64 (persistent only) */
     float tau_near;         /* flag radius / l_ref for NEAR_VERTEX, NEAR_EDGE and the FP64 band; <= 0: 1e-4 */
-    float tau_snap;         /* vertex-snap radius / l_ref; <= 0: 1e-6 */
+    float tau_snap;         /* vertex-snap radius / l_ref; <= 0: 1e-6 (precision 32), 1e-12 (64) */
     void *workspace;        /* optional device scratch (see sg_exp_map_workspace_size); NULL: the
                                library allocates stream-ordered scratch itself */
     size_t workspace_bytes;
     void *prof_events;      /* optional: pointer to two cudaEvent_t recorded on `stream` right
                                before and after the call's walk kernel (forward walk, or the
                                backward re-walk), for per-kernel timing; NULL: none */
+    int32_t boundary_mode;  /* 0: a walk stops on the boundary (Sec. 4, the original rule);
+                               1: hole avoidance (Sec. 4): trace along the boundary and resume
+                               with the last straightest direction as soon as a face receives
+                               it (SG_ST_HOLE).  Mode 1 runs on the persistent kernel with FP64
+                               classification; the plain kernel and sg_exp_map_trace reject it
+                               (SG_ERR_UNSUPPORTED). */
+    int32_t precision;      /* 32 (default): FP32 walk with FP64 classification near vertices;
+                               64: every quantity of the walk in FP64 (state, face shapes,
+                               frames, vertex angles), for inputs whose FP32 error exceeds the
+                               classification margins; persistent kernel, forward only (the
+                               trace, the backward, boundary_mode 1 and the plain kernel reject
+                               it with SG_ERR_UNSUPPORTED).  The first FP64 call on a mesh
+                               allocates and derives its FP64 geometry (synchronous cudaMalloc,
+                               88 B per face and 8 B per vertex, kept by the mesh). */
 } sg_opts;
 
 /* Fills `o` with the defaults described above. */
@@ -125,9 +140,38 @@ typedef struct sg_mesh_info {
     int32_t record_bytes;      /* bytes per face walk record */
     int64_t device_bytes;      /* total device memory held by the mesh */
     double l_ref_mean;         /* mean edge length of mesh 0 */
+    int64_t n_degenerate;      /* faces left degenerate by the last sg_mesh_update_vertices */
 } sg_mesh_info;
 
+/* Fills `info`.  After sg_mesh_update_vertices it reads the current l_ref and degenerate
+ * count back from the device (a synchronous copy that waits for the update). */
 sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info);
+
+/*
+ * sg_mesh_update_vertices -- move the vertices of a mesh to new positions, keeping its faces
+ * and adjacency, and re-derive on the device every geometric word of its walk records: the
+ * per-face intrinsic shape and 3-D frame, the half-edge records, the total angle theta(x) of
+ * each vertex and l_ref (Sec. 4 "Straightest geodesics": all of them are functions of the
+ * vertex positions; the adjacency and boundary flags depend on F only).  This serves
+ * optimisation of vertex positions with the grad_V output of sg_exp_map_backward, without a
+ * host round trip or a rebuild of the adjacency.
+ *   m       a mesh from sg_mesh_create*
+ *   V       device float32 [n_vertices][3] new positions, in the mesh's vertex order
+ *           (meshes of a batch concatenated, as at creation); read during the call's kernels
+ *   stream  cudaStream_t as void*; the work is enqueued on it and the host is not synchronised,
+ *           except by the first call on a mesh, which allocates O(n_vertices) FP64 scratch
+ *           (cudaMalloc) that the mesh keeps until sg_mesh_destroy.
+ * The records are rewritten in place: walks reading the mesh on other streams must be ordered
+ * before the call by the caller.  The arithmetic is that of sg_mesh_create (FP64, no
+ * multiply-add contraction), so an updated mesh walks like one created from the new positions;
+ * the FP64 sums (theta, l_ref) are accumulated in a different order, which can move their FP32
+ * values by one unit in the last place.
+ * A face that the new positions make zero-area or non-finite marks its mesh (its member of a
+ * batch) unusable: every query on it returns SG_ST_INVALID until a later update makes all of
+ * its faces valid again; sg_mesh_get_info reports the count.
+ * Errors: SG_ERR_INVALID_ARG (null mesh or V), SG_ERR_OOM (first-call scratch), SG_ERR_CUDA.
+ */
+sg_status sg_mesh_update_vertices(sg_mesh *m, const float *V, void *stream);
 
 /*
  * sg_exp_map_workspace_size -- bytes of device scratch sg_exp_map needs for nq queries
@@ -188,19 +232,58 @@ sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int32_t *mesh_i
 #define SG_EST_GFD 1  /* Eqs. jv, jp: geodesic finite differences */
 
 /*
- * sg_exp_map_backward -- vector-Jacobian products of the end point p' = Exp_p(v).
+ * sg_exp_map_trace -- the forward walk with the traced geodesic as an extra output.
+ * Straightest geodesics trace geodesics as a by-product of the exponential map (Sec. 1,
+ * Sec. 4 "Straightest geodesics"): inside a face the geodesic is a straight segment, so the
+ * ordered faces it enters and the points where it enters them, followed by the end point, are
+ * its polyline.  Same walk, inputs and end outputs as sg_exp_map without carried vectors, on
+ * the persistent kernel (opts.kernel only chooses whether queries are sorted: PLAIN disables
+ * the sort and the FP64 classification).
+ *   path_cap       entries stored per query (>= 0)
+ *   out_path_face  device int32 [nq][path_cap]: local ids of the faces entered, in order (the
+ *                  start face first; a vertex hit that leaves through the same face repeats
+ *                  it).  Entries past min(path_len, path_cap) are not written.
+ *   out_path_pt    device float32 [nq][path_cap][3] or NULL: the point where the walk enters
+ *                  each face (the start point, an edge crossing point, or the hit vertex)
+ *   out_path_len   device int32 [nq]: faces entered; above path_cap the path was truncated
+ *                  (0 for invalid and zero-length queries, which enter no face)
+ * The face sequence is the one that out_hash hashes.  Asynchronous on `stream`.
+ * Errors: as sg_exp_map.
+ */
+sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
+                           const float *bary, const float *v, const float *length, int32_t path_cap,
+                           int32_t *out_path_face, float *out_path_pt, int32_t *out_path_len, int32_t *out_face,
+                           float *out_bary, float *out_pos, float *out_dir, uint32_t *out_status,
+                           int32_t *out_ncross, uint64_t *out_hash, const sg_opts *opts, void *stream);
+
+/*
+ * sg_exp_map_backward -- vector-Jacobian products of the forward outputs (Sec. 4 "Gradient
+ * computation": the chain rule through Exp, with J^v, J^p from EP, Eq. proxy_func, or GFD,
+ * Eqs. jv, jp).
  *   estimator  SG_EST_EP or SG_EST_GFD; eps_v, eps_p the GFD steps (world units, > 0)
  *   mesh_id, face, bary, v   the forward inputs (device, as in sg_exp_map; L = |v|)
  *   end_face, end_bary, end_dir  the forward outputs for these queries (device)
  *   end_status the forward status words (device) or NULL (then SG_ST_FLIPPED is taken as 0,
  *              exact for orientable meshes)
- *   g_pos      device float32 [nq][3] upstream gradient dL/dp'
+ * Upstream gradients (device float32; all but g_pos may be NULL):
+ *   g_pos      [nq][3]  dL/dp' of the end point
+ *   g_bary     [nq][3]  dL/db' of the end barycentrics (e.g. when b' starts a next step): it
+ *                       enters as the tangent vector g_t with g_t . dp = sum_k g_bary_k db'_k
+ *   g_dir      [nq][3]  dL/dd' of the transported unit direction: differentiated with the
+ *                       rotation R = M_p' M_p^T of Eq. proxy_func held fixed (both estimators):
+ *                       grad_v += (I - d0 d0^T) R^T g_dir / |v|
+ *   n_w, g_w   [nq][n_w][3] dL/dw' of the carried vectors (0 <= n_w <= 4; g_w and grad_w
+ *                       both given or both NULL)
  * Outputs (device, caller-allocated, any may be NULL):
  *   grad_v     float32 [nq][3]  dL/dv (tangent to the start face)
  *   grad_p     float32 [nq][3]  dL/dp in the start face plane (zero for EP, Sec. 4)
  *   grad_bary  float32 [nq][3]  dL/db_k = <grad_p, x_k> (meaningful up to the simplex gauge)
- *   grad_V     float32 [nV][3]  dL/dX, ACCUMULATED (+=) over queries; the derivative of the
- *                               end point with the face sequence held fixed (see DESIGN)
+ *   grad_V     float32 [nV][3]  dL/dX, ACCUMULATED (+=) over queries: the derivative of the end
+ *                               point (and barycentrics) in the vertex positions with the face
+ *                               sequence held fixed; queries with a vertex hit or a boundary stop
+ *                               add nothing and get SG_ST_NO_GRADV
+ *   grad_w     float32 [nq][n_w][3]  dL/dw = R^T g_w (parallel transport is a rotation of the
+ *                               tangent planes for a fixed face sequence; exact)
  *   out_status uint32 [nq]      SG_ST_* of the extra walks (GFD) or of the re-walk
  * Asynchronous on `stream`.
  */
@@ -208,14 +291,15 @@ sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, 
                               int64_t nq, const int32_t *mesh_id, const int32_t *face,
                               const float *bary, const float *v, const int32_t *end_face,
                               const float *end_bary, const float *end_dir,
-                              const uint32_t *end_status, const float *g_pos,
+                              const uint32_t *end_status, const float *g_pos, const float *g_bary,
+                              const float *g_dir, int32_t n_w, const float *g_w,
                               float *grad_v, float *grad_p, float *grad_bary, float *grad_V,
-                              uint32_t *out_status, const sg_opts *o, void *stream);
+                              float *grad_w, uint32_t *out_status, const sg_opts *o, void *stream);
 
 /*
  * sg_exp_map_backward_workspace_size -- bytes of device scratch sg_exp_map_backward needs for
  * nq queries with `estimator` (SG_EST_*) and, if want_grad_V != 0, the vertex gradient: the
- * GFD column table (16 B per query) and swept-perturbation task list (12 B per query), and
+ * GFD column table (16 B per query) and literal-walk task list (12 B per query), and
  * a float4 accumulator per vertex for grad_V.  Pass it as o->workspace; without it the
  * library allocates stream-ordered scratch itself.
  */

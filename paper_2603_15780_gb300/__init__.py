@@ -33,7 +33,8 @@ EST_EP, EST_GFD = 0, 1
 
 EXPORTED = ["sg_opts_default", "sg_status_string", "sg_mesh_create", "sg_mesh_create_batched",
             "sg_mesh_destroy", "sg_mesh_get_info", "sg_exp_map_workspace_size", "sg_exp_map",
-            "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc", "sg_exp_map_backward_workspace_size"]
+            "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc", "sg_exp_map_backward_workspace_size",
+            "sg_mesh_update_vertices", "sg_exp_map_trace"]
 
 
 def status_names(st: int) -> list[str]:
@@ -53,12 +54,14 @@ class Opts(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("kernel", C.c_int32), ("sort", C.c_int32),
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("fp64_escalate", C.c_int32),
                 ("tau_near", C.c_float), ("tau_snap", C.c_float), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("prof_events", C.c_void_p)]
+                ("workspace_bytes", C.c_size_t), ("prof_events", C.c_void_p), ("boundary_mode", C.c_int32),
+                ("precision", C.c_int32)]
 
 
 class MeshInfo(C.Structure):
     _fields_ = [("n_vertices", C.c_int64), ("n_faces", C.c_int64), ("n_mesh", C.c_int32),
-                ("record_bytes", C.c_int32), ("device_bytes", C.c_int64), ("l_ref_mean", C.c_double)]
+                ("record_bytes", C.c_int32), ("device_bytes", C.c_int64), ("l_ref_mean", C.c_double),
+                ("n_degenerate", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -83,14 +86,18 @@ def lib():
             L.sg_mesh_create_batched.argtypes = [P, P, P, P, C.c_int32, C.POINTER(P)]
             L.sg_mesh_destroy.argtypes = [P]
             L.sg_mesh_get_info.argtypes = [P, C.POINTER(MeshInfo)]
+            L.sg_mesh_update_vertices.argtypes = [P, P, P]
             L.sg_exp_map_workspace_size.argtypes = [P, C.c_int64, C.POINTER(Opts), C.POINTER(C.c_size_t)]
             L.sg_exp_map.argtypes = [P, C.c_int64, P, P, P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P,
                                      C.POINTER(Opts), P]
             L.sg_exp_map_noalloc.argtypes = list(L.sg_exp_map.argtypes)
+            L.sg_exp_map_trace.argtypes = [P, C.c_int64, P, P, P, P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P,
+                                           C.POINTER(Opts), P]
             L.sg_exp_map_backward_workspace_size.argtypes = [P, C.c_int32, C.c_int64, C.c_int32,
                                                              C.POINTER(C.c_size_t)]
             L.sg_exp_map_backward.argtypes = [P, C.c_int32, C.c_float, C.c_float, C.c_int64, P, P, P, P,
-                                              P, P, P, P, P, P, P, P, P, P, C.POINTER(Opts), P]
+                                              P, P, P, P, P, P, P, C.c_int32, P, P, P, P, P, P, P,
+                                              C.POINTER(Opts), P]
             for f in EXPORTED:
                 if f not in ("sg_opts_default",):
                     getattr(L, f).restype = getattr(L, f).restype or C.c_int
@@ -178,6 +185,21 @@ class Mesh:
     def handle(self):
         return self._h
 
+    def update_vertices(self, V, stream=None):
+        """Move the vertices to V (float32 [n_vertices, 3], any device; same faces) and re-derive
+        the mesh geometry on the GPU with sg_mesh_update_vertices.  Enqueued on `stream` (default:
+        torch's current stream).  Returns the device copy of V that the call read; it is
+        recorded on the stream, so the caching allocator does not reuse it before the update ran."""
+        torch = _torch()
+        Vd = _dev(V, torch.float32, (-1, 3))
+        if Vd.shape[0] != self.n_vertices:
+            raise SgError(f"update_vertices: expected {self.n_vertices} vertices, got {Vd.shape[0]}")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().sg_mesh_update_vertices(self._h, _ptr(Vd), C.c_void_p(s.cuda_stream)),
+               "sg_mesh_update_vertices")
+        Vd.record_stream(s)
+        return Vd
+
     def info(self) -> MeshInfo:
         i = MeshInfo()
         _check(lib().sg_mesh_get_info(self._h, C.byref(i)), "sg_mesh_get_info")
@@ -248,6 +270,47 @@ def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, mesh_id=None, *, wan
     return out
 
 
+def exp_map_trace(mesh: Mesh, face, bary, v, length=None, mesh_id=None, *, path_cap: int = 64,
+                  want_points=True, want_hash=False, opts: Opts | None = None, workspace=None, stream=None,
+                  **opt_kw):
+    """sg_exp_map_trace on torch CUDA tensors: the exponential map plus the traced geodesic.
+    Returns dict(face, bary, pos, dir, status, ncross, hash (if want_hash), path_face [nq, cap],
+    path_pt [nq, cap, 3] (if want_points), path_len [nq]).  The polyline of query i is
+    path_pt[i, :path_len[i]] followed by pos[i] when path_len[i] <= path_cap; path entries
+    past path_len are not written (the tensors start as -1 / 0)."""
+    torch = _torch()
+    face = _dev(face, torch.int32)
+    nq = face.numel()
+    bary = _dev(bary, torch.float32, (nq, 3))
+    v = _dev(v, torch.float32, (nq, 3))
+    length = _dev(length, torch.float32, (nq,))
+    mesh_id = _dev(mesh_id, torch.int32, (nq,))
+    o = opts if opts is not None else default_opts(**opt_kw)
+    dev = face.device
+    out = {"face": torch.empty(nq, dtype=torch.int32, device=dev),
+           "bary": torch.empty(nq, 3, device=dev), "pos": torch.empty(nq, 3, device=dev),
+           "dir": torch.empty(nq, 3, device=dev), "status": torch.empty(nq, dtype=torch.int32, device=dev),
+           "ncross": torch.empty(nq, dtype=torch.int32, device=dev),
+           "path_face": torch.full((nq, path_cap), -1, dtype=torch.int32, device=dev),
+           "path_len": torch.empty(nq, dtype=torch.int32, device=dev)}
+    if want_points:
+        out["path_pt"] = torch.zeros(nq, path_cap, 3, device=dev)
+    if want_hash:
+        out["hash"] = torch.empty(nq, dtype=torch.int64, device=dev)
+    if workspace is None:
+        workspace = torch.empty(workspace_size(mesh, nq, o), dtype=torch.uint8, device=dev)
+    o.workspace = workspace.data_ptr()
+    o.workspace_bytes = workspace.numel()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().sg_exp_map_trace(mesh.handle, nq, _ptr(mesh_id), _ptr(face), _ptr(bary), _ptr(v), _ptr(length),
+                                path_cap, _ptr(out["path_face"]), _ptr(out.get("path_pt")), _ptr(out["path_len"]),
+                                _ptr(out["face"]), _ptr(out["bary"]), _ptr(out["pos"]), _ptr(out["dir"]),
+                                _ptr(out["status"]), _ptr(out["ncross"]), _ptr(out.get("hash")), C.byref(o),
+                                C.c_void_p(s.cuda_stream))
+    _check(rc, "sg_exp_map_trace")
+    return out
+
+
 def backward_workspace_size(mesh: Mesh, estimator, nq: int, want_grad_V: bool) -> int:
     est = {"ep": EST_EP, "gfd": EST_GFD}.get(estimator, estimator)
     n = C.c_size_t()
@@ -257,10 +320,12 @@ def backward_workspace_size(mesh: Mesh, estimator, nq: int, want_grad_V: bool) -
 
 
 def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_bary, end_dir, end_status, g_pos,
-                     mesh_id=None, *, eps_v=1e-4, eps_p=1e-4, want_grad_V=False,
-                     grad_V=None, opts: Opts | None = None, workspace=None, stream=None):
-    """sg_exp_map_backward.  estimator: "ep"/"gfd" or EST_*.  Returns dict(grad_v, grad_p,
-    grad_bary, grad_V (if requested; accumulated into `grad_V` when given), status)."""
+                     mesh_id=None, *, g_bary=None, g_dir=None, g_w=None, eps_v=1e-4, eps_p=1e-4,
+                     want_grad_V=False, grad_V=None, opts: Opts | None = None, workspace=None, stream=None):
+    """sg_exp_map_backward.  estimator: "ep"/"gfd" or EST_*.  Upstream gradients: g_pos (end
+    point), optional g_bary (end barycentrics), g_dir (end direction), g_w [nq, n_w, 3] (carried
+    vectors).  Returns dict(grad_v, grad_p, grad_bary, grad_w (if g_w), grad_V (if requested;
+    accumulated into `grad_V` when given), status)."""
     torch = _torch()
     est = {"ep": EST_EP, "gfd": EST_GFD}.get(estimator, estimator)
     face = _dev(face, torch.int32)
@@ -272,11 +337,20 @@ def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_bary, e
     end_status = _dev(end_status, torch.int32, (nq,))
     end_bary = _dev(end_bary, torch.float32, (nq, 3))
     g_pos = _dev(g_pos, torch.float32, (nq, 3))
+    g_bary = _dev(g_bary, torch.float32, (nq, 3))
+    g_dir = _dev(g_dir, torch.float32, (nq, 3))
+    n_w = 0
+    if g_w is not None:
+        g_w = _dev(g_w, torch.float32)
+        n_w = g_w.numel() // (3 * max(nq, 1))
+        g_w = g_w.reshape(nq, n_w, 3)
     mesh_id = _dev(mesh_id, torch.int32, (nq,))
     dev = face.device
     res = {"grad_v": torch.empty(nq, 3, device=dev), "grad_p": torch.empty(nq, 3, device=dev),
            "grad_bary": torch.empty(nq, 3, device=dev),
            "status": torch.empty(nq, dtype=torch.int32, device=dev)}
+    if n_w:
+        res["grad_w"] = torch.empty(nq, n_w, 3, device=dev)
     if want_grad_V or grad_V is not None:
         if grad_V is None:
             grad_V = torch.zeros(mesh.n_vertices, 3, device=dev)
@@ -290,8 +364,9 @@ def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_bary, e
     s = stream if stream is not None else torch.cuda.current_stream()
     rc = lib().sg_exp_map_backward(mesh.handle, est, eps_v, eps_p, nq, _ptr(mesh_id), _ptr(face), _ptr(bary),
                                    _ptr(v), _ptr(end_face), _ptr(end_bary), _ptr(end_dir), _ptr(end_status),
-                                   _ptr(g_pos), _ptr(res["grad_v"]), _ptr(res["grad_p"]),
-                                   _ptr(res["grad_bary"]), _ptr(res.get("grad_V")), _ptr(res["status"]),
+                                   _ptr(g_pos), _ptr(g_bary), _ptr(g_dir), n_w, _ptr(g_w if n_w else None),
+                                   _ptr(res["grad_v"]), _ptr(res["grad_p"]), _ptr(res["grad_bary"]),
+                                   _ptr(res.get("grad_V")), _ptr(res.get("grad_w")), _ptr(res["status"]),
                                    C.byref(o), C.c_void_p(s.cuda_stream))
     _check(rc, "sg_exp_map_backward")
     return res
@@ -301,9 +376,10 @@ def _autograd_function():
     import torch
 
     class ExpMap(torch.autograd.Function):
-        """pos = Exp_p(v) with p = (face, bary) on `mesh`; differentiable in v, bary and
-        (through `V`, the mesh's vertex tensor, if it requires grad) the vertex positions.
-        estimator: "ep" (Eq. proxy_func, grad for bary is zero) or "gfd" (Eqs. jv, jp)."""
+        """(pos, face, bary, dir, status) = Exp_p(v) with p = (face, bary) on `mesh`.
+        Differentiable outputs: pos, bary (so that the end point can start a next step) and dir;
+        inputs v, bary and (through `V`, the mesh's vertex tensor, if it requires grad) the vertex
+        positions.  estimator: "ep" (Eq. proxy_func, grad for bary is zero) or "gfd" (Eqs. jv, jp)."""
 
         @staticmethod
         def forward(ctx, mesh, face, bary, v, estimator="gfd", V=None, mesh_id=None, eps=1e-4):
@@ -313,18 +389,55 @@ def _autograd_function():
                                   out["status"], mesh_id if mesh_id is not None else torch.empty(0))
             ctx.has_V = V is not None
             ctx.mark_non_differentiable(out["face"], out["status"])
+            ctx.set_materialize_grads(False)
             return out["pos"], out["face"], out["bary"], out["dir"], out["status"]
 
         @staticmethod
-        def backward(ctx, g_pos, _gf, _gb, _gd, _gs):
+        def backward(ctx, g_pos, _gf, g_bary, g_dir, _gs):
             face, bary, v, ef, eb, ed, es, mid = ctx.saved_tensors
+            if g_pos is None:
+                g_pos = torch.zeros(face.numel(), 3, device=face.device)
             r = exp_map_backward(ctx.mesh, ctx.estimator, face, bary, v, ef, eb, ed, es, g_pos.contiguous(),
-                                 mesh_id=mid if mid.numel() else None, eps_v=ctx.eps, eps_p=ctx.eps,
+                                 mesh_id=mid if mid.numel() else None,
+                                 g_bary=None if g_bary is None else g_bary.contiguous(),
+                                 g_dir=None if g_dir is None else g_dir.contiguous(),
+                                 eps_v=ctx.eps, eps_p=ctx.eps,
                                  want_grad_V=ctx.needs_input_grad[5] and ctx.has_V)
             gV = r.get("grad_V")
             return None, None, r["grad_bary"], r["grad_v"], None, gV, None, None
 
     return ExpMap
+
+
+def exp_map_steps(mesh: Mesh, face, bary, field, K: int, estimator="gfd", V=None, mesh_id=None, eps=1e-4,
+                  x0=None, return_steps=False):
+    """The K-step exponential map of the flow-matching application (Sec. 5, Eq. fmobj):
+    p_{k+1} = Exp_{p_k}(field(x_k, k) / K) for k = 0..K-1, with the vector field re-evaluated at
+    each intermediate point x_k so that the trajectory can turn.  `field(x, k)` maps positions
+    [nq, 3] to ambient vectors [nq, 3] (projected onto each face by the walk).  Every step is one
+    differentiable ExpMap call; its end (face, bary) starts the next step and carries gradients
+    back through grad_bary (GFD's J^p).  x0 defaults to the start positions, taken from a
+    zero-length walk (not differentiated).  Returns (pos, face, bary, status) of the last step,
+    and with return_steps=True also the list of per-step dicts (face, bary, v, end_face,
+    end_bary, end_dir, status; detached)."""
+    torch = _torch()
+    face = _dev(face, torch.int32)
+    nq = face.numel()
+    if x0 is None:
+        x0 = exp_map(mesh, face, _dev(bary, torch.float32, (nq, 3)), torch.zeros(nq, 3, device=face.device),
+                     mesh_id=mesh_id)["pos"]
+    x = x0
+    st = None
+    steps = []
+    for k in range(K):
+        v = field(x, k) / K
+        f_in, b_in = face, bary
+        x, face, bary, d, st_k = ExpMap.apply(mesh, face, bary, v, estimator, V, mesh_id, eps)
+        st = st_k if st is None else (st | st_k)
+        if return_steps:
+            steps.append({"face": f_in, "bary": torch.as_tensor(b_in).detach(), "v": v.detach(), "end_face": face,
+                          "end_bary": bary.detach(), "end_dir": d.detach(), "status": st_k})
+    return (x, face, bary, st, steps) if return_steps else (x, face, bary, st)
 
 
 class _Lazy:

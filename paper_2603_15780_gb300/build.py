@@ -16,7 +16,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsgeo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["exp_map.cu", "backward.cu", "mesh_build.cpp"]
+SOURCES = ["exp_map.cu", "exp_map64.cu", "backward.cu", "mesh_update.cu", "mesh_build.cpp"]
+# The host mesh builder and the device vertex update evaluate the same FP64 expressions; both are
+# compiled without multiply-add contraction so that they round identically.
+PER_FILE = {"mesh_build.cpp": ["-Xcompiler", "-ffp-contract=off"], "mesh_update.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:
@@ -46,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     for s in srcs:
         o = os.path.join(OUT_DIR, os.path.basename(s) + ".o")
         objs.append(o)
-        cmd = [nv, "-c", s, "-o", o] + common
+        cmd = [nv, "-c", s, "-o", o] + common + PER_FILE.get(os.path.basename(s), [])
         if s.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

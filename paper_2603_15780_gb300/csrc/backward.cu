@@ -45,6 +45,8 @@
 #include "sgeo_internal.h"
 #include "walk.cuh"
 
+#define SG_BWD_MAX_W 4
+
 struct BwdArgs {
     WalkParams P;
     QueryIn in;
@@ -54,14 +56,18 @@ struct BwdArgs {
     const float *__restrict__ end_dir;
     const uint32_t *__restrict__ end_status;
     const float *__restrict__ g_pos;
-    float *grad_v, *grad_p, *grad_bary, *grad_V;
+    const float *__restrict__ g_bary;  // [nq][3] upstream gradient of end_bary, or NULL
+    const float *__restrict__ g_dir;   // [nq][3] upstream gradient of end_dir, or NULL
+    const float *__restrict__ g_w;     // [nq][n_w][3] upstream gradients of the carried vectors, or NULL
+    int32_t n_w;
+    float *grad_v, *grad_p, *grad_bary, *grad_V, *grad_w;
     uint32_t *out_status;
     float eps_v, eps_p;
     float4 *gacc;       // [nV] vertex-gradient accumulator (scratch)
     float2 *eacc;       // [nE] per interior edge (start, end) coefficients, canonical orientation (scratch)
     const int2 *edges;  // [nE] (canonical half-edge, twin)
     float *cols;        // [nq][4] column contractions: par, perp, u, v (scratch)
-    int32_t *tasks;     // [3 nq] (q << 2 | k) swept perturbations (scratch)
+    int32_t *tasks;     // [3 nq] (q << 2 | k) columns recomputed by literal walks (scratch)
     int32_t *ntask;     // task counter (scratch)
 };
 
@@ -112,6 +118,18 @@ struct EndAdj {
     F3 g, nm;           // upstream gradient, end-face normal
     int gfe;            // global end face
 };
+
+// Tangent gradient equivalent to an upstream gradient gb on the barycentrics of a point of face
+// f (Sec. 4: points are (face, b) pairs): g_t = sum_k gb_k grad(b_k), with grad b_1 =
+// (1/l01, -x2x/(l01 x2y)) and grad b_2 = (0, 1/x2y) in the face frame (grad b_0 = -grad b_1 -
+// grad b_2), so g_t . dp = sum_k gb_k db_k for every displacement dp in the face plane.
+__device__ __forceinline__ F3 bary_grad_to_tangent(const WalkParams &P, int f, F3 gb) {
+    const FaceRec R = load_rec(P.rec, f);
+    const float g1 = gb.y - gb.x, g2 = gb.z - gb.x;
+    const float tx = g1 / R.l01;
+    const float ty = (g2 - g1 * R.x2x / R.l01) / R.x2y;
+    return lift(load_frm(P, f), tx, ty);
+}
 
 __device__ __forceinline__ EndAdj end_adjoint(const BwdArgs &A, int64_t q, int foff) {
     EndAdj E;
@@ -254,7 +272,7 @@ struct RewalkJob {
     RewalkHook<GFD, GRADV> H;
     int64_t q;
     uint32_t st;
-    bool valid;
+    bool valid, hole_q;
     F3 gq;
 
     __device__ __forceinline__ bool init(int64_t t) {
@@ -266,7 +284,8 @@ struct RewalkJob {
         st = 0;
         if (!valid) return false;
         uint32_t fst = A->end_status ? __ldg(A->end_status + q) : 0u;
-        H.gradv = GRADV && !(fst & (SG_ST_VERTEX_HIT | SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_INVALID));
+        H.gradv = GRADV && !(fst & (SG_ST_VERTEX_HIT | SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_INVALID | SG_ST_HOLE));
+        hole_q = (fst & SG_ST_HOLE) != 0;
         if (GRADV && !H.gradv) st |= SG_ST_NO_GRADV;
         const float L = w.Lh, d0x = w.dx, d0y = w.dy;
         if (GFD) {
@@ -323,8 +342,11 @@ struct RewalkJob {
             atomic_add3(A->gacc, fve.z, b2 * gn);
         }
         if (GFD) {
+            // A walk that stopped at the boundary or at MAX_STEPS, or slid along the boundary
+            // (hole avoidance), takes literal walks for all perturbed columns; the par column
+            // is the chord from p' in every case (Round 2 of the paper's batching).
             unsigned split = H.S.split;
-            if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) split = 7u;
+            if ((w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) || hole_q) split = 7u;
             if (split) {
                 st |= SG_ST_GFD_SPLIT;
                 int base = atomicAdd(A->ntask, __popc(split));
@@ -368,10 +390,11 @@ __device__ F3 pos_diff(const WalkParams &P, const Walker &a, const Walker &b) {
 
 // 3-D chord of a walk of length `len` from the walker's position along unit 2-D direction u
 // (face frame), as the cancellation-free difference of the end and start positions
+template <bool HOLE>
 __device__ F3 short_chord(const WalkParams &P, const Walker &w0, float ux, float uy, float len) {
     Walker w = w0;
     w.dx = ux; w.dy = uy; w.Lh = len; w.Ll = 0.f; w.mode = 6; w.steps = 0;
-    while (!walker_step<true>(w, P)) {
+    while (!walker_step<true, HOLE>(w, P)) {
     }
     return pos_diff(P, w, w0);
 }
@@ -387,6 +410,7 @@ __device__ __forceinline__ void rmap(float x, float y, float d0x, float d0y, con
     oy = al * E.dmy + E.sm * be * E.dmx;
 }
 
+template <bool HOLE>
 __global__ void __launch_bounds__(128) k_bwd_chords(BwdArgs A) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= A.nq) return;
@@ -402,19 +426,20 @@ __global__ void __launch_bounds__(128) k_bwd_chords(BwdArgs A) {
         Walker we;
         end_walker(A, q, w, E, we);
         float ux, uy;
-        col.x = contract(short_chord(P, we, E.dmx, E.dmy, A.eps_v), E, A.eps_v);
+        col.x = contract(short_chord<HOLE>(P, we, E.dmx, E.dmy, A.eps_v), E, A.eps_v);
         rmap(-d0y, d0x, d0x, d0y, E, ux, uy);
-        col.y = contract(short_chord(P, we, ux, uy, A.eps_v), E, A.eps_v);
+        col.y = contract(short_chord<HOLE>(P, we, ux, uy, A.eps_v), E, A.eps_v);
         rmap(1.f, 0.f, d0x, d0y, E, ux, uy);
-        col.z = contract(short_chord(P, we, ux, uy, A.eps_p), E, A.eps_p);
+        col.z = contract(short_chord<HOLE>(P, we, ux, uy, A.eps_p), E, A.eps_p);
         rmap(evx, evy, d0x, d0y, E, ux, uy);
-        col.w = contract(short_chord(P, we, ux, uy, A.eps_p), E, A.eps_p);
+        col.w = contract(short_chord<HOLE>(P, we, ux, uy, A.eps_p), E, A.eps_p);
     }
     *reinterpret_cast<float4 *>(A.cols + 4 * q) = col;
 }
 
 // literal walk of one swept perturbation (task = q << 2 | k): k = 1 walks Exp(p, v + eps e_perp);
 // k = 2, 3 walk p_u = Exp(p, eps e_u) carrying v, then Exp(p_u, v_u) (two phases)
+template <bool HOLE>
 struct LiteralJob {
     const BwdArgs *A;
     Walker w;
@@ -443,7 +468,7 @@ struct LiteralJob {
         return true;
     }
     __device__ __forceinline__ bool step() {
-        if (!walker_step<true>(w, A->P)) return false;
+        if (!walker_step<true, HOLE>(w, A->P)) return false;
         if (phase == 1) return true;
         // end of p -> p_u: continue with v transported along the short walk
         float vc = d0x * ux + d0y * uy, vs = ux * d0y - uy * d0x;  // v/L relative to e_u
@@ -466,8 +491,9 @@ struct LiteralJob {
     }
 };
 
+template <bool HOLE>
 __global__ void __launch_bounds__(128) k_bwd_literal(BwdArgs A) {
-    LiteralJob job;
+    LiteralJob<HOLE> job;
     job.A = &A;
     run_persistent(A.ntask + 2, (int64_t)*A.ntask, job);
 }
@@ -495,6 +521,100 @@ __global__ void __launch_bounds__(256) k_bwd_assemble(BwdArgs A) {
     if (A.grad_v) st3(A.grad_v, q, gv);
     if (A.grad_p) st3(A.grad_p, q, gp);
     if (A.grad_bary) st3(A.grad_bary, q, gb);
+}
+
+// ------------------------------------------------------------------ end-barycentric upstream
+// An upstream gradient on the end barycentrics b' enters every estimator as its tangent
+// equivalent g_t (bary_grad_to_tangent), added to g_pos once before the other kernels run.
+__global__ void __launch_bounds__(256) k_fold_gbary(BwdArgs A, const float *g_pos, float *g_eff) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= A.nq) return;
+    F3 g = ld3(g_pos, q);
+    const int m = A.in.mesh_id ? __ldg(A.in.mesh_id + q) : 0;
+    const int lf = __ldg(A.end_face + q);
+    if (m >= 0 && m < A.in.n_mesh) {
+        const int foff = __ldg(A.P.face_off + m);
+        if (lf >= 0 && lf < __ldg(A.P.face_off + m + 1) - foff)
+            g = g + bary_grad_to_tangent(A.P, foff + lf, ld3(A.g_bary, q));
+    }
+    st3(g_eff, q, g);
+}
+
+// For grad_V: b' also moves with the end vertices at a fixed end point (sum_k x_k db'_k =
+// dp' - sum_k b'_k dx_k), which takes b'_k g_t off each end vertex of a query the re-walk
+// differentiated.
+__global__ void __launch_bounds__(256) k_gradv_gbary(BwdArgs A) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= A.nq) return;
+    Walker w;
+    Carry<0> cw;
+    if (!walker_init<0>(A.P, A.in, q, w, cw) || (w.st & SG_ST_INVALID)) return;
+    const uint32_t fst = __ldg(A.end_status + q);
+    if (fst & (SG_ST_VERTEX_HIT | SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_INVALID | SG_ST_HOLE)) return;
+    const int gfe = w.foff + __ldg(A.end_face + q);
+    const F3 gt = bary_grad_to_tangent(A.P, gfe, ld3(A.g_bary, q));
+    const F3 b = ld3(A.end_bary, q);
+    const int4 t = __ldg(A.P.fv + gfe);
+    atomic_add3(A.gacc, t.x, (-b.x) * gt);
+    atomic_add3(A.gacc, t.y, (-b.y) * gt);
+    atomic_add3(A.gacc, t.z, (-b.z) * gt);
+}
+
+// ------------------------------------------------------------------ direction and carried vectors
+// Sec. 4 "Parallel Transport": along the walk the direction and every carried vector keep their
+// angle to each other, so for a fixed face sequence w' = R w with R = M_p' M_p^T the rotation of
+// Eq. proxy_func, and grad_w = R^T g_w (exact).  The direction d' = R v/|v| is differentiated
+// with R held fixed, as EP does for the end point (under both estimators: GFD's differences
+// are taken of end points only): grad_v += (I - d0 d0^T) R^T g_dir / |v|.
+__global__ void __launch_bounds__(256) k_bwd_transport(BwdArgs A) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= A.nq) return;
+    const WalkParams &P = A.P;
+    Walker w;
+    Carry<0> cw;
+    const bool live = walker_init<0>(P, A.in, q, w, cw);
+    const bool valid = live && !(w.st & SG_ST_INVALID);
+    F3 gw[SG_BWD_MAX_W];
+    for (int k = 0; k < A.n_w; ++k) gw[k] = f3(0.f, 0.f, 0.f);
+    if (valid) {
+        const int gfe = w.foff + __ldg(A.end_face + q);
+        const Fr2 Fm = load_frm(P, gfe), F0 = load_frm(P, w.f);
+        F3 dd = ld3(A.end_dir, q);
+        float dmx = dd.x * Fm.e1x + dd.y * Fm.e1y + dd.z * Fm.e1z;
+        float dmy = dd.x * Fm.e2x + dd.y * Fm.e2y + dd.z * Fm.e2z;
+        const float n2 = dmx * dmx + dmy * dmy;
+        if (n2 > 0.f) { const float r = rsqrtf(n2); dmx *= r; dmy *= r; }
+        const uint32_t est = A.end_status ? __ldg(A.end_status + q) : 0u;
+        const float sm = (est & SG_ST_FLIPPED) ? -1.f : 1.f;
+        const float d0x = w.dx, d0y = w.dy;
+        // R^T g for a tangent g at the end, as a start-frame 2-vector (along, across d0)
+        auto back = [&](F3 g, float &al, float &ac) {
+            const float gx = g.x * Fm.e1x + g.y * Fm.e1y + g.z * Fm.e1z;
+            const float gy = g.x * Fm.e2x + g.y * Fm.e2y + g.z * Fm.e2z;
+            al = gx * dmx + gy * dmy;
+            ac = sm * (-gx * dmy + gy * dmx);
+        };
+        if (A.g_dir && A.grad_v) {
+            const F3 v = ld3(A.in.v, q);
+            const float v1 = v.x * F0.e1x + v.y * F0.e1y + v.z * F0.e1z, v2 = v.x * F0.e2x + v.y * F0.e2y + v.z * F0.e2z;
+            const float Lv = sqrtf(v1 * v1 + v2 * v2);
+            if (Lv > 0.f) {
+                float al, ac;
+                back(ld3(A.g_dir, q), al, ac);
+                const F3 add = (ac / Lv) * lift(F0, -d0y, d0x);
+                A.grad_v[3 * q] += add.x; A.grad_v[3 * q + 1] += add.y; A.grad_v[3 * q + 2] += add.z;
+            }
+        }
+        if (A.g_w) {
+            for (int k = 0; k < A.n_w; ++k) {
+                float al, ac;
+                back(ld3(A.g_w, (int64_t)A.n_w * q + k), al, ac);
+                gw[k] = lift(F0, al * d0x - ac * d0y, al * d0y + ac * d0x);
+            }
+        }
+    }
+    if (A.grad_w)
+        for (int k = 0; k < A.n_w; ++k) st3(A.grad_w, (int64_t)A.n_w * q + k, gw[k]);
 }
 
 // per interior edge: its coefficients times N_a + N_b (the outward in-plane normals of the edge
@@ -539,12 +659,13 @@ unsigned persistent_grid(K kernel, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
 }
 struct BwdLayout {
-    size_t gacc, eacc, cols, tasks, ntask, total;
+    size_t gacc, eacc, cols, tasks, ntask, gpos, total;
 };
 BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool grad_V) {
     BwdLayout L{};
     size_t o = 0;
     L.ntask = o; o = align_up(o + 64, 256);
+    L.gpos = o; o = align_up(o + sizeof(float) * 3 * (size_t)std::max<int64_t>(nq, 1), 256);
     if (grad_V) {
         L.gacc = o; o = align_up(o + sizeof(float4) * (size_t)nV, 256);
         L.eacc = o; o = align_up(o + sizeof(float2) * (size_t)std::max<int64_t>(nE, 1), 256);
@@ -570,18 +691,22 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
                                          const int32_t *mesh_id, const int32_t *face, const float *bary,
                                          const float *v, const int32_t *end_face, const float *end_bary,
                                          const float *end_dir, const uint32_t *end_status, const float *g_pos,
+                                         const float *g_bary, const float *g_dir, int32_t n_w, const float *g_w,
                                          float *grad_v, float *grad_p, float *grad_bary, float *grad_V,
-                                         uint32_t *out_status, const sg_opts *o, void *stream) {
+                                         float *grad_w, uint32_t *out_status, const sg_opts *o, void *stream) {
     if (!m || nq < 0) return SG_ERR_INVALID_ARG;
     if (estimator != SG_EST_EP && estimator != SG_EST_GFD) return SG_ERR_INVALID_ARG;
     if (nq == 0) return SG_OK;
     if (nq > (int64_t)(INT32_MAX / 4) - 1024) return SG_ERR_INVALID_ARG;
     if (!face || !bary || !v || !end_face || !end_bary || !end_dir || !g_pos) return SG_ERR_INVALID_ARG;
     if (grad_V && !end_status) return SG_ERR_INVALID_ARG;
+    if (n_w < 0 || n_w > SG_BWD_MAX_W || (n_w > 0 && (!g_w) != (!grad_w))) return SG_ERR_INVALID_ARG;
     if (estimator == SG_EST_GFD && !(eps_v > 0.f && eps_p > 0.f)) return SG_ERR_INVALID_ARG;
     sg_opts r;
     sg_opts_default(&r);
     if (o) r = *o;
+    if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
+    if (r.precision == 64) return SG_ERR_UNSUPPORTED;
     if (r.max_steps <= 0) r.max_steps = 1 << 20;
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
     if (r.tau_snap <= 0.f) r.tau_snap = 1e-6f;
@@ -594,7 +719,9 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.in.length = nullptr; A.in.w = nullptr;
     A.nq = nq;
     A.end_face = end_face; A.end_bary = end_bary; A.end_dir = end_dir; A.end_status = end_status; A.g_pos = g_pos;
-    A.grad_v = grad_v; A.grad_p = grad_p; A.grad_bary = grad_bary; A.grad_V = grad_V; A.out_status = out_status;
+    A.g_bary = g_bary; A.g_dir = g_dir; A.n_w = grad_w ? n_w : 0; A.g_w = g_w;
+    A.grad_v = grad_v; A.grad_p = grad_p; A.grad_bary = grad_bary; A.grad_V = grad_V; A.grad_w = grad_w;
+    A.out_status = out_status;
     A.eps_v = eps_v; A.eps_p = eps_p;
 
     BwdLayout Lw = bwd_layout(m->nV, m->nE, nq, estimator, grad_V != nullptr);
@@ -615,6 +742,12 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     }
     if (estimator == SG_EST_GFD) { A.cols = (float *)(base + Lw.cols); A.tasks = (int32_t *)(base + Lw.tasks); }
     cudaMemsetAsync(A.ntask, 0, 64, s);
+    const unsigned gq256 = (unsigned)((nq + 255) / 256);
+    if (g_bary) {  // fold the end-barycentric gradient into an effective g_pos
+        float *geff = (float *)(base + Lw.gpos);
+        k_fold_gbary<<<gq256, 256, 0, s>>>(A, g_pos, geff);
+        A.g_pos = geff;
+    }
     if (grad_V) {
         cudaMemsetAsync(A.gacc, 0, sizeof(float4) * (size_t)m->nV, s);
         cudaMemsetAsync(A.eacc, 0, sizeof(float2) * (size_t)std::max<int64_t>(m->nE, 1), s);
@@ -622,22 +755,26 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     const unsigned g128 = (unsigned)((nq + 127) / 128), g256 = (unsigned)((nq + 255) / 256);
     if (estimator == SG_EST_EP) {
         k_ep_backward<<<g256, 256, 0, s>>>(A);
-        if (grad_V) {
-            BwdArgs B = A;
-            B.out_status = nullptr;
-            k_bwd_rewalk<false, true><<<persistent_grid(k_bwd_rewalk<false, true>, nq), 128, 0, s>>>(B);
-        }
+        // the grad_V re-walk rewrites the status with its walk's bits and SG_ST_NO_GRADV
+        if (grad_V) k_bwd_rewalk<false, true><<<persistent_grid(k_bwd_rewalk<false, true>, nq), 128, 0, s>>>(A);
     } else {
         cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
         if (pev) cudaEventRecord(pev[0], s);
         if (grad_V) k_bwd_rewalk<true, true><<<persistent_grid(k_bwd_rewalk<true, true>, nq), 128, 0, s>>>(A);
         else k_bwd_rewalk<true, false><<<persistent_grid(k_bwd_rewalk<true, false>, nq), 128, 0, s>>>(A);
         if (pev) cudaEventRecord(pev[1], s);
-        k_bwd_chords<<<g128, 128, 0, s>>>(A);
-        k_bwd_literal<<<persistent_grid(k_bwd_literal, 3 * nq), 128, 0, s>>>(A);
+        if (r.boundary_mode) {
+            k_bwd_chords<true><<<g128, 128, 0, s>>>(A);
+            k_bwd_literal<true><<<persistent_grid(k_bwd_literal<true>, 3 * nq), 128, 0, s>>>(A);
+        } else {
+            k_bwd_chords<false><<<g128, 128, 0, s>>>(A);
+            k_bwd_literal<false><<<persistent_grid(k_bwd_literal<false>, 3 * nq), 128, 0, s>>>(A);
+        }
         k_bwd_assemble<<<g256, 256, 0, s>>>(A);
     }
+    if ((g_dir && grad_v) || (A.n_w > 0)) k_bwd_transport<<<g256, 256, 0, s>>>(A);
     if (grad_V) {
+        if (g_bary) k_gradv_gbary<<<g256, 256, 0, s>>>(A);
         if (m->nE > 0)
             k_gradv_edges<<<(unsigned)((m->nE + 255) / 256), 256, 0, s>>>(m->nE, A.P, m->d_edges, A.eacc, A.gacc);
         k_gradv_flush<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, A.gacc, grad_V);

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_walk_plain(FwdArgs a) {
     walker_finish<NW>(a, q, w, cw);
 }
 
-template <int NW, bool ESC>
+template <int NW, bool ESC, bool HOLE = false>
 struct FwdJob {
     const FwdArgs *a;
     Walker w;
@@ -89,14 +89,89 @@ struct FwdJob {
         q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
         return walker_init<NW>(a->P, a->in, q, w, cw);
     }
-    __device__ __forceinline__ bool step() { return walker_step<ESC>(w, a->P); }
+    __device__ __forceinline__ bool step() { return walker_step<ESC, HOLE>(w, a->P); }
     __device__ __forceinline__ void finish() { walker_finish<NW>(*a, q, w, cw); }
 };
 
-template <int NW, bool ESC>
+template <int NW, bool ESC, bool HOLE = false>
 __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
-    FwdJob<NW, ESC> job;
+    FwdJob<NW, ESC, HOLE> job;
     job.a = &a;
+    run_persistent(a.counter, a.nq, job);
+}
+
+// ------------------------------------------------------------------ geodesic tracing
+// The same walk, with the traced geodesic as an extra output (the by-product named in Sec. 1
+// and Sec. 4): every face the walk enters, in order, and the 3-D point where it enters it (the
+// start point, then each edge crossing point or, after a vertex hit, the vertex).  Inside a
+// face the straightest geodesic is a straight segment, so these points followed by the end
+// point are the polyline of the geodesic.
+struct TraceOut {
+    int32_t cap;
+    int32_t *face;  // [nq][cap] local face ids
+    float *pt;      // [nq][cap][3] entry points, or NULL
+    int32_t *len;   // [nq] faces entered (may exceed cap; entries past cap are dropped)
+};
+
+template <bool ESC>
+struct TraceJob {
+    const FwdArgs *a;
+    const TraceOut *t;
+    Walker w;
+    Carry<0> cw;
+    int64_t q;
+    int n;
+    __device__ __forceinline__ void rec(float x, float y, float z) {
+        if (n < t->cap) {
+            const int64_t i = q * t->cap + n;
+            t->face[i] = w.f - w.foff;
+            if (t->pt) { t->pt[3 * i] = x; t->pt[3 * i + 1] = y; t->pt[3 * i + 2] = z; }
+        }
+        n++;
+    }
+    __device__ __forceinline__ bool init(int64_t tk) {
+        q = a->perm ? (int64_t)__ldg(a->perm + tk) : tk;
+        n = 0;
+        const bool live = walker_init<0>(a->P, a->in, q, w, cw);
+        if (live && w.Lh > 0.f) {  // Exp_p(0) = p enters no face
+            const float *b = a->in.bary + 3 * q;
+            float b0 = fmaxf(__ldg(b), 0.f), b1 = fmaxf(__ldg(b + 1), 0.f), b2 = fmaxf(__ldg(b + 2), 0.f);
+            const float rs = 1.f / (b0 + b1 + b2);
+            b0 *= rs; b1 *= rs; b2 *= rs;
+            const int4 t3 = __ldg(a->P.fv + w.f);
+            const float4 x0 = __ldg(a->P.V + t3.x), x1 = __ldg(a->P.V + t3.y), x2 = __ldg(a->P.V + t3.z);
+            rec(b0 * x0.x + b1 * x1.x + b2 * x2.x, b0 * x0.y + b1 * x1.y + b2 * x2.y, b0 * x0.z + b1 * x1.z + b2 * x2.z);
+        }
+        return live;
+    }
+    __device__ __forceinline__ bool step() {
+        const int nc = w.ncross;
+        const bool done = walker_step<ESC>(w, a->P);
+        if (w.ncross != nc) {
+            // entered face w.f through its local edge k at fraction px from corner k
+            const int k = w.h - 3 * w.f;
+            const int4 t3 = __ldg(a->P.fv + w.f);
+            const float4 xa = __ldg(a->P.V + sel3(k, t3.x, t3.y, t3.z)), xb = __ldg(a->P.V + sel3(nxt(k), t3.x, t3.y, t3.z));
+            rec(fmaf(w.px, xb.x - xa.x, xa.x), fmaf(w.px, xb.y - xa.y, xa.y), fmaf(w.px, xb.z - xa.z, xa.z));
+        } else if (!done && w.mode >= 3 && w.mode < 6) {
+            // a vertex transport left the walker on corner mode-3 of face w.f
+            const int4 t3 = __ldg(a->P.fv + w.f);
+            const float4 xv = __ldg(a->P.V + sel3(w.mode - 3, t3.x, t3.y, t3.z));
+            rec(xv.x, xv.y, xv.z);
+        }
+        return done;
+    }
+    __device__ __forceinline__ void finish() {
+        walker_finish<0>(*a, q, w, cw);
+        t->len[q] = n;
+    }
+};
+
+template <bool ESC>
+__global__ void __launch_bounds__(256, 4) k_trace_persistent(FwdArgs a, TraceOut t) {
+    TraceJob<ESC> job;
+    job.a = &a;
+    job.t = &t;
     run_persistent(a.counter, a.nq, job);
 }
 
@@ -223,8 +298,9 @@ sg_opts resolve(const sg_opts *o) {
     if (o) r = *o;
     if (r.max_steps <= 0) r.max_steps = 1 << 20;
     if (r.block <= 0) r.block = 256;
+    if (r.precision <= 0) r.precision = 32;
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
-    if (r.tau_snap <= 0.f) r.tau_snap = 1e-6f;
+    if (r.tau_snap <= 0.f) r.tau_snap = r.precision == 64 ? 1e-12f : 1e-6f;
     if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
     if (r.sort < 0) r.sort = 1;
     if (r.kernel == SG_KERNEL_PLAIN) { r.sort = 0; r.fp64_escalate = 0; }
@@ -249,6 +325,15 @@ cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
         per = std::max(per, 1);
     }
     int64_t need = (a.nq + o.block - 1) / o.block;
+    if (o.boundary_mode) {  // hole avoidance: its own instantiation, FP64 classification
+        if (o.blocks_per_sm <= 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk_persistent<NW, true, true>, o.block, 0);
+            per = std::max(per, 1);
+        }
+        int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(need, 1));
+        k_walk_persistent<NW, true, true><<<(unsigned)grid, o.block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(need, 1));
     if (o.fp64_escalate)
         k_walk_persistent<NW, true><<<(unsigned)grid, o.block, 0, s>>>(a);
@@ -272,10 +357,12 @@ void sg_opts_default(sg_opts *o) {
     o->blocks_per_sm = 0;
     o->fp64_escalate = 1;
     o->tau_near = 1e-4f;
-    o->tau_snap = 1e-6f;
+    o->tau_snap = 0.f;
     o->workspace = nullptr;
     o->workspace_bytes = 0;
     o->prof_events = nullptr;
+    o->boundary_mode = 0;
+    o->precision = 32;
 }
 
 const char *sg_status_string(sg_status s) {
@@ -349,6 +436,13 @@ sg_status sg_mesh_destroy(sg_mesh *m) {
     cudaFree(m->d_V);
     cudaFree(m->d_face_off);
     cudaFree(m->d_lref);
+    cudaFree(m->d_theta);
+    cudaFree(m->d_lsum);
+    cudaFree(m->d_ecount);
+    cudaFree(m->d_ndegen);
+    cudaFree(m->d_rec64);
+    cudaFree(m->d_frm64);
+    cudaFree(m->d_th64);
     delete m;
     return SG_OK;
 }
@@ -361,6 +455,18 @@ sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info) {
     info->record_bytes = 32 + 3 * 32;
     info->device_bytes = m->device_bytes;
     info->l_ref_mean = m->lref.empty() ? 0.0 : m->lref[0];
+    info->n_degenerate = 0;
+    if (m->updated) {  // geometry re-derived on the device: read back the current values
+        std::vector<int> nd(m->n_mesh);
+        double ls = 0.0;
+        unsigned long long ne = 0;
+        if (cudaMemcpy(nd.data(), m->d_ndegen, sizeof(int) * nd.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&ls, m->d_lsum, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&ne, m->d_ecount, sizeof(ne), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return SG_ERR_CUDA;
+        for (int x : nd) info->n_degenerate += x;
+        info->l_ref_mean = ne ? ls / (double)ne : 0.0;
+    }
     return SG_OK;
 }
 
@@ -370,6 +476,64 @@ sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts 
     *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT && r.sort).total;
     return SG_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Fills the walk parameters and query inputs shared by the forward entry points.
+FwdArgs fwd_args(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const float *bary,
+                 const float *v, const float *length, const float *w, const sg_opts &r) {
+    FwdArgs a{};
+    a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.frm = m->d_frm; a.P.half = m->d_half; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
+    a.P.max_steps = r.max_steps; a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
+    a.nq = nq; a.in.n_mesh = m->n_mesh; a.nF_total = (int32_t)m->nF;
+    a.in.mesh_id = mesh_id; a.in.face = face; a.in.bary = bary; a.in.v = v; a.in.length = length; a.in.w = w;
+    return a;
+}
+
+// Work queue of the persistent kernels: the ticket counter and, when sorting, the permutation
+// of queries by (mesh, start face).  Uses the caller's workspace or stream-ordered scratch
+// (*own_ws = the pointer to free after the walk).
+sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const sg_opts &r,
+                        bool sort, cudaStream_t s, FwdArgs &a, void **own_ws) {
+    *own_ws = nullptr;
+    WsLayout L = ws_layout(m->nF, nq, sort);
+    void *ws = nullptr;
+    if (r.workspace) {
+        if (r.workspace_bytes < L.total) return SG_ERR_OOM;
+        ws = r.workspace;
+    } else {
+        if (cudaMallocAsync(&ws, L.total, s) != cudaSuccess) { cudaGetLastError(); return SG_ERR_OOM; }
+        *own_ws = ws;
+    }
+    char *base = (char *)ws;
+    a.counter = (int32_t *)(base + L.counter);
+    if (cudaMemsetAsync(a.counter, 0, 64, s) != cudaSuccess) return SG_ERR_CUDA;
+    if (sort) {
+        int32_t *counts = (int32_t *)(base + L.counts);
+        int32_t *sums = (int32_t *)(base + L.sums);
+        int32_t *perm = (int32_t *)(base + L.perm);
+        int64_t nk = m->nF + 1;
+        int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
+        cudaMemsetAsync(counts, 0, sizeof(int32_t) * nk, s);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int g = (int)std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 8);
+        k_sort_keys_hist<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts);
+        k_scan_tiles<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(counts, nk, sums);
+        k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums, ntiles);
+        k_scan_add<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(counts, nk, sums);
+        k_sort_scatter<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts, perm);
+        a.perm = perm;
+    }
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const float *bary,
                      const float *v, const float *length, int32_t n_w, const float *w, int32_t *out_face,
@@ -383,50 +547,40 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     sg_opts r = resolve(o);
     if (r.kernel != SG_KERNEL_PLAIN && r.kernel != SG_KERNEL_PERSISTENT) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
+    if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
+    if (r.boundary_mode && r.kernel == SG_KERNEL_PLAIN) return SG_ERR_UNSUPPORTED;
+    if (r.precision != 32 && r.precision != 64) return SG_ERR_INVALID_ARG;
+    if (r.precision == 64 && (r.boundary_mode || r.kernel == SG_KERNEL_PLAIN)) return SG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
-    FwdArgs a{};
-    a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.frm = m->d_frm; a.P.half = m->d_half; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
-    a.P.max_steps = r.max_steps; a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
+    FwdArgs a = fwd_args(m, nq, mesh_id, face, bary, v, length, w, r);
     a.P.want_hash = out_hash != nullptr;
-    a.nq = nq; a.in.n_mesh = m->n_mesh; a.nF_total = (int32_t)m->nF;
-    a.in.mesh_id = mesh_id; a.in.face = face; a.in.bary = bary; a.in.v = v; a.in.length = length; a.in.w = w;
     a.out_face = out_face; a.out_bary = out_bary; a.out_pos = out_pos; a.out_dir = out_dir;
     a.out_w = out_w; a.out_status = out_status; a.out_ncross = out_ncross; a.out_hash = out_hash;
 
     const bool persistent = r.kernel == SG_KERNEL_PERSISTENT;
-    const bool sort = persistent && r.sort;
-    void *ws = nullptr;
-    bool own_ws = false;
+    void *own_ws = nullptr;
     if (persistent) {
-        WsLayout L = ws_layout(m->nF, nq, sort);
-        if (r.workspace) {
-            if (r.workspace_bytes < L.total) return SG_ERR_OOM;
-            ws = r.workspace;
-        } else {
-            if (cudaMallocAsync(&ws, L.total, s) != cudaSuccess) { cudaGetLastError(); return SG_ERR_OOM; }
-            own_ws = true;
+        sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.sort != 0, s, a, &own_ws);
+        if (st != SG_OK) {
+            if (own_ws) cudaFreeAsync(own_ws, s);
+            return st;
         }
-        char *base = (char *)ws;
-        a.counter = (int32_t *)(base + L.counter);
-        if (cudaMemsetAsync(a.counter, 0, 64, s) != cudaSuccess) return SG_ERR_CUDA;
-        if (sort) {
-            int32_t *counts = (int32_t *)(base + L.counts);
-            int32_t *sums = (int32_t *)(base + L.sums);
-            int32_t *perm = (int32_t *)(base + L.perm);
-            int64_t nk = m->nF + 1;
-            int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
-            cudaMemsetAsync(counts, 0, sizeof(int32_t) * nk, s);
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            int g = (int)std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 8);
-            k_sort_keys_hist<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts);
-            k_scan_tiles<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(counts, nk, sums);
-            k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums, ntiles);
-            k_scan_add<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(counts, nk, sums);
-            k_sort_scatter<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts, perm);
-            a.perm = perm;
+    }
+    if (r.precision == 64) {
+        // the FP64 geometry is a lazily built cache of the mesh (hence the const_cast)
+        sg_status st = sg_geom64_prepare(const_cast<sg_mesh *>(m), s);
+        if (st != SG_OK) {
+            if (own_ws) cudaFreeAsync(own_ws, s);
+            return st;
         }
+        SgFwdIO io{a.in, nq, out_face, out_bary, out_pos, out_dir, out_w, out_status, out_ncross, out_hash, a.perm,
+                   a.counter};
+        cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
+        if (pev) cudaEventRecord(pev[0], s);
+        cudaError_t e = sg_launch_walk64(m, io, n_w, r, s);
+        if (pev) cudaEventRecord(pev[1], s);
+        if (own_ws) cudaFreeAsync(own_ws, s);
+        return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
     }
     cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
     if (pev) cudaEventRecord(pev[0], s);
@@ -439,7 +593,54 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
         default: e = launch_walk<4>(a, r, s); break;
     }
     if (pev) cudaEventRecord(pev[1], s);
-    if (own_ws) cudaFreeAsync(ws, s);
+    if (own_ws) cudaFreeAsync(own_ws, s);
+    if (e != cudaSuccess) {
+        std::snprintf(g_err, sizeof g_err, "%s", cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+    }
+    return SG_OK;
+}
+
+sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
+                           const float *bary, const float *v, const float *length, int32_t path_cap,
+                           int32_t *out_path_face, float *out_path_pt, int32_t *out_path_len, int32_t *out_face,
+                           float *out_bary, float *out_pos, float *out_dir, uint32_t *out_status,
+                           int32_t *out_ncross, uint64_t *out_hash, const sg_opts *o, void *stream) {
+    if (!m || nq < 0 || path_cap < 0) return SG_ERR_INVALID_ARG;
+    if (nq == 0) return SG_OK;
+    if (nq > (int64_t)INT32_MAX - 1024) return SG_ERR_INVALID_ARG;
+    if (!face || !bary || !v || !out_face || !out_bary || !out_pos || !out_dir || !out_status || !out_path_len)
+        return SG_ERR_INVALID_ARG;
+    if (path_cap > 0 && !out_path_face) return SG_ERR_INVALID_ARG;
+    sg_opts r = resolve(o);
+    if (r.boundary_mode || r.precision == 64) return SG_ERR_UNSUPPORTED;
+    if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    FwdArgs a = fwd_args(m, nq, mesh_id, face, bary, v, length, nullptr, r);
+    a.P.want_hash = out_hash != nullptr;
+    a.out_face = out_face; a.out_bary = out_bary; a.out_pos = out_pos; a.out_dir = out_dir;
+    a.out_w = nullptr; a.out_status = out_status; a.out_ncross = out_ncross; a.out_hash = out_hash;
+    TraceOut t{path_cap, out_path_face, path_cap > 0 ? out_path_pt : nullptr, out_path_len};
+    void *own_ws = nullptr;
+    sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.sort != 0 && r.kernel != SG_KERNEL_PLAIN, s, a, &own_ws);
+    if (st != SG_OK) {
+        if (own_ws) cudaFreeAsync(own_ws, s);
+        return st;
+    }
+    int dev = 0, sms = 0, per = r.blocks_per_sm;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool esc = r.fp64_escalate && r.kernel != SG_KERNEL_PLAIN;
+    if (per <= 0) {
+        if (esc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_persistent<true>, r.block, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace_persistent<false>, r.block, 0);
+        per = std::max(per, 1);
+    }
+    int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>((nq + r.block - 1) / r.block, 1));
+    if (esc) k_trace_persistent<true><<<(unsigned)grid, r.block, 0, s>>>(a, t);
+    else k_trace_persistent<false><<<(unsigned)grid, r.block, 0, s>>>(a, t);
+    cudaError_t e = cudaGetLastError();
+    if (own_ws) cudaFreeAsync(own_ws, s);
     if (e != cudaSuccess) {
         std::snprintf(g_err, sizeof g_err, "%s", cudaGetErrorString(e));
         return SG_ERR_CUDA;

@@ -1,0 +1,473 @@
+// exp_map64.cu -- the full-precision walk (sg_opts.precision = 64).
+//
+// The same straightest-geodesic walk as walk.cuh (Alg. geodesic_step, transport_over_edge,
+// transport_over_vertex; Sec. 4), with every quantity of the walker state and of the face
+// geometry in FP64: the position, direction and remaining length, the face shapes, frames and
+// vertex angles.  It serves inputs where the FP32 walk's accumulated error exceeds the
+// classification margins (long walks over sliver triangles), at the cost of FP64 arithmetic.
+// The walker stays in the face frames (no half-edge records); a crossing maps it into the
+// neighbour's frame through the shared edge, the unfolding isometry of Sec. 4.
+//
+// The FP64 geometry is derived on the device from the mesh's vertex positions (converted to
+// FP64) the first time a call asks for it, and again after sg_mesh_update_vertices.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "sgeo_internal.h"
+#include "walk.cuh"
+
+namespace {
+
+struct R64 {
+    int n0, n1, n2;
+    double l01, x2x, x2y, il1, il2;
+};
+
+struct P64 {
+    const int4 *__restrict__ rec;     // FP32 records: neighbour links
+    const double *__restrict__ rec64; // [nF][6] l01, x2x, x2y, 1/l12, 1/l20, -
+    const double *__restrict__ frm64; // [nF][6] e1, e2
+    const double *__restrict__ th64;  // [nV] theta, negated on the boundary
+    const int4 *__restrict__ fv;
+    const float4 *__restrict__ V;
+    const int32_t *__restrict__ face_off;
+    const float *__restrict__ lref;
+    int max_steps, want_hash;
+    double tau_near, tau_snap;
+};
+
+__device__ __forceinline__ R64 load64(const P64 &P, int f) {
+    const int4 a = __ldg(P.rec + 2 * f);
+    const double2 *r = reinterpret_cast<const double2 *>(P.rec64 + 6 * f);
+    const double2 u = __ldg(r), v = __ldg(r + 1), w = __ldg(r + 2);
+    return R64{a.x, a.y, a.z, u.x, u.y, v.x, v.y, w.x};
+}
+__device__ __forceinline__ int nb64(const R64 &r, int k) { return sel3(k, r.n0, r.n1, r.n2); }
+__device__ __forceinline__ double cx64(const R64 &r, int k) { return sel3(k, 0.0, r.l01, r.x2x); }
+__device__ __forceinline__ double cy64(const R64 &r, int k) { return sel3(k, 0.0, 0.0, r.x2y); }
+
+struct W64 {
+    int f, foff, mode, steps, ncross;
+    uint32_t st;
+    uint64_t hash;
+    double px, py, dx, dy, L, lref;
+    R64 R;
+};
+
+__device__ __forceinline__ void hash64(W64 &w, int f, int want) {
+    if (want) {
+        w.hash ^= (uint64_t)(uint32_t)(f - w.foff);
+        w.hash *= SG_FNV_PRIME;
+    }
+}
+__device__ __forceinline__ double sig64(const W64 &w, double cx, double cy) {
+    return w.dx * (cy - w.py) - w.dy * (cx - w.px);
+}
+__device__ __forceinline__ void norm2(double &x, double &y) {
+    const double r = 1.0 / sqrt(x * x + y * y);
+    x *= r; y *= r;
+}
+__device__ __forceinline__ double corner_angle(const R64 &R, int c) {
+    const double ax = cx64(R, nxt(c)) - cx64(R, c), ay = cy64(R, nxt(c)) - cy64(R, c);
+    const double bx = cx64(R, prv(c)) - cx64(R, c), by = cy64(R, prv(c)) - cy64(R, c);
+    return atan2(fabs(ax * by - ay * bx), ax * bx + ay * by);
+}
+
+// straightest rule at corner c of w.f (Alg. transport_over_vertex): the outgoing ray splits
+// theta in two equal halves with the reversed incoming ray; the fan is walked toward corner c-1
+template <int NW>
+__device__ bool vertex64(W64 &w, int c, const P64 &P) {
+    const int4 t = __ldg(P.fv + w.f);
+    const double th = __ldg(P.th64 + sel3(c, t.x, t.y, t.z));
+    w.st |= SG_ST_VERTEX_HIT;
+    const double cx = cx64(w.R, c), cy = cy64(w.R, c);
+    w.px = cx; w.py = cy;
+    if (th < 0.0) {
+        w.st |= SG_ST_BOUNDARY;
+        return false;
+    }
+    const double half = 0.5 * th;
+    const double rx = -w.dx, ry = -w.dy;
+    int e = prv(c);
+    const double ex = cx64(w.R, prv(c)) - cx, ey = cy64(w.R, prv(c)) - cy;
+    double A = atan2(fabs(rx * ey - ry * ex), rx * ex + ry * ey);
+    if (A >= half) {
+        double hx = ex - (ex * rx + ey * ry) * rx, hy = ey - (ex * rx + ey * ry) * ry;
+        norm2(hx, hy);
+        double sh, ch;
+        sincos(half, &sh, &ch);
+        w.dx = ch * rx + sh * hx;
+        w.dy = ch * ry + sh * hy;
+        norm2(w.dx, w.dy);
+        w.mode = 3 + c;
+        hash64(w, w.f, P.want_hash);
+        return true;
+    }
+    int cur_c = c;
+    R64 Rc = w.R;
+    for (int guard = 0; guard < 4096; ++guard) {
+        const int nb = nb64(Rc, e);
+        if (nb < 0) {
+            w.st |= SG_ST_BOUNDARY;
+            return false;
+        }
+        const int g = nb >> 3, kp = nb & 3, fl = (nb >> 2) & 1;
+        if (fl) w.st ^= SG_PARITY_BIT;
+        const R64 Rg = load64(P, g);
+        const bool x_end_cur = (cur_c == nxt(e));
+        const bool x_start_g = (x_end_cur != (bool)fl);
+        const int cg = x_start_g ? kp : nxt(kp);
+        const int yg = x_start_g ? nxt(kp) : kp;
+        const int zg = 3 - cg - yg;
+        const double gx = cx64(Rg, cg), gy = cy64(Rg, cg);
+        double ux = cx64(Rg, yg) - gx, uy = cy64(Rg, yg) - gy;
+        const double zx = cx64(Rg, zg) - gx, zy = cy64(Rg, zg) - gy;
+        const double gam = atan2(fabs(ux * zy - uy * zx), ux * zx + uy * zy);
+        if (A + gam >= half) {
+            const double beta = half - A;
+            norm2(ux, uy);
+            double hx = zx - (zx * ux + zy * uy) * ux, hy = zy - (zx * ux + zy * uy) * uy;
+            norm2(hx, hy);
+            double sb, cb;
+            sincos(beta, &sb, &cb);
+            w.dx = cb * ux + sb * hx;
+            w.dy = cb * uy + sb * hy;
+            norm2(w.dx, w.dy);
+            w.f = g;
+            w.R = Rg;
+            w.px = gx; w.py = gy;
+            w.mode = 3 + cg;
+            hash64(w, g, P.want_hash);
+            return true;
+        }
+        A += gam;
+        e = (nxt(cg) == zg) ? cg : zg;
+        cur_c = cg;
+        Rc = Rg;
+    }
+    w.st |= SG_ST_MAX_STEPS;
+    return false;
+}
+
+// one step of Alg. geodesic_step in FP64 (same decisions as the FP32 general step)
+template <int NW>
+__device__ bool step64(W64 &w, const P64 &P) {
+    if (w.steps >= P.max_steps) {
+        w.st |= SG_ST_MAX_STEPS;
+        return true;
+    }
+    w.steps++;
+    const R64 &R = w.R;
+    const double near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
+    const double s0 = sig64(w, 0.0, 0.0), s1 = sig64(w, R.l01, 0.0), s2 = sig64(w, R.x2x, R.x2y);
+    const int mode = w.mode;
+    int j, hit = -1;
+    double mflag;
+    if (mode < 3) {
+        const int k = mode, a = prv(k);
+        const double sa = sel3(a, s0, s1, s2);
+        mflag = fabs(sa);
+        if (mflag <= snap) { hit = a; mflag = 3.0e300; }
+        j = sa > 0.0 ? nxt(k) : prv(k);
+    } else if (mode < 6) {
+        const int c = mode - 3, a = nxt(c), b = prv(c);
+        j = a;
+        const double fa = fabs(sel3(a, s0, s1, s2)), fb = fabs(sel3(b, s0, s1, s2));
+        mflag = fmin(fa, fb);
+        if (mflag <= snap) { hit = fa <= fb ? a : b; mflag = fmax(fa, fb); }
+    } else {
+        if (s0 < 0.0 && s1 >= 0.0) j = 0;
+        else if (s1 < 0.0 && s2 >= 0.0) j = 1;
+        else if (s2 < 0.0 && s0 >= 0.0) j = 2;
+        else { w.st |= SG_ST_INVALID; return true; }
+        const double fa = fabs(sel3(j, s0, s1, s2)), fb = fabs(sel3(nxt(j), s0, s1, s2)), fo = fabs(sel3(prv(j), s0, s1, s2));
+        mflag = fmin(fmin(fa, fb), fo);
+        if (fmin(fa, fb) <= snap) { hit = fa <= fb ? j : nxt(j); mflag = fmin(fmax(fa, fb), fo); }
+    }
+    if (mflag < near) w.st |= SG_ST_NEAR_VERTEX;
+    const int jb = nxt(j);
+    const double ax = cx64(R, j), ay = cy64(R, j), bx = cx64(R, jb), by = cy64(R, jb);
+    double qx, qy, s;
+    if (hit >= 0) {
+        qx = cx64(R, hit); qy = cy64(R, hit);
+        s = (hit == j) ? 0.0 : 1.0;
+    } else {
+        const double sa = sel3(j, s0, s1, s2), sb = sel3(jb, s0, s1, s2);
+        const double den = sa - sb;
+        s = den != 0.0 ? sa / den : 0.5;
+        s = fmin(fmax(s, 0.0), 1.0);
+        qx = ax + s * (bx - ax);
+        qy = ay + s * (by - ay);
+    }
+    const double t = fmax((qx - w.px) * w.dx + (qy - w.py) * w.dy, 0.0);
+    if (t >= w.L) {
+        w.px += w.L * w.dx;
+        w.py += w.L * w.dy;
+        w.L = 0.0;
+        const double d0 = fabs(w.py);
+        const double d1 = fabs((R.x2x - R.l01) * w.py - R.x2y * (w.px - R.l01)) * R.il1;
+        const double d2 = fabs(R.x2x * w.py - R.x2y * w.px) * R.il2;
+        if (fmin(fmin(d0, d1), d2) <= near) w.st |= SG_ST_NEAR_EDGE;
+        return true;
+    }
+    w.L -= t;
+    if (hit >= 0) return !vertex64<NW>(w, hit, P);
+    const int nb = nb64(R, j);
+    if (nb < 0) {
+        w.px = qx; w.py = qy;
+        w.st |= SG_ST_BOUNDARY;
+        return true;
+    }
+    // into the frame of g: the shared edge is g's local edge kp (A' -> B'), reversed unless the
+    // adjacency is flipped; g lies on the left of A' -> B' in its own frame
+    const int g = nb >> 3, kp = nb & 3, fl = (nb >> 2) & 1;
+    const R64 G = load64(P, g);
+    const double ex = bx - ax, ey = by - ay, le = sqrt(ex * ex + ey * ey);
+    const double ux = ex / le, uy = ey / le;
+    const double da = w.dx * ux + w.dy * uy;           // along the edge (P_j -> P_j+1)
+    const double dn = -w.dx * uy + w.dy * ux;          // along the inward normal of f (< 0 when leaving)
+    const double Ax = cx64(G, kp), Ay = cy64(G, kp), Bx = cx64(G, nxt(kp)), By = cy64(G, nxt(kp));
+    const double gx = Bx - Ax, gy = By - Ay, lg = sqrt(gx * gx + gy * gy);
+    const double vx = gx / lg, vy = gy / lg;           // unit A' -> B'; g's inward normal = (-vy, vx)
+    const double sgn = fl ? 1.0 : -1.0;                // image of the edge direction P_j -> P_j+1
+    double ndx = sgn * da * vx - dn * -vy, ndy = sgn * da * vy - dn * vx;
+    norm2(ndx, ndy);
+    const double sp = fl ? s : 1.0 - s;                // fraction along A' -> B'
+    w.px = Ax + sp * gx;
+    w.py = Ay + sp * gy;
+    w.dx = ndx; w.dy = ndy;
+    w.f = g;
+    w.R = G;
+    w.mode = kp;
+    if (fl) w.st ^= SG_PARITY_BIT;
+    w.ncross++;
+    hash64(w, g, P.want_hash);
+    return false;
+}
+
+struct Fwd64Args {
+    P64 P;
+    QueryIn in;
+    int64_t nq;
+    int32_t *out_face;
+    float *out_bary, *out_pos, *out_dir, *out_w;
+    uint32_t *out_status;
+    int32_t *out_ncross;
+    uint64_t *out_hash;
+    const int32_t *__restrict__ perm;
+    int32_t *counter;
+};
+
+template <int NW>
+struct Job64 {
+    const Fwd64Args *a;
+    W64 w;
+    double cc[NW > 0 ? NW : 1], cs[NW > 0 ? NW : 1];
+    int64_t q;
+
+    __device__ __forceinline__ bool init(int64_t t) {
+        q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
+        const P64 &P = a->P;
+        const QueryIn &in = a->in;
+        const int m = in.mesh_id ? __ldg(in.mesh_id + q) : 0;
+        const int lf = __ldg(in.face + q);
+        w.st = 0; w.steps = 0; w.ncross = 0; w.hash = SG_FNV_OFFSET; w.mode = 6;
+        bool bad = (m < 0 || m >= in.n_mesh);
+        const int foff = bad ? 0 : __ldg(P.face_off + m);
+        const int nfm = bad ? 1 : __ldg(P.face_off + m + 1) - foff;
+        bad = bad || lf < 0 || lf >= nfm;
+        const float lr = bad ? 1.f : __ldg(P.lref + m);
+        bad = bad || !(lr > 0.f);
+        w.foff = foff;
+        w.f = bad ? foff : foff + lf;
+        w.lref = bad ? 1.0 : (double)lr;
+        w.R = load64(P, w.f);
+        double b0 = __ldg(in.bary + 3 * q), b1 = __ldg(in.bary + 3 * q + 1), b2 = __ldg(in.bary + 3 * q + 2);
+        const double sb = b0 + b1 + b2;
+        if (!(fabs(sb - 1.0) <= 1e-6) || b0 < -1e-7 || b1 < -1e-7 || b2 < -1e-7) bad = true;
+        for (int k = 0; k < NW; ++k) { cc[k] = 0.0; cs[k] = 0.0; }
+        w.px = w.py = w.dx = w.dy = 0.0; w.L = 0.0;
+        if (bad) { w.st |= SG_ST_INVALID; return false; }
+        b0 = fmax(b0, 0.0) / sb; b1 = fmax(b1, 0.0) / sb; b2 = fmax(b2, 0.0) / sb;
+        w.px = b1 * w.R.l01 + b2 * w.R.x2x;
+        w.py = b2 * w.R.x2y;
+        const double *fr = P.frm64 + 6 * w.f;
+        const double vx = __ldg(in.v + 3 * q), vy = __ldg(in.v + 3 * q + 1), vz = __ldg(in.v + 3 * q + 2);
+        const double v1 = vx * fr[0] + vy * fr[1] + vz * fr[2], v2 = vx * fr[3] + vy * fr[4] + vz * fr[5];
+        const double Lv = sqrt(v1 * v1 + v2 * v2);
+        const double L = in.length ? (double)__ldg(in.length + q) : Lv;
+        if (!(L >= 0.0) || (Lv == 0.0 && L > 0.0)) { w.st |= SG_ST_INVALID; return false; }
+        if (Lv > 0.0) { w.dx = v1 / Lv; w.dy = v2 / Lv; }
+        w.L = L;
+        for (int k = 0; k < NW; ++k) {
+            const float *wp = in.w + (3 * NW) * q + 3 * k;
+            const double wx = __ldg(wp), wy = __ldg(wp + 1), wz = __ldg(wp + 2);
+            const double w1 = wx * fr[0] + wy * fr[1] + wz * fr[2], w2 = wx * fr[3] + wy * fr[4] + wz * fr[5];
+            cc[k] = w1 * w.dx + w2 * w.dy;
+            cs[k] = w.dx * w2 - w.dy * w1;
+        }
+        const int zeros = (b0 == 0.0) + (b1 == 0.0) + (b2 == 0.0);
+        if (zeros) w.st |= SG_ST_START_ON_EDGE;
+        if (zeros == 2 && L > 0.0) {
+            const int c = b0 == 1.0 ? 0 : (b1 == 1.0 ? 1 : 2);
+            const double cx = cx64(w.R, c), cy = cy64(w.R, c);
+            const double ax = cx64(w.R, nxt(c)) - cx, ay = cy64(w.R, nxt(c)) - cy;
+            const double bx = cx64(w.R, prv(c)) - cx, by = cy64(w.R, prv(c)) - cy;
+            if (!(ax * w.dy - ay * w.dx > 0.0 && w.dx * by - w.dy * bx > 0.0)) {
+                w.st |= SG_ST_INVALID;
+                w.L = 0.0;
+                return false;
+            }
+            w.px = cx; w.py = cy;
+            w.mode = 3 + c;
+        }
+        if (L > 0.0) hash64(w, w.f, P.want_hash);
+        return L > 0.0;
+    }
+    __device__ __forceinline__ bool step() { return step64<NW>(w, a->P); }
+    __device__ __forceinline__ void finish() {
+        const Fwd64Args &A = *a;
+        const R64 &R = w.R;
+        const double b2 = w.py / R.x2y, b1 = (w.px - b2 * R.x2x) / R.l01, b0 = 1.0 - b1 - b2;
+        const int4 t = __ldg(A.P.fv + w.f);
+        const float4 x0 = __ldg(A.P.V + t.x), x1 = __ldg(A.P.V + t.y), x2 = __ldg(A.P.V + t.z);
+        const double *fr = A.P.frm64 + 6 * w.f;
+        A.out_face[q] = w.f - w.foff;
+        A.out_bary[3 * q] = (float)b0; A.out_bary[3 * q + 1] = (float)b1; A.out_bary[3 * q + 2] = (float)b2;
+        A.out_pos[3 * q] = (float)(b0 * x0.x + b1 * x1.x + b2 * x2.x);
+        A.out_pos[3 * q + 1] = (float)(b0 * x0.y + b1 * x1.y + b2 * x2.y);
+        A.out_pos[3 * q + 2] = (float)(b0 * x0.z + b1 * x1.z + b2 * x2.z);
+        A.out_dir[3 * q] = (float)(w.dx * fr[0] + w.dy * fr[3]);
+        A.out_dir[3 * q + 1] = (float)(w.dx * fr[1] + w.dy * fr[4]);
+        A.out_dir[3 * q + 2] = (float)(w.dx * fr[2] + w.dy * fr[5]);
+        if (NW > 0 && A.out_w) {
+            const double sg = (w.st & SG_PARITY_BIT) ? -1.0 : 1.0;
+            for (int k = 0; k < NW; ++k) {
+                const double c = cc[k], s = sg * cs[k];
+                const double u1 = c * w.dx - s * w.dy, u2 = c * w.dy + s * w.dx;
+                float *o = A.out_w + (3 * NW) * q + 3 * k;
+                o[0] = (float)(u1 * fr[0] + u2 * fr[3]);
+                o[1] = (float)(u1 * fr[1] + u2 * fr[4]);
+                o[2] = (float)(u1 * fr[2] + u2 * fr[5]);
+            }
+        }
+        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u);
+        if (A.out_ncross) A.out_ncross[q] = w.ncross;
+        if (A.out_hash) A.out_hash[q] = w.hash;
+    }
+};
+
+template <int NW>
+__global__ void __launch_bounds__(128) k_walk64(Fwd64Args a) {
+    Job64<NW> job;
+    job.a = &a;
+    run_persistent(a.counter, a.nq, job);
+}
+
+// FP64 geometry from the FP32 vertex positions (converted exactly), the same expressions as
+// the host builder: face shape and frame, corner angles summed into theta
+__global__ void k_geom64_faces(int64_t nF, const int4 *__restrict__ fv, const float4 *__restrict__ V, double *rec64,
+                               double *frm64, double *th64) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nF) return;
+    const int4 t = fv[f];
+    const float4 a = V[t.x], b = V[t.y], c = V[t.z];
+    const double x0[3] = {a.x, a.y, a.z}, x1[3] = {b.x, b.y, b.z}, x2[3] = {c.x, c.y, c.z};
+    double e1[3], e2[3], n[3];
+    for (int i = 0; i < 3; ++i) { e1[i] = x1[i] - x0[i]; e2[i] = x2[i] - x0[i]; }
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double l01 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double u[3], nh[3], w[3];
+    for (int i = 0; i < 3; ++i) { u[i] = e1[i] * (1.0 / l01); nh[i] = n[i] * (1.0 / nn); }
+    w[0] = nh[1] * u[2] - nh[2] * u[1];
+    w[1] = nh[2] * u[0] - nh[0] * u[2];
+    w[2] = nh[0] * u[1] - nh[1] * u[0];
+    const double x2x = e2[0] * u[0] + e2[1] * u[1] + e2[2] * u[2];
+    const double x2y = e2[0] * w[0] + e2[1] * w[1] + e2[2] * w[2];
+    const double d12[3] = {x2[0] - x1[0], x2[1] - x1[1], x2[2] - x1[2]};
+    const double l12 = sqrt(d12[0] * d12[0] + d12[1] * d12[1] + d12[2] * d12[2]);
+    const double l20 = sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
+    double *r = rec64 + 6 * f;
+    r[0] = l01; r[1] = x2x; r[2] = x2y; r[3] = 1.0 / l12; r[4] = 1.0 / l20; r[5] = 0.0;
+    double *fr = frm64 + 6 * f;
+    fr[0] = u[0]; fr[1] = u[1]; fr[2] = u[2]; fr[3] = w[0]; fr[4] = w[1]; fr[5] = w[2];
+    const double *X[3] = {x0, x1, x2};
+    const int tv[3] = {t.x, t.y, t.z};
+    for (int k = 0; k < 3; ++k) {
+        const double *p = X[k], *q1 = X[(k + 1) % 3], *q2 = X[(k + 2) % 3];
+        const double ea[3] = {q1[0] - p[0], q1[1] - p[1], q1[2] - p[2]}, eb[3] = {q2[0] - p[0], q2[1] - p[1], q2[2] - p[2]};
+        const double cr[3] = {ea[1] * eb[2] - ea[2] * eb[1], ea[2] * eb[0] - ea[0] * eb[2], ea[0] * eb[1] - ea[1] * eb[0]};
+        atomicAdd(th64 + tv[k], atan2(sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]),
+                                      ea[0] * eb[0] + ea[1] * eb[1] + ea[2] * eb[2]));
+    }
+}
+
+// boundary vertices carry the sign of the FP32 theta (negative)
+__global__ void k_geom64_sign(int64_t nV, const float4 *__restrict__ V, double *th64) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    if (signbit(V[v].w)) th64[v] = -th64[v];
+}
+
+}  // namespace
+
+// Builds (first use) or refreshes (after a vertex update) the FP64 geometry, on `s`.
+sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s) {
+    if (!m->d_rec64) {
+        const size_t b0 = sizeof(double) * 6 * (size_t)m->nF, b1 = b0, b2 = sizeof(double) * (size_t)m->nV;
+        if (cudaMalloc((void **)&m->d_rec64, b0) != cudaSuccess || cudaMalloc((void **)&m->d_frm64, b1) != cudaSuccess ||
+            cudaMalloc((void **)&m->d_th64, b2) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(m->d_rec64); cudaFree(m->d_frm64); cudaFree(m->d_th64);
+            m->d_rec64 = m->d_frm64 = m->d_th64 = nullptr;
+            return SG_ERR_OOM;
+        }
+        m->device_bytes += (int64_t)(b0 + b1 + b2);
+        m->geom64_stale = true;
+    }
+    if (m->geom64_stale) {
+        if (cudaMemsetAsync(m->d_th64, 0, sizeof(double) * (size_t)m->nV, s) != cudaSuccess) return SG_ERR_CUDA;
+        k_geom64_faces<<<(unsigned)((m->nF + 255) / 256), 256, 0, s>>>(m->nF, m->d_fv, m->d_V, m->d_rec64, m->d_frm64,
+                                                                      m->d_th64);
+        k_geom64_sign<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, m->d_V, m->d_th64);
+        if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
+        m->geom64_stale = false;
+    }
+    return SG_OK;
+}
+
+cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const sg_opts &r, cudaStream_t s) {
+    Fwd64Args a{};
+    a.P.rec = m->d_rec; a.P.rec64 = m->d_rec64; a.P.frm64 = m->d_frm64; a.P.th64 = m->d_th64;
+    a.P.fv = m->d_fv; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
+    a.P.max_steps = r.max_steps; a.P.want_hash = io.out_hash != nullptr;
+    a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
+    a.in = io.in; a.nq = io.nq;
+    a.out_face = io.out_face; a.out_bary = io.out_bary; a.out_pos = io.out_pos; a.out_dir = io.out_dir;
+    a.out_w = io.out_w; a.out_status = io.out_status; a.out_ncross = io.out_ncross; a.out_hash = io.out_hash;
+    a.perm = io.perm; a.counter = io.counter;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto go = [&](auto kern) {
+        int per = r.blocks_per_sm;
+        if (per <= 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 128, 0);
+            per = std::max(per, 1);
+        }
+        const int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>((io.nq + 127) / 128, 1));
+        kern<<<(unsigned)grid, 128, 0, s>>>(a);
+    };
+    switch (n_w) {
+        case 0: go(k_walk64<0>); break;
+        case 1: go(k_walk64<1>); break;
+        case 2: go(k_walk64<2>); break;
+        case 3: go(k_walk64<3>); break;
+        default: go(k_walk64<4>); break;
+    }
+    return cudaGetLastError();
+}

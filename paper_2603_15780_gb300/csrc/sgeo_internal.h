@@ -29,7 +29,8 @@
 //   edges int2[nE]     (canonical half-edge, twin half-edge) of each interior edge
 //   V     float4[nV]   vertex position (x,y,z); .w = total angle theta(x), negated for boundary
 //                      vertices (Sec. 4: theta = sum of incident corner angles)
-//   face_off int32[n_mesh+1], lref float[n_mesh] (mean edge length per mesh)
+//   face_off int32[n_mesh+1], lref float[n_mesh] (mean edge length per mesh; -1 marks a mesh whose
+//                      vertices were moved to a degenerate face, every query on it is rejected)
 //
 // The walk of a query touches one record per edge crossing (one dependent 32-B gather);
 // fv/V are read only at the start, at vertex hits and at the end.
@@ -57,6 +58,17 @@ struct sg_mesh {
     std::vector<int64_t> face_off, vert_off;
     std::vector<double> lref;
     int64_t device_bytes = 0;
+    // scratch of sg_mesh_update_vertices (allocated by its first call)
+    double *d_theta = nullptr;
+    double *d_lsum = nullptr;
+    unsigned long long *d_ecount = nullptr;
+    int *d_ndegen = nullptr;
+    bool updated = false;
+    // FP64 geometry of the full-precision walk (built by its first call, refreshed after an update)
+    double *d_rec64 = nullptr;
+    double *d_frm64 = nullptr;
+    double *d_th64 = nullptr;
+    bool geom64_stale = true;
 };
 
 // host-side builder (mesh_build.cpp); fills the host arrays, returns SG_OK or an error

@@ -118,12 +118,213 @@ __device__ __forceinline__ void renorm(float &x, float &y) {
     x *= r; y *= r;
 }
 
+// ------------------------------------------------------------------ hole avoidance
+// Sec. 4 "Straightest geodesics": instead of stopping at the boundary, the walk may trace along
+// it and resume as soon as possible with the last straightest direction (App. transport_over_
+// vertex / transport_over_edge, hole-avoidance branches).  The paper describes the face choice
+// (its transport_error) without defining it; the reading used here:
+//   - D is the direction, in 3-D, that the walker had when it reached the boundary;
+//   - a face around the boundary vertex receives D when D projected onto its plane points
+//     strictly into the face's corner at the vertex; the receiving face of least |D . n_f|
+//     is taken and the straightest walk resumes from the vertex inside it;
+//   - when no face receives D, the walk follows the boundary to the next boundary vertex,
+//     keeping its sense along the boundary (at a vertex hit directly by the ray: the boundary
+//     edge whose direction agrees best with D), spending the edge's length;
+//   - a decision closer than tau_near is flagged NEAR_VERTEX.
+__device__ __forceinline__ void frm_axes(const WalkParams &P, int f, float &e1x, float &e1y, float &e1z, float &e2x,
+                                         float &e2y, float &e2z) {
+    const float4 a = __ldg(P.frm + 2 * f), b = __ldg(P.frm + 2 * f + 1);
+    e1x = a.x; e1y = a.y; e1z = a.z; e2x = a.w; e2y = b.x; e2z = b.y;
+}
+
+// The walker sits on corner c of face w.f (a boundary vertex; w.R is the face record).
+// Returns true when the walk resumes (walker on a corner of the receiving face), false when
+// it ended (length spent along the boundary, or MAX_STEPS).
+__device__ __forceinline__ bool hole_vertex(Walker &w, const WalkParams &P, int c, int came_from, float Dx, float Dy,
+                                            float Dz) {
+    w.st |= SG_ST_HOLE;
+    const float tau = P.tau_near;
+    for (;;) {
+        const int f0 = w.f;
+        const FaceRec R0 = w.R;
+        const int4 fv0 = __ldg(P.fv + f0);
+        const int v0 = sel3(c, fv0.x, fv0.y, fv0.z);
+        int bg = -1, bcg = 0;
+        unsigned bfl = 0u;
+        float bux = 0.f, buy = 0.f, berr = 3.0e38f, serr = 3.0e38f;
+        int nb = 0, ebf[2] = {0, 0}, ebc[2] = {0, 0}, ebo[2] = {0, 0};
+        unsigned ebfl[2] = {0u, 0u};
+        // does face g (record Rg, v0 on its corner cg, orientation fl relative to f0) receive D?
+        auto consider = [&](int g, const FaceRec &Rg, int cg, unsigned fl) {
+            float e1x, e1y, e1z, e2x, e2y, e2z;
+            frm_axes(P, g, e1x, e1y, e1z, e2x, e2y, e2z);
+            float ux = Dx * e1x + Dy * e1y + Dz * e1z, uy = Dx * e2x + Dy * e2y + Dz * e2z;
+            const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+            const float err = fabsf(Dx * nx + Dy * ny + Dz * nz);
+            const float lu = sqrtf(ux * ux + uy * uy);
+            if (!(lu > 1e-6f)) return;
+            ux /= lu; uy /= lu;
+            const float px = corner_x(Rg, cg), py = corner_y(Rg, cg);
+            const float ax = corner_x(Rg, nxt(cg)) - px, ay = corner_y(Rg, nxt(cg)) - py;
+            const float bx = corner_x(Rg, prv(cg)) - px, by = corner_y(Rg, prv(cg)) - py;
+            const float sa = (ax * uy - ay * ux) * rsqrtf(ax * ax + ay * ay);
+            const float sb = (ux * by - uy * bx) * rsqrtf(bx * bx + by * by);
+            const float mg = fminf(sa, sb);
+            if (fabsf(mg) < tau) w.st |= SG_ST_NEAR_VERTEX;
+            if (!(mg > 0.f)) return;
+            if (err < berr) {
+                serr = berr; berr = err; bg = g; bcg = cg; bfl = fl; bux = ux; buy = uy;
+            } else if (err < serr) {
+                serr = err;
+            }
+        };
+        consider(f0, R0, c, 0u);
+        for (int dir = 0; dir < 2; ++dir) {
+            int cur = f0, cur_c = c;
+            FaceRec Rc = R0;
+            unsigned fl = 0u;
+            int e = dir == 0 ? c : prv(c);  // local edge c runs c -> c+1, local edge c-1 runs c-1 -> c
+            for (int guard = 0; guard < 4096; ++guard) {
+                const int nbv = nbr_of(Rc, e);
+                if (nbv < 0) {  // boundary edge at v0
+                    if (nb < 2) { ebf[nb] = cur; ebc[nb] = cur_c; ebo[nb] = (e == cur_c) ? nxt(e) : e; ebfl[nb] = fl; }
+                    ++nb;
+                    break;
+                }
+                const int g = nbv >> 3, kp = nbv & 3, gfl = (nbv >> 2) & 1;
+                if (g == f0) break;
+                fl ^= (unsigned)gfl;
+                const FaceRec Rg = load_rec(P.rec, g);
+                const bool x_end_cur = (cur_c == nxt(e));
+                const bool x_start_g = (x_end_cur != (bool)gfl);
+                const int cg = x_start_g ? kp : nxt(kp);
+                const int yg = x_start_g ? nxt(kp) : kp;
+                const int zg = 3 - cg - yg;
+                consider(g, Rg, cg, fl);
+                e = (nxt(cg) == zg) ? cg : zg;
+                cur = g; cur_c = cg; Rc = Rg;
+            }
+        }
+        if (bg >= 0) {
+            if (serr - berr < tau) w.st |= SG_ST_NEAR_VERTEX;
+            w.f = bg;
+            w.R = load_rec(P.rec, bg);
+            w.px = corner_x(w.R, bcg); w.py = corner_y(w.R, bcg);
+            w.dx = bux; w.dy = buy;
+            w.mode = 3 + bcg;
+            if (bfl) w.st ^= SG_PARITY_BIT;
+            walker_hash(w, bg, P.want_hash);
+            return true;
+        }
+        if (nb == 0) { w.st |= SG_ST_BOUNDARY; return false; }
+        nb = nb > 2 ? 2 : nb;
+        int k = 0;
+        if (nb == 2) {
+            const int4 t0 = __ldg(P.fv + ebf[0]);
+            const int o0 = sel3(ebo[0], t0.x, t0.y, t0.z);
+            if (came_from >= 0) {
+                k = (o0 == came_from) ? 1 : 0;
+            } else {
+                const int4 t1 = __ldg(P.fv + ebf[1]);
+                const int o1 = sel3(ebo[1], t1.x, t1.y, t1.z);
+                const float4 xv = __ldg(P.V + v0), x0 = __ldg(P.V + o0), x1 = __ldg(P.V + o1);
+                const float a0x = x0.x - xv.x, a0y = x0.y - xv.y, a0z = x0.z - xv.z;
+                const float a1x = x1.x - xv.x, a1y = x1.y - xv.y, a1z = x1.z - xv.z;
+                const float d0 = (Dx * a0x + Dy * a0y + Dz * a0z) * rsqrtf(a0x * a0x + a0y * a0y + a0z * a0z);
+                const float d1 = (Dx * a1x + Dy * a1y + Dz * a1z) * rsqrtf(a1x * a1x + a1y * a1y + a1z * a1z);
+                k = d1 > d0 ? 1 : 0;
+                if (fabsf(d1 - d0) < tau) w.st |= SG_ST_NEAR_VERTEX;
+            }
+        }
+        const int fb = ebf[k], cb = ebc[k], co = ebo[k];
+        if (ebfl[k]) w.st ^= SG_PARITY_BIT;
+        if (fb != w.f) {
+            w.f = fb;
+            w.R = load_rec(P.rec, fb);
+            walker_hash(w, fb, P.want_hash);
+        }
+        const float ax = corner_x(w.R, cb), ay = corner_y(w.R, cb);
+        if (w.steps >= P.max_steps) {
+            w.st |= SG_ST_MAX_STEPS;
+            w.px = ax; w.py = ay; w.mode = 3 + cb;
+            return false;
+        }
+        w.steps++;
+        const float bx = corner_x(w.R, co), by = corner_y(w.R, co);
+        const float ex = bx - ax, ey = by - ay, le = sqrtf(ex * ex + ey * ey);
+        const float L = w.Lh + w.Ll;
+        if (L <= le) {
+            const float t = L / le;
+            w.px = fmaf(t, ex, ax); w.py = fmaf(t, ey, ay);
+            w.Lh = 0.f; w.Ll = 0.f;
+            float e1x, e1y, e1z, e2x, e2y, e2z;
+            frm_axes(P, fb, e1x, e1y, e1z, e2x, e2y, e2z);
+            float ux = Dx * e1x + Dy * e1y + Dz * e1z, uy = Dx * e2x + Dy * e2y + Dz * e2z;
+            const float lu = sqrtf(ux * ux + uy * uy);
+            if (lu > 1e-6f) { w.dx = ux / lu; w.dy = uy / lu; } else { w.dx = ex / le; w.dy = ey / le; }
+            w.mode = 6;
+            return false;
+        }
+        {   // compensated L -= le
+            float a = w.Lh, b = -le;
+            float sum = a + b;
+            float bb = sum - a;
+            float err = (a - (sum - bb)) + (b - bb);
+            w.Lh = sum;
+            w.Ll += err;
+        }
+        came_from = v0;
+        c = co;
+        w.px = bx; w.py = by; w.mode = 3 + co;
+    }
+}
+
+// The walk reached boundary edge j of face w.f at (w.px, w.py) (face frame, w.R the face
+// record): slide along it toward the endpoint the direction points to (corner j+1 when
+// d . (P_{j+1} - P_j) >= 0, else corner j), then handle that boundary vertex.  Returns true
+// when the walk resumes.
+__device__ __forceinline__ bool hole_edge(Walker &w, const WalkParams &P, int j) {
+    w.st |= SG_ST_HOLE;
+    const FaceRec &R = w.R;
+    const float ax = corner_x(R, j), ay = corner_y(R, j), bx = corner_x(R, nxt(j)), by = corner_y(R, nxt(j));
+    const float ex = bx - ax, ey = by - ay;
+    const float de = (w.dx * ex + w.dy * ey) * rsqrtf(ex * ex + ey * ey);
+    if (fabsf(de) < P.tau_near) w.st |= SG_ST_NEAR_VERTEX;
+    const int tgt = de >= 0.f ? nxt(j) : j, oth = de >= 0.f ? j : nxt(j);
+    const float tx = corner_x(R, tgt) - w.px, ty = corner_y(R, tgt) - w.py;
+    const float dist = sqrtf(tx * tx + ty * ty);
+    const float L = w.Lh + w.Ll;
+    if (L <= dist) {
+        const float t = dist > 0.f ? L / dist : 0.f;
+        w.px = fmaf(t, tx, w.px); w.py = fmaf(t, ty, w.py);
+        w.Lh = 0.f; w.Ll = 0.f;
+        w.mode = 6;
+        return false;
+    }
+    {   // compensated L -= dist
+        float a = w.Lh, b = -dist;
+        float sum = a + b;
+        float bb = sum - a;
+        float err = (a - (sum - bb)) + (b - bb);
+        w.Lh = sum;
+        w.Ll += err;
+    }
+    w.steps++;
+    float e1x, e1y, e1z, e2x, e2y, e2z;
+    frm_axes(P, w.f, e1x, e1y, e1z, e2x, e2y, e2z);
+    const float Dx = w.dx * e1x + w.dy * e2x, Dy = w.dx * e1y + w.dy * e2y, Dz = w.dx * e1z + w.dy * e2z;
+    const int4 t3 = __ldg(P.fv + w.f);
+    w.px = corner_x(R, tgt); w.py = corner_y(R, tgt); w.mode = 3 + tgt;
+    return hole_vertex(w, P, tgt, sel3(oth, t3.x, t3.y, t3.z), Dx, Dy, Dz);
+}
+
 // Vertex transport: the walker reached corner c of face w.f with direction d.
 // Straightest rule (Sec. 4, Alg. transport_over_vertex): leave along the ray that splits the
 // total angle theta(x) in two equal halves with the reversed incoming ray.  The fan is walked
 // from -d through the faces around x until the accumulated corner angles pass theta/2; the
 // outgoing ray lies in that face at the excess angle from the shared edge.
 // Returns false if the walk must stop (boundary vertex).
+template <bool HOLE = false>
 __device__ __forceinline__ bool vertex_transport(Walker &w, int c, const WalkParams &P) {
     int4 fvv = __ldg(P.fv + w.f);
     int vid = sel3(c, fvv.x, fvv.y, fvv.z);
@@ -131,7 +332,12 @@ __device__ __forceinline__ bool vertex_transport(Walker &w, int c, const WalkPar
     w.st |= SG_ST_VERTEX_HIT;
     float cx = corner_x(w.R, c), cy = corner_y(w.R, c);
     w.px = cx; w.py = cy;
-    if (th < 0.f) {  // boundary vertex: original rule stops here (Sec. 4)
+    if (th < 0.f) {  // boundary vertex: original rule stops here (Sec. 4), or hole avoidance
+        if (HOLE) {
+            float e1x, e1y, e1z, e2x, e2y, e2z;
+            frm_axes(P, w.f, e1x, e1y, e1z, e2x, e2y, e2z);
+            return hole_vertex(w, P, c, -1, w.dx * e1x + w.dy * e2x, w.dx * e1y + w.dy * e2y, w.dx * e1z + w.dy * e2z);
+        }
         w.st |= SG_ST_BOUNDARY;
         return false;
     }
@@ -245,7 +451,7 @@ __device__ __forceinline__ void half_to_face(Walker &w, const WalkParams &P, flo
 // (sigma_C > 0), else C -> A.  The twin half-edge's frame has the crossed edge as its x axis
 // (reversed unless the adjacency is flipped) and the new face on +y, so the new direction is
 // (-+ d.e, d.n_out) / |e|, renormalised; no corner lookups are needed.
-template <bool ESC, class Hook>
+template <bool ESC, bool HOLE, class Hook>
 __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &hook) {
     const FaceRec &R = w.R;
     const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
@@ -306,11 +512,13 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         const int c = prv(w.h - 3 * w.f);  // the apex is corner k+2 of the face
         half_to_face(w, P, cx, cy);
         hook.on_vertex(w, c);
-        return !vertex_transport(w, c, P);
+        return !vertex_transport<HOLE>(w, c, P);
     }
     const int link = right ? hlinkR(R) : hlinkL(R);
-    if (link < 0) {  // boundary edge: original rule stops (Sec. 4)
+    if (link < 0) {  // boundary edge: original rule stops (Sec. 4), or hole avoidance
+        const int k = w.h - 3 * w.f;
         half_to_face(w, P, qx, qy);
+        if (HOLE) return !hole_edge(w, P, right ? nxt(k) : prv(k));
         w.st |= SG_ST_BOUNDARY;
         return true;
     }
@@ -340,11 +548,11 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     return false;
 }
 
-template <bool ESC, class Hook>
+template <bool ESC, bool HOLE, class Hook>
 __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hook &hook);
 
 // One step of Alg. geodesic_step.  Returns true when the walk is finished.
-template <bool ESC, class Hook = NoHook>
+template <bool ESC, bool HOLE = false, class Hook = NoHook>
 __device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook &&hook = Hook()) {
     if (w.steps >= P.max_steps) {
         if (w.mode == SG_MODE_HALF) half_to_face(w, P, w.px * hl(w.R), 0.f);
@@ -352,13 +560,13 @@ __device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook
         return true;
     }
     w.steps++;
-    if (w.mode == SG_MODE_HALF) return half_step<ESC>(w, P, hook);
-    return general_step<ESC>(w, P, hook);
+    if (w.mode == SG_MODE_HALF) return half_step<ESC, HOLE>(w, P, hook);
+    return general_step<ESC, HOLE>(w, P, hook);
 }
 
 // Step from a corner (after a vertex transport) or from a free start point (face frame); a
 // crossing moves the walker into the half-edge frame of the face it enters.
-template <bool ESC, class Hook>
+template <bool ESC, bool HOLE, class Hook>
 __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hook &hook) {
     const FaceRec &R = w.R;
     const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
@@ -445,12 +653,13 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
     }
     if (hit >= 0) {
         hook.on_vertex(w, hit);
-        if (!vertex_transport(w, hit, P)) return true;
+        if (!vertex_transport<HOLE>(w, hit, P)) return true;
         return false;
     }
     const int nb = nbr_of(R, j);
-    if (nb < 0) {  // boundary edge: original rule stops (Sec. 4)
+    if (nb < 0) {  // boundary edge: original rule stops (Sec. 4), or hole avoidance
         w.px = qx; w.py = qy;
+        if (HOLE) return !hole_edge(w, P, j);
         w.st |= SG_ST_BOUNDARY;
         return true;
     }
@@ -489,6 +698,21 @@ struct QueryIn {
     const float *__restrict__ length;
     const float *__restrict__ w;
 };
+
+// Inputs and outputs of one forward call, handed to the full-precision walk (exp_map64.cu).
+struct SgFwdIO {
+    QueryIn in;
+    int64_t nq;
+    int32_t *out_face;
+    float *out_bary, *out_pos, *out_dir, *out_w;
+    uint32_t *out_status;
+    int32_t *out_ncross;
+    uint64_t *out_hash;
+    const int32_t *perm;
+    int32_t *counter;
+};
+sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s);
+cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const sg_opts &r, cudaStream_t s);
 
 struct Frame3 {
     float ox, oy, oz;  // corner 0
@@ -534,9 +758,11 @@ __device__ bool walker_init(const WalkParams &P, const QueryIn &a, int64_t q, Wa
     int foff = bad ? 0 : __ldg(P.face_off + m);
     int nfm = bad ? 1 : __ldg(P.face_off + m + 1) - foff;
     bad = bad || lf < 0 || lf >= nfm;
+    float lr = bad ? 1.f : __ldg(P.lref + m);
+    bad = bad || !(lr > 0.f);  // a mesh moved to a degenerate face carries l_ref = -1
     w.foff = foff;
     w.f = bad ? foff : foff + lf;
-    w.lref = bad ? 1.f : __ldg(P.lref + m);
+    w.lref = bad ? 1.f : lr;
     w.R = load_rec(P.rec, w.f);
     float b0 = __ldg(a.bary + 3 * q), b1 = __ldg(a.bary + 3 * q + 1), b2 = __ldg(a.bary + 3 * q + 2);
     float sb = b0 + b1 + b2;

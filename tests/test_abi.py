@@ -30,7 +30,7 @@ def test_defaults_and_status_strings():
     import paper_2603_15780_gb300 as sg
     o = sg.default_opts()
     assert o.max_steps == 1 << 20 and o.block == 256 and o.fp64_escalate == 1
-    assert abs(o.tau_near - 1e-4) < 1e-9 and abs(o.tau_snap - 1e-6) < 1e-12
+    assert abs(o.tau_near - 1e-4) < 1e-9 and o.tau_snap == 0.0 and o.precision == 32  # snap: 1e-6 (FP32) / 1e-12 (FP64)
     assert sg.lib().sg_status_string(2) == b"non-manifold mesh"
     assert sg.lib().sg_version().startswith(b"sgeo")
 
@@ -42,7 +42,9 @@ def test_null_arguments_rejected_without_gpu_work():
     assert L.sg_mesh_create(None, 3, None, 1, C.byref(out)) == 1
     o = sg.default_opts()
     assert L.sg_exp_map(None, 1, None, None, None, None, None, 0, *([None] * 9), C.byref(o), None) == 1
-    assert L.sg_exp_map_backward(None, 0, 1e-4, 1e-4, 1, *([None] * 14), C.byref(o), None) == 1
+    assert L.sg_exp_map_backward(None, 0, 1e-4, 1e-4, 1, *([None] * 11), 0, *([None] * 7), C.byref(o), None) == 1
+    assert L.sg_exp_map_trace(None, 1, None, None, None, None, None, 8, *([None] * 10), C.byref(o), None) == 1
+    assert L.sg_mesh_update_vertices(None, None, None) == 1
     n = C.c_size_t()
     assert L.sg_exp_map_workspace_size(None, 1, None, C.byref(n)) == 1
 
