@@ -148,7 +148,9 @@ struct TraceJob {
         const int nc = w.ncross;
         const bool done = walker_step<ESC>(w, a->P);
         if (w.ncross != nc) {
-            // entered face w.f through its local edge k at fraction px from corner k
+            // entered face h / 3 through its local edge k at fraction px from corner k (in the
+            // half-edge mode the walker does not keep w.f up to date)
+            if (w.mode == SG_MODE_HALF) w.f = w.h / 3;
             const int k = w.h - 3 * w.f;
             const int4 t3 = __ldg(a->P.fv + w.f);
             const float4 xa = __ldg(a->P.V + sel3(k, t3.x, t3.y, t3.z)), xb = __ldg(a->P.V + sel3(nxt(k), t3.x, t3.y, t3.z));

@@ -74,7 +74,7 @@ struct WalkParams {
 
 // Walker state (all registers).  mode 7: on the entry edge of half-edge h (the hot case; R
 // holds the half-edge record, (px, py) = (fraction s along the edge, 0), d in the edge
-// frame); modes 0..2 entered through local edge `mode`, 3..5 sitting on corner mode-3 after a
+// frame; f is stale and recomputed as h / 3 on leaving this mode); modes 0..2 entered through local edge `mode`, 3..5 sitting on corner mode-3 after a
 // vertex transport, 6 free start -- in these R holds the face record and p, d are in the face
 // frame.  Every walk ends in a face mode.
 #define SG_MODE_HALF 7
@@ -435,6 +435,7 @@ struct NoHook {
 // R becomes the face record (needed at the end of a walk and before a vertex transport).
 __device__ __forceinline__ void half_to_face(Walker &w, const WalkParams &P, float xe, float ye) {
     const float ca = hca(w.R), sa = hsa(w.R);
+    w.f = w.h / 3;  // not kept up to date on the hot path
     const int k = w.h - 3 * w.f;
     const FaceRec F = load_rec(P.rec, w.f);
     w.px = corner_x(F, k) + ca * xe - sa * ye;
@@ -509,15 +510,15 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         w.Ll += err;
     }
     if (hit) {
-        const int c = prv(w.h - 3 * w.f);  // the apex is corner k+2 of the face
         half_to_face(w, P, cx, cy);
+        const int c = prv(w.h - 3 * w.f);  // the apex is corner k+2 of the face
         hook.on_vertex(w, c);
         return !vertex_transport<HOLE>(w, c, P);
     }
     const int link = right ? hlinkR(R) : hlinkL(R);
     if (link < 0) {  // boundary edge: original rule stops (Sec. 4), or hole avoidance
-        const int k = w.h - 3 * w.f;
         half_to_face(w, P, qx, qy);
+        const int k = w.h - 3 * w.f;
         if (HOLE) return !hole_edge(w, P, right ? nxt(k) : prv(k));
         w.st |= SG_ST_BOUNDARY;
         return true;
@@ -527,11 +528,13 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     const float da = fmaf(w.dx, ex, w.dy * ey);   // |e| (d . e_hat)
     const float dc = fmaf(w.dx, ey, -w.dy * ex);  // |e| (d . n_out)
     const FaceRec G = load_rec(P.half, hn);
-    float ndx = fl ? da : -da, ndy = dc;
-    renorm(ndx, ndy);
-    const int g = hn / 3;
+    // |(da, dc)| = |e|: one reciprocal square root normalises it (rsqrtf's error, a few 1e-7,
+    // does not accumulate: every step renormalises the direction it receives)
+    const float re = rsqrtf(fmaf(da, da, dc * dc));
+    const float ndx = (fl ? da : -da) * re, ndy = dc * re;
     {
-        const int k = w.h - 3 * w.f;
+        const int k = w.h - 3 * (w.h / 3);
+        const int g = hn / 3;
         hook.on_cross(w, Cross{right ? nxt(k) : prv(k), x0, y0, x1, y1, qx, qy, w.Lh + w.Ll, g, hn - 3 * g, fl,
                                0.f, 0.f, hl(G), 0.f, ndx, ndy, hca(R), hsa(R), hca(G), hsa(G)},
                       G);
@@ -539,12 +542,11 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     w.px = fl ? s : 1.f - s;
     w.py = 0.f;
     w.dx = ndx; w.dy = ndy;
-    w.f = g;
     w.h = hn;
     w.R = G;
     if (fl) w.st ^= SG_PARITY_BIT;
     w.ncross++;
-    walker_hash(w, g, P.want_hash);
+    if (P.want_hash) walker_hash(w, hn / 3, 1);
     return false;
 }
 
