@@ -269,6 +269,114 @@ def run_multimesh(args):
         open(args.json_out, "w").write(json.dumps(line) + "\n")
 
 
+def run_config(args, index):
+    """Forward throughput and accuracy on one of the single-mesh workloads: 0 (icosphere s3, 4096
+    queries, 1 carried vector), 1 (torus 262k faces, 4M queries, 2 carried vectors) or 4 (sliver
+    heightfield 4.2M faces, 16M queries; also EP / GFD backward and the FP64 walk).  Variants: the
+    persistent kernel (start-face sort, FP64 classification) and the plain one-thread-per-query
+    FP32 kernel; accuracy of each against the FP64 oracle on a sample of 2000 queries."""
+    import torch
+    import meshgen
+    import oracle
+    import paper_2603_15780_gb300 as sg
+    dev = torch.device("cuda", 0)
+    wl = meshgen.workload(index)
+    X, F = wl.single
+    q = wl.queries
+    nq = len(q)
+    nw = {0: 1, 1: 2, 4: 0}[index]
+    X32 = np.ascontiguousarray(X, np.float32)
+    mesh = sg.Mesh(X32, F)
+    T = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    face, bary, v = T(q.face, torch.int32), T(q.bary), T(q.v)
+    w = T(q.w[:, :nw]) if nw else None
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    steps = args.steps if index != 4 else min(args.steps, 5)
+
+    def timed(fn, n_steps):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(n_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    variants = {"persistent": sg.default_opts(),
+                "plain": sg.default_opts(kernel=sg.KERNEL_PLAIN, sort=0, fp64_escalate=0)}
+    res, outs = {}, {}
+    clk = Clocks(0, os.path.join(ROOT, "gpurun_out", f"clocks_w{index}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_w.csv")
+    for name, o in variants.items():
+        out = sg.exp_map(mesh, face, bary, v, w, opts=o)
+        ws = out.pop("_workspace", None)
+        t = timed(lambda: sg.exp_map(mesh, face, bary, v, w, opts=o, workspace=ws, out=out), steps)
+        nc = int(out["ncross"].sum().item())
+        res[name] = {"ms": t, "geodesics_per_s": nq / (t * 1e-3), "crossings_per_s": nc / (t * 1e-3)}
+        outs[name] = out
+    sub64 = None
+    if index == 4:
+        # the full-precision walk on the first 1M queries
+        n64 = min(nq, 1 << 20)
+        sub64 = n64
+        o64 = sg.default_opts(precision=64)
+        out = sg.exp_map(mesh, face[:n64], bary[:n64], v[:n64], opts=o64)
+        ws = out.pop("_workspace", None)
+        t = timed(lambda: sg.exp_map(mesh, face[:n64], bary[:n64], v[:n64], opts=o64, workspace=ws, out=out), 3)
+        nc = int(out["ncross"].sum().item())
+        res["fp64"] = {"ms": t, "queries": n64, "geodesics_per_s": n64 / (t * 1e-3), "crossings_per_s": nc / (t * 1e-3)}
+        outs["fp64"] = out
+        # backward at full size (EP, GFD) on the persistent forward's outputs
+        po = outs["persistent"]
+        g = T(q.g_pos)
+        for est in ("ep", "gfd"):
+            nb = sg.backward_workspace_size(mesh, est, nq, False)
+            bws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            fn = lambda: sg.exp_map_backward(mesh, est, face, bary, v, po["face"], po["bary"], po["dir"], po["status"],
+                                             g, workspace=bws)
+            t = timed(fn, 3)
+            res[f"bwd_{est}"] = {"ms": t, "geodesics_per_s": nq / (t * 1e-3)}
+    clocks = clk.stop()
+    # accuracy against the oracle on 2000 queries
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(nq if sub64 is None else sub64, 2000, replace=False))
+    om = oracle.Mesh(X32.astype(np.float64), F)
+    f64 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    acc = {}
+    for name, o_kw in (("persistent", {}), ("plain", {}), ("fp64", {"tau_snap": 1e-12})):
+        if name not in outs:
+            continue
+        ref = oracle.exp_map(om, q.face[idx], f64(q.bary[idx]), f64(q.v[idx]),
+                             f64(q.w[idx, :nw]) if nw else None, **o_kw)
+        o = outs[name]
+        st = o["status"][idx].cpu().numpy().astype(np.uint32)
+        fl = ((st | ref["status"]) & 12) != 0
+        err = np.linalg.norm(o["pos"][idx].cpu().numpy() - ref["pos"], axis=1) / meshgen.bbox_diag(X)
+        same = o["face"][idx].cpu().numpy() == ref["face"]
+        acc[name] = {"flagged": float(fl.mean()), "same_end_face_unflagged": float(same[~fl].mean()),
+                     "max_pos_err_over_diag_unflagged": float(err[~fl].max()),
+                     "median_pos_err_over_diag": float(np.median(err)),
+                     "frac_within_1e-5_diag": float((err <= 1e-5).mean())}
+    name = {0: "icosphere-s3 1280F 4096q 1w", 1: "torus 512x256 262144F 4Mq 2w",
+            4: "heightfield 1449^2 4.2MF slivers 16Mq"}[index]
+    line = {"metric": "geodesics/s forward (persistent)", "value": res["persistent"]["geodesics_per_s"],
+            "unit": "geodesics/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": res["persistent"]["ms"], "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "queries": nq, "faces": int(mesh.n_faces), "carried_vectors": nw,
+                       "l2": "flushed between steps (512 MB write)"},
+            "variants": res, "speedup_vs_plain": res["plain"]["ms"] / res["persistent"]["ms"],
+            "accuracy_vs_oracle_2000": acc, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    if args.json_out:
+        open(args.json_out, "w").write(json.dumps(line) + "\n")
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -286,7 +394,8 @@ def main():
     ap.add_argument("--fp64", type=int, default=1)
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--no-autotune", action="store_true", help="multimesh: default persistent options")
-    ap.add_argument("--workload", default="fwdbwd", choices=["fwdbwd", "multimesh"],
+    ap.add_argument("--workload", default="fwdbwd",
+                    choices=["fwdbwd", "multimesh", "icosphere-s3", "torus", "heightfield"],
                     help="fwdbwd: the headline step; multimesh: 64 uneven meshes, plain per-mesh launches vs "
                          "one graph-captured persistent launch")
     args = ap.parse_args()
@@ -305,6 +414,9 @@ def main():
     import paper_2603_15780_gb300 as sg
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload in ("icosphere-s3", "torus", "heightfield"):
+        run_config(args, {"icosphere-s3": 0, "torus": 1, "heightfield": 4}[args.workload])
+        return
     if args.workload == "multimesh":
         if rank == 0:
             run_multimesh(args)
@@ -438,12 +550,12 @@ def main():
     # end frame gathers (vertex ids + 3 vertices: 2 x 64 B), the end face record (32 B) and the
     # outputs (face, bary, pos, dir, status, ncross: 48 B)
     walk_bytes = ncross * RECORD_BYTES + nq * (28 + 4 + 32 + 128 + 32 + 48)
-    # GFD re-walk with vertex gradients: per crossing the 32-B half-edge record and two 8-B
-    # atomic adds of half-edge coefficients; per query the inputs (28 B), start face record,
-    # frame, vertex ids and vertices (128 B), forward end state and upstream gradient with the
-    # end frame (64 B), end face record (32 B), start/end vertex atomics (6 x 16 B) and
+    # GFD re-walk with vertex gradients: per crossing the 32-B half-edge record and one 8-B
+    # atomic add into the crossed edge's coefficients; per query the inputs (28 B), start face
+    # record, frame, vertex ids and vertices (128 B), forward end state and upstream gradient
+    # with the end frame (64 B), end face record (32 B), start/end vertex atomics (6 x 16 B) and
     # end-face frame and ids (48 B), status (4 B)
-    rewalk_bytes = ncross * (RECORD_BYTES + 16) + nq * (28 + 128 + 64 + 32 + 96 + 48 + 4)
+    rewalk_bytes = ncross * (RECORD_BYTES + 8) + nq * (28 + 128 + 64 + 32 + 96 + 48 + 4)
     kern = {"k_walk_persistent": (walk_bytes, float(np.mean(ktimes["walk"]))),
             "k_bwd_rewalk": (rewalk_bytes, float(np.mean(ktimes["rewalk"])))}
     dom = max(kern, key=lambda k: kern[k][1])

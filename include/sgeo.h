@@ -71,7 +71,8 @@ typedef enum sg_status {
 typedef struct sg_opts {
     int32_t max_steps;      /* loop cap per query (Alg. gpu_parallel MAX_STEPS); <= 0: 1<<20 */
     int32_t kernel;         /* SG_KERNEL_*; AUTO = persistent */
-    int32_t sort;           /* 1: order queries by (mesh, start face) before walking; 0: no; <0: auto (on) */
+    int32_t sort;           /* 1: order queries by (mesh, start face) before walking; 0: no;
+                               <0: auto (on from 65536 queries) */
     int32_t block;          /* threads per block; <= 0: 256 */
     int32_t blocks_per_sm;  /* persistent kernel residency; <= 0: as many as fit */
     int32_t fp64_escalate;  /* 1: re-evaluate near-vertex classification in FP64 (persistent only) */
@@ -107,8 +108,8 @@ const char *sg_status_string(sg_status s);
 
 /*
  * sg_mesh_create -- build the walk records of one triangle mesh M = {X, F} (Sec. 4).
- *   V   host float32 [nV][3] vertex positions
- *   F   host int32 [nF][3] vertex indices, 0 <= F < nV
+ *   V   float32 [nV][3] vertex positions, host or device memory (detected)
+ *   F   int32 [nF][3] vertex indices, 0 <= F < nV, host or device memory (detected)
  * Builds, in FP64 on the host, the triangle adjacency (only adjacencies are stored, so
  * non-orientable meshes work, App. "Main differences with SotA implementation"), the
  * per-face intrinsic 2-D shape, the vertex total angle theta(x) (Sec. 4), boundary
@@ -122,10 +123,12 @@ sg_status sg_mesh_create(const float *V, int64_t nV, const int32_t *F, int64_t n
 /*
  * sg_mesh_create_batched -- several meshes in one object for heterogeneous batching
  * (Sec. 4 "Parallelisation on the GPU": face indices and (f, b) offset per mesh).
- *   V      host float32 [v_off[n_mesh]][3], meshes concatenated
- *   v_off  host int64 [n_mesh + 1] vertex offsets (v_off[0] = 0)
- *   F      host int32 [f_off[n_mesh]][3], indices LOCAL to each mesh's vertices
- *   f_off  host int64 [n_mesh + 1] face offsets (f_off[0] = 0)
+ *   V      float32 [v_off[n_mesh]][3], meshes concatenated
+ *   v_off  int64 [n_mesh + 1] vertex offsets (v_off[0] = 0)
+ *   F      int32 [f_off[n_mesh]][3], indices LOCAL to each mesh's vertices
+ *   f_off  int64 [n_mesh + 1] face offsets (f_off[0] = 0)
+ * Each array may be host or device memory (detected with cudaPointerGetAttributes; device
+ * arrays are copied to the host, where the adjacency is built).
  * Queries then name a mesh (mesh_id) and a face local to it.  Same errors as above.
  */
 sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int32_t *F,

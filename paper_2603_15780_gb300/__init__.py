@@ -147,13 +147,24 @@ def _dev(t, dtype, shape=None):
 
 class Mesh:
     """One mesh, or several meshes batched with CSR offsets (pass a list of (V, F)).
-    Vertex positions float32 [N,3] and faces int32 [F,3] on the host; built synchronously
-    on the current CUDA device by sg_mesh_create / sg_mesh_create_batched."""
+    Vertex positions float32 [N,3] and faces int32 [F,3], on the host or (one mesh, torch
+    tensors) on the device; built synchronously on the current CUDA device by sg_mesh_create /
+    sg_mesh_create_batched."""
 
     def __init__(self, V, F=None):
-        _torch()
+        torch = _torch()
         h = C.c_void_p()
-        if F is not None:
+        if F is not None and isinstance(V, torch.Tensor) and V.is_cuda:
+            # device arrays go to sg_mesh_create as they are (the library copies them to the host)
+            Vd = V.detach().to(torch.float32).contiguous().reshape(-1, 3)
+            Fd = torch.as_tensor(F, device=Vd.device).to(torch.int32).contiguous().reshape(-1, 3)
+            _check(lib().sg_mesh_create(_ptr(Vd), Vd.shape[0], _ptr(Fd), Fd.shape[0], C.byref(h)), "sg_mesh_create")
+            self.n_mesh = 1
+            self.v_off = np.array([0, Vd.shape[0]], np.int64)
+            self.f_off = np.array([0, Fd.shape[0]], np.int64)
+            self.V = Vd.cpu().numpy()
+            self.F = Fd.cpu().numpy()
+        elif F is not None:
             V = np.ascontiguousarray(V, dtype=np.float32).reshape(-1, 3)
             F = np.ascontiguousarray(F, dtype=np.int32).reshape(-1, 3)
             _check(lib().sg_mesh_create(V.ctypes.data_as(C.c_void_p), len(V), F.ctypes.data_as(C.c_void_p),

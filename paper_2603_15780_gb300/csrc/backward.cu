@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(256) k_ep_backward(BwdArgs A) {
 struct StraddleHook {
     float Ltot, sphi, cphi;      // e_perp wedge: opening angle atan(eps_v / L)
     float ua, ub, va, vb;        // e_u / e_v offsets along and across d0 (start frame)
+    float uq, vq;                // ua / ub and va / vb (0 when ub, vb = 0)
     float tol;
     unsigned split;
     __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy, float px, float py) {
@@ -187,11 +188,11 @@ struct StraddleHook {
         if (tau < -tol || tau > Ltot + tol) return;
         if (sig > -tol && sig * cphi - tau * sphi < tol) split |= 1u;
         if (ub > 0.f ? (sig > -tol && sig < ub + tol) : (sig < tol && sig > ub - tol)) {
-            float s = tau - (ub != 0.f ? sig / ub : 0.f) * ua;
+            float s = tau - sig * uq;
             if (s > -tol && s < Ltot + tol) split |= 2u;
         }
         if (vb > 0.f ? (sig > -tol && sig < vb + tol) : (sig < tol && sig > vb - tol)) {
-            float s = tau - (vb != 0.f ? sig / vb : 0.f) * va;
+            float s = tau - sig * vq;
             if (s > -tol && s < Ltot + tol) split |= 4u;
         }
     }
@@ -273,7 +274,6 @@ struct RewalkJob {
     int64_t q;
     uint32_t st;
     bool valid, hole_q;
-    F3 gq;
 
     __device__ __forceinline__ bool init(int64_t t) {
         q = t;
@@ -297,10 +297,11 @@ struct RewalkJob {
             H.S.ua = A->eps_p * d0x;  H.S.ub = -A->eps_p * d0y;
             H.S.va = A->eps_p * (evx * d0x + evy * d0y);
             H.S.vb = A->eps_p * (-evx * d0y + evy * d0x);
+            H.S.uq = H.S.ub != 0.f ? H.S.ua / H.S.ub : 0.f;
+            H.S.vq = H.S.vb != 0.f ? H.S.va / H.S.vb : 0.f;
         }
         if (GRADV && H.gradv) {
             EndAdj E = end_adjoint(*A, q, w.foff);
-            gq = E.g;
             H.G.eacc = A->eacc;
             H.G.a = E.a;
             H.G.bs = E.sm * E.b;
@@ -336,7 +337,7 @@ struct RewalkJob {
             const int4 fve = __ldg(A->P.fv + w.f);
             float b2 = w.py / R.x2y, b1 = (w.px - b2 * R.x2x) / R.l01, b0 = 1.f - b1 - b2;
             F3 n = nrm_of(load_frm(A->P, w.f));
-            F3 gn = dot3(gq, n) * n;
+            F3 gn = dot3(ld3(A->g_pos, q), n) * n;  // g (reloaded rather than kept through the walk)
             atomic_add3(A->gacc, fve.x, b0 * gn);
             atomic_add3(A->gacc, fve.y, b1 * gn);
             atomic_add3(A->gacc, fve.z, b2 * gn);

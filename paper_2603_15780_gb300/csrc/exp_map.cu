@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "sgeo_internal.h"
 #include "walk.cuh"
@@ -294,7 +295,11 @@ WsLayout ws_layout(int64_t nF, int64_t nq, bool sort) {
     return L;
 }
 
-sg_opts resolve(const sg_opts *o) {
+// Below this batch size the start-face sort costs more (five small launches) than the gather
+// coherence it buys, so the automatic choice (sort < 0) leaves it off.
+#define SG_SORT_MIN_BATCH 65536
+
+sg_opts resolve(const sg_opts *o, int64_t nq) {
     sg_opts r;
     sg_opts_default(&r);
     if (o) r = *o;
@@ -304,7 +309,7 @@ sg_opts resolve(const sg_opts *o) {
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
     if (r.tau_snap <= 0.f) r.tau_snap = r.precision == 64 ? 1e-12f : 1e-6f;
     if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
-    if (r.sort < 0) r.sort = 1;
+    if (r.sort < 0) r.sort = nq >= SG_SORT_MIN_BATCH ? 1 : 0;
     if (r.kernel == SG_KERNEL_PLAIN) { r.sort = 0; r.fp64_escalate = 0; }
     return r;
 }
@@ -382,10 +387,53 @@ const char *sg_status_string(sg_status s) {
 
 const char *sg_version(void) { return "sgeo 0.1 (sm_103a)"; }
 
+}  // extern "C"
+
+namespace {
+
+// true when p is CUDA device (or managed) memory; host pointers, registered or not, are false
+bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// host copy of `n` elements of p when p is device memory (the builder runs on the host)
+template <class T>
+const T *host_view(const T *p, size_t n, std::vector<T> &buf, bool *err) {
+    if (!p || !on_device(p)) return p;
+    buf.resize(std::max<size_t>(n, 1));
+    if (cudaMemcpy(buf.data(), p, sizeof(T) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        *err = true;
+    }
+    return buf.data();
+}
+
+}  // namespace
+
+extern "C" {
+
 sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int32_t *F, const int64_t *f_off,
                                  int32_t n_mesh, sg_mesh **out) {
     if (!out) return SG_ERR_INVALID_ARG;
     *out = nullptr;
+    if (!V || !v_off || !F || !f_off || n_mesh <= 0) return SG_ERR_INVALID_ARG;
+    // any of the four arrays may live in device memory: copy those to the host first
+    bool err = false;
+    std::vector<int64_t> vo_buf, fo_buf;
+    std::vector<float> v_buf;
+    std::vector<int32_t> f_buf;
+    v_off = host_view(v_off, (size_t)n_mesh + 1, vo_buf, &err);
+    f_off = host_view(f_off, (size_t)n_mesh + 1, fo_buf, &err);
+    if (err) return SG_ERR_CUDA;
+    if (v_off[n_mesh] <= 0 || f_off[n_mesh] <= 0) return SG_ERR_INVALID_ARG;
+    V = host_view(V, 3 * (size_t)v_off[n_mesh], v_buf, &err);
+    F = host_view(F, 3 * (size_t)f_off[n_mesh], f_buf, &err);
+    if (err) return SG_ERR_CUDA;
     sg_host_mesh H;
     sg_status st = sg_build_host_mesh(V, v_off, F, f_off, n_mesh, &H);
     if (st != SG_OK) return st;
@@ -474,7 +522,7 @@ sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info) {
 
 sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts *o, size_t *bytes) {
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
-    sg_opts r = resolve(o);
+    sg_opts r = resolve(o, nq);
     *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT && r.sort).total;
     return SG_OK;
 }
@@ -546,7 +594,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (nq > (int64_t)INT32_MAX - 1024) return SG_ERR_INVALID_ARG;
     if (!face || !bary || !v || !out_face || !out_bary || !out_pos || !out_dir || !out_status) return SG_ERR_INVALID_ARG;
     if (n_w > 0 && !w) return SG_ERR_INVALID_ARG;
-    sg_opts r = resolve(o);
+    sg_opts r = resolve(o, nq);
     if (r.kernel != SG_KERNEL_PLAIN && r.kernel != SG_KERNEL_PERSISTENT) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
@@ -614,7 +662,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
     if (!face || !bary || !v || !out_face || !out_bary || !out_pos || !out_dir || !out_status || !out_path_len)
         return SG_ERR_INVALID_ARG;
     if (path_cap > 0 && !out_path_face) return SG_ERR_INVALID_ARG;
-    sg_opts r = resolve(o);
+    sg_opts r = resolve(o, nq);
     if (r.boundary_mode || r.precision == 64) return SG_ERR_UNSUPPORTED;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

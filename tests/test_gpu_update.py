@@ -150,3 +150,17 @@ def test_descent_step_along_grad_V():
     actual = float(((out2["pos"].double() - out["pos"].double()) * gk.double()).sum())
     assert pred < 0
     assert abs(actual - pred) <= 0.05 * abs(pred), (actual, pred)
+
+
+def test_mesh_from_device_arrays_equals_host_build():
+    """sg_mesh_create with V and F in device memory (detected, copied to the host) builds the
+    same records as from host arrays: identical walks."""
+    import torch
+    rng = np.random.default_rng(45)
+    X, F = meshgen.icosphere(3, 0.004, rng)
+    X32 = parity.as_f32(X)
+    q = meshgen.sample_queries(X, F, 3000, rng, 0.0, 1.5, 1)
+    host = parity.run_gpu(sg().Mesh(X32, F), q, 1)
+    dev = parity.run_gpu(sg().Mesh(torch.tensor(X32, device="cuda"), torch.tensor(F, device="cuda")), q, 1)
+    for k in OUT_KEYS:
+        assert np.array_equal(host[k], dev[k]), k
