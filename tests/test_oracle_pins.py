@@ -328,7 +328,10 @@ def test_cone_vertex_straightest_rule(theta):
         dvec = -p / rho
         f, b = locate(X, F, p, tol=1e-10)
         assert f == f0
-        out = oracle.exp_map(m, [f], [b], [dvec * (rho + lam)], [[np.cross(np.cross(u, w), dvec)]])
+        n0 = np.cross(u, w)
+        beta = float(rng.uniform(-math.pi, math.pi))    # carried vector at a signed angle beta
+        w0 = math.cos(beta) * dvec + math.sin(beta) * np.cross(n0, dvec)
+        out = oracle.exp_map(m, [f], [b], [dvec * (rho + lam)], [[w0]])
         assert out["status"][0] & oracle.VERTEX_HIT
         phi = (G[f0] + a + T / 2) % T
         j = int(np.searchsorted(G, phi, side="right") - 1)
@@ -340,9 +343,11 @@ def test_cone_vertex_straightest_rule(theta):
         if min(loc, gam[j] - loc) < 1e-6:
             continue  # outgoing ray along an edge (degenerate reading)
         assert np.abs(out["pos"][0] - expect).max() < 1e-12
-        # carried vector: |w| = 1 and it stays perpendicular to the direction
-        assert abs(np.linalg.norm(out["w"][0, 0]) - 1.0) < 1e-12
-        assert abs(np.dot(out["w"][0, 0], out["dir"][0])) < 1e-12
+        # carried vector: the same signed angle beta to the direction, about the end face's
+        # normal (the fan is consistently oriented)
+        nj = np.cross(uj, wj)
+        dj = out["dir"][0]
+        assert np.abs(out["w"][0, 0] - (math.cos(beta) * dj + math.sin(beta) * np.cross(nj, dj))).max() < 1e-12
         checked += 1
     assert checked > 30
 
