@@ -177,16 +177,16 @@ __global__ void __launch_bounds__(256) k_ep_backward(BwdArgs A) {
 // ------------------------------------------------------------------ re-walk hooks
 // Straddle test of the GFD perturbations against the corners the base walk meets.
 struct StraddleHook {
-    float Ltot, sphi, cphi;      // e_perp wedge: opening angle atan(eps_v / L)
-    float ua, ub, va, vb;        // e_u / e_v offsets along and across d0 (start frame)
-    float uq, vq;                // ua / ub and va / vb (0 when ub, vb = 0)
-    float tol;
+    float Ltot, tphi;            // e_perp wedge: tan of its opening angle, eps_v / L
+    float ub, vb;                // e_u / e_v offsets across d0 (start frame)
+    float uq, vq;                // offsets along d0 over those across (0 when ub, vb = 0)
+    float tol;                   // tau_near l_ref (1 + tphi^2), at least tau_near l_ref / cos(phi)
     unsigned split;
     __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy, float px, float py) {
         float tau = (Ltot - (w.Lh + w.Ll)) + (cx - px) * w.dx + (cy - py) * w.dy;
         float sig = (w.st & SG_PARITY_BIT) ? -sig_loc : sig_loc;
         if (tau < -tol || tau > Ltot + tol) return;
-        if (sig > -tol && sig * cphi - tau * sphi < tol) split |= 1u;
+        if (sig > -tol && sig - tau * tphi < tol) split |= 1u;
         if (ub > 0.f ? (sig > -tol && sig < ub + tol) : (sig < tol && sig > ub - tol)) {
             float s = tau - sig * uq;
             if (s > -tol && s < Ltot + tol) split |= 2u;
@@ -272,8 +272,7 @@ struct RewalkJob {
     Walker w;
     RewalkHook<GFD, GRADV> H;
     int64_t q;
-    uint32_t st;
-    bool valid, hole_q;
+    bool valid;
 
     __device__ __forceinline__ bool init(int64_t t) {
         q = t;
@@ -281,24 +280,23 @@ struct RewalkJob {
         Carry<0> cw;
         bool live = walker_init<0>(P, A->in, q, w, cw);
         valid = live && !(w.st & SG_ST_INVALID);
-        st = 0;
         if (!valid) return false;
         uint32_t fst = A->end_status ? __ldg(A->end_status + q) : 0u;
         H.gradv = GRADV && !(fst & (SG_ST_VERTEX_HIT | SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_INVALID | SG_ST_HOLE));
-        hole_q = (fst & SG_ST_HOLE) != 0;
-        if (GRADV && !H.gradv) st |= SG_ST_NO_GRADV;
+        if (GRADV && !H.gradv) w.st |= SG_ST_NO_GRADV;  // the walker never touches this bit
         const float L = w.Lh, d0x = w.dx, d0y = w.dy;
         if (GFD) {
-            sincosf(atan2f(A->eps_v, L), &H.S.sphi, &H.S.cphi);
+            H.S.tphi = A->eps_v / L;
             H.S.Ltot = L;
-            H.S.tol = P.tau_near * w.lref;
-            H.S.split = 0u;
+            H.S.tol = P.tau_near * w.lref * (1.f + H.S.tphi * H.S.tphi);
+            // a walk that slid along the boundary (hole avoidance) takes literal walks
+            H.S.split = (fst & SG_ST_HOLE) ? 7u : 0u;
             float evx = w.R.x2x * w.R.il2, evy = w.R.x2y * w.R.il2;  // e_u = (1,0), e_v = P2/|P2|
-            H.S.ua = A->eps_p * d0x;  H.S.ub = -A->eps_p * d0y;
-            H.S.va = A->eps_p * (evx * d0x + evy * d0y);
+            const float ua = A->eps_p * d0x, va = A->eps_p * (evx * d0x + evy * d0y);
+            H.S.ub = -A->eps_p * d0y;
             H.S.vb = A->eps_p * (-evx * d0y + evy * d0x);
-            H.S.uq = H.S.ub != 0.f ? H.S.ua / H.S.ub : 0.f;
-            H.S.vq = H.S.vb != 0.f ? H.S.va / H.S.vb : 0.f;
+            H.S.uq = H.S.ub != 0.f ? ua / H.S.ub : 0.f;
+            H.S.vq = H.S.vb != 0.f ? va / H.S.vb : 0.f;
         }
         if (GRADV && H.gradv) {
             EndAdj E = end_adjoint(*A, q, w.foff);
@@ -330,7 +328,7 @@ struct RewalkJob {
             if (A->out_status) A->out_status[q] = (w.st & ~SG_PARITY_BIT) | (GRADV ? SG_ST_NO_GRADV : 0u);
             return;
         }
-        st |= w.st & ~SG_PARITY_BIT;
+        uint32_t st = w.st & ~SG_PARITY_BIT;
         if (GRADV && H.gradv) {
             // end face: grad x_j += b'_j (g . n) n
             const FaceRec &R = w.R;
@@ -347,7 +345,7 @@ struct RewalkJob {
             // (hole avoidance), takes literal walks for all perturbed columns; the par column
             // is the chord from p' in every case (Round 2 of the paper's batching).
             unsigned split = H.S.split;
-            if ((w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) || hole_q) split = 7u;
+            if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) split = 7u;
             if (split) {
                 st |= SG_ST_GFD_SPLIT;
                 int base = atomicAdd(A->ntask, __popc(split));
@@ -360,7 +358,7 @@ struct RewalkJob {
 };
 
 template <bool GFD, bool GRADV>
-__global__ void __launch_bounds__(128, 6) k_bwd_rewalk(BwdArgs A) {
+__global__ void __launch_bounds__(128, 7) k_bwd_rewalk(BwdArgs A) {
     RewalkJob<GFD, GRADV> job;
     job.A = &A;
     run_persistent(A.ntask + 1, A.nq, job);
@@ -393,6 +391,16 @@ __device__ F3 pos_diff(const WalkParams &P, const Walker &a, const Walker &b) {
 // (face frame), as the cancellation-free difference of the end and start positions
 template <bool HOLE>
 __device__ F3 short_chord(const WalkParams &P, const Walker &w0, float ux, float uy, float len) {
+    // a chord that ends inside the end face, farther than tau_near l_ref from its edges, is the
+    // lifted step itself (no walk, and no cancellation of the two end positions)
+    {
+        const FaceRec &R = w0.R;
+        const float x = fmaf(len, ux, w0.px), y = fmaf(len, uy, w0.py);
+        const float tol = P.tau_near * w0.lref;
+        const float e1 = ((R.x2x - R.l01) * y - R.x2y * (x - R.l01)) * R.il1;
+        const float e2 = (R.x2y * x - R.x2x * y) * R.il2;
+        if (y > tol && e1 > tol && e2 > tol) return lift(load_frm(P, w0.f), len * ux, len * uy);
+    }
     Walker w = w0;
     w.dx = ux; w.dy = uy; w.Lh = len; w.Ll = 0.f; w.mode = 6; w.steps = 0;
     while (!walker_step<true, HOLE>(w, P)) {
