@@ -692,8 +692,9 @@ static int om_init(const om_mesh *m, int64_t f, const double *b, const double *v
         vcopy(w + 3 * q, w_in + 3 * q);
         vaxpy(w + 3 * q, -vdot(w + 3 * q, n), n);
     }
+    if (!(L <= 1e300)) return 1;  /* a non-finite vector is invalid input */
     if (len) {
-        if (!(*len >= 0.0)) return 1;
+        if (!(*len >= 0.0 && *len <= 1e300)) return 1;
         if (L == 0.0 && *len > 0.0) return 1;
         s->L = *len;
     } else {

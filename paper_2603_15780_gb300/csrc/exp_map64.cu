@@ -297,7 +297,7 @@ struct Job64 {
         const double v1 = vx * fr[0] + vy * fr[1] + vz * fr[2], v2 = vx * fr[3] + vy * fr[4] + vz * fr[5];
         const double Lv = sqrt(v1 * v1 + v2 * v2);
         const double L = in.length ? (double)__ldg(in.length + q) : Lv;
-        if (!(L >= 0.0) || (Lv == 0.0 && L > 0.0)) { w.st |= SG_ST_INVALID; return false; }
+        if (!(L >= 0.0 && L <= 1.0e300) || !(Lv <= 1.0e300) || (Lv == 0.0 && L > 0.0)) { w.st |= SG_ST_INVALID; return false; }
         if (Lv > 0.0) { w.dx = v1 / Lv; w.dy = v2 / Lv; }
         w.L = L;
         for (int k = 0; k < NW; ++k) {

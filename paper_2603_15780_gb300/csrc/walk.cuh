@@ -786,7 +786,8 @@ __device__ bool walker_init(const WalkParams &P, const QueryIn &a, int64_t q, Wa
     float v2 = vx * F.e2x + vy * F.e2y + vz * F.e2z;
     float Lv = sqrtf(v1 * v1 + v2 * v2);
     float L = a.length ? __ldg(a.length + q) : Lv;
-    if (!(L >= 0.f) || (Lv == 0.f && L > 0.f)) {
+    // a non-finite vector or length is invalid input (comparisons with NaN are false)
+    if (!(L >= 0.f && L <= 3.0e38f) || !(Lv <= 3.0e38f) || (Lv == 0.f && L > 0.f)) {
         w.st |= SG_ST_INVALID;
         w.dx = w.dy = 0.f; w.Lh = 0.f;
         for (int k = 0; k < NW; ++k) { cw.c[k] = 0.f; cw.s[k] = 0.f; }
