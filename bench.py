@@ -377,6 +377,109 @@ def run_config(args, index):
         open(args.json_out, "w").write(json.dumps(line) + "\n")
 
 
+def run_features(args):
+    """Throughput of the features beyond the headline step, each on the workload named in its
+    entry (CUDA events, L2 flushed between steps, median of the timed steps):
+      trace      sg_exp_map_trace on the icosphere-s6 workload (1M queries, 64 path entries)
+                 against sg_exp_map on the same queries;
+      fp64       the full-precision walk on the same workload against the FP32 walk;
+      hole       hole avoidance on the icosphere s6 with 8% of its faces removed (1M queries)
+                 against the stopping walk;
+      update     sg_mesh_update_vertices on the icosphere s6 (81,920 faces);
+      k_step     exp_map_steps with K = 5 and a linear field on 1M queries, forward and
+                 forward + GFD backward through all steps."""
+    import torch
+    import meshgen
+    import paper_2603_15780_gb300 as sg
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    n_steps = max(3, min(args.steps, 20))
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(n_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    T = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    wl = meshgen.workload(2)
+    X, F = wl.single
+    q = wl.queries
+    nq = len(q)
+    X32 = np.ascontiguousarray(X, np.float32)
+    mesh = sg.Mesh(X32, F)
+    face, bary, v = T(q.face, torch.int32), T(q.bary), T(q.v)
+    res = {}
+    out = sg.exp_map(mesh, face, bary, v)
+    ws = out.pop("_workspace")
+    t_fwd = timed(lambda: sg.exp_map(mesh, face, bary, v, workspace=ws, out=out))
+    res["exp_map"] = {"ms": t_fwd, "geodesics_per_s": nq / (t_fwd * 1e-3)}
+    t_tr = timed(lambda: sg.exp_map_trace(mesh, face, bary, v, path_cap=64, workspace=ws))
+    res["trace"] = {"ms": t_tr, "geodesics_per_s": nq / (t_tr * 1e-3), "path_cap": 64,
+                    "path_bytes_per_query": 64 * 16, "vs_exp_map": t_tr / t_fwd}
+    o64 = sg.default_opts(precision=64)
+    out64 = sg.exp_map(mesh, face, bary, v, opts=o64)
+    ws64 = out64.pop("_workspace")
+    t64 = timed(lambda: sg.exp_map(mesh, face, bary, v, opts=o64, workspace=ws64, out=out64))
+    res["fp64"] = {"ms": t64, "geodesics_per_s": nq / (t64 * 1e-3), "vs_fp32": t64 / t_fwd}
+    # update: positions with fresh radial noise
+    rng = np.random.default_rng(5)
+    Vn = T(X32 * (1.0 + 0.003 * rng.standard_normal((len(X32), 1))).astype(np.float32))
+    Vo = T(X32)
+    flip = [Vn, Vo]
+    k = [0]
+
+    def upd():
+        mesh.update_vertices(flip[k[0] & 1])
+        k[0] += 1
+    t_up = timed(upd)
+    mesh.update_vertices(Vo)
+    res["update_vertices"] = {"ms": t_up, "faces": int(mesh.n_faces), "faces_per_s": mesh.n_faces / (t_up * 1e-3)}
+    # K-step with a linear field
+    A = torch.tensor(0.8 * rng.standard_normal((3, 3)), dtype=torch.float32, device=dev)
+    t_k = timed(lambda: sg.exp_map_steps(mesh, face, bary, lambda x, kk: x @ A.T, 5, "gfd"))
+    Ag = A.clone().requires_grad_(True)
+    gK = torch.randn(nq, 3, device=dev)
+
+    def kstep_bwd():
+        xK = sg.exp_map_steps(mesh, face, bary, lambda x, kk: x @ Ag.T, 5, "gfd")[0]
+        (xK * gK).sum().backward()
+    t_kb = timed(kstep_bwd)
+    res["k_step"] = {"K": 5, "fwd_ms": t_k, "fwd_bwd_gfd_ms": t_kb, "geodesics_per_s_fwd": 5 * nq / (t_k * 1e-3)}
+    # hole avoidance on the sphere with 8% of its faces removed
+    rngh = np.random.default_rng(6)
+    Xh, Fh = meshgen.remove_faces(X, F, 0.08, rngh)
+    qh = meshgen.sample_queries(Xh, Fh, nq, rngh, 0.1, 1.0, 0)
+    mh = sg.Mesh(np.ascontiguousarray(Xh, np.float32), Fh)
+    fh, bh, vh = T(qh.face, torch.int32), T(qh.bary), T(qh.v)
+    for name, o in (("stop", sg.default_opts()), ("hole", sg.default_opts(boundary_mode=1))):
+        oh = sg.exp_map(mh, fh, bh, vh, opts=o)
+        wsh = oh.pop("_workspace")
+        th = timed(lambda: sg.exp_map(mh, fh, bh, vh, opts=o, workspace=wsh, out=oh))
+        st = oh["status"].cpu().numpy()
+        res[f"holey_sphere_{name}"] = {"ms": th, "geodesics_per_s": nq / (th * 1e-3),
+                                       "boundary_frac": float(((st & 1) != 0).mean()),
+                                       "hole_frac": float(((st & 2048) != 0).mean())}
+    line = {"metric": "feature throughput (see entries)", "value": res["trace"]["geodesics_per_s"],
+            "unit": "geodesics/s", "n_gpus": 1, "steps": n_steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "icosphere-s6-noisy 81920F 1Mq (holey: 8% faces removed)",
+                       "l2": "flushed between steps (512 MB write)"},
+            "features": res}
+    print(json.dumps(line), flush=True)
+    if args.json_out:
+        open(args.json_out, "w").write(json.dumps(line) + "\n")
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -395,7 +498,7 @@ def main():
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--no-autotune", action="store_true", help="multimesh: default persistent options")
     ap.add_argument("--workload", default="fwdbwd",
-                    choices=["fwdbwd", "multimesh", "icosphere-s3", "torus", "heightfield"],
+                    choices=["fwdbwd", "multimesh", "icosphere-s3", "torus", "heightfield", "features"],
                     help="fwdbwd: the headline step; multimesh: 64 uneven meshes, plain per-mesh launches vs "
                          "one graph-captured persistent launch")
     args = ap.parse_args()
@@ -414,6 +517,9 @@ def main():
     import paper_2603_15780_gb300 as sg
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "features":
+        run_features(args)
+        return
     if args.workload in ("icosphere-s3", "torus", "heightfield"):
         run_config(args, {"icosphere-s3": 0, "torus": 1, "heightfield": 4}[args.workload])
         return
@@ -519,23 +625,38 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in hb.values())
         d2h = sum(t.numel() * t.element_size() for t in host_out.values())
         e_ms = []
+        # copies that do not gate the next kernel run on a second stream: the upstream gradient
+        # goes up while the forward walks, the end points come down while the backward runs
+        side = torch.cuda.Stream(device=dev)
         for k in range(args.steps + 1):
             flush.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            side.wait_event(e0)
+            with torch.cuda.stream(side):
+                gd = hb["g"].to(dev, non_blocking=True)
+                g_ready = torch.cuda.Event()
+                g_ready.record(side)
             fd = hb["face"].to(dev, non_blocking=True)
             bd = hb["bary"].to(dev, non_blocking=True)
             vd = hb["v"].to(dev, non_blocking=True)
-            gd = hb["g"].to(dev, non_blocking=True)
             o = sg.exp_map(mesh, fd, bd, vd, workspace=ws, opts=opts)
+            fwd_done = torch.cuda.Event()
+            fwd_done.record(stream)
+            side.wait_event(fwd_done)
+            with torch.cuda.stream(side):
+                host_out["pos"].copy_(o["pos"], non_blocking=True)
+                o["pos"].record_stream(side)
+            stream.wait_event(g_ready)
+            gd.record_stream(stream)
             sg.exp_map_backward(mesh, "ep", fd, bd, vd, o["face"], o["bary"], o["dir"], o["status"], gd)
             gV.zero_()
             r = sg.exp_map_backward(mesh, "gfd", fd, bd, vd, o["face"], o["bary"], o["dir"], o["status"], gd,
                                     eps_v=EPS, eps_p=EPS, grad_V=gV)
             host_out["grad_v"].copy_(r["grad_v"], non_blocking=True)
             host_out["grad_p"].copy_(r["grad_p"], non_blocking=True)
-            host_out["pos"].copy_(o["pos"], non_blocking=True)
+            stream.wait_stream(side)
             e1.record(stream)
             torch.cuda.synchronize()
             if k > 0:

@@ -288,7 +288,7 @@ def exp_map_trace(mesh: Mesh, face, bary, v, length=None, mesh_id=None, *, path_
     Returns dict(face, bary, pos, dir, status, ncross, hash (if want_hash), path_face [nq, cap],
     path_pt [nq, cap, 3] (if want_points), path_len [nq]).  The polyline of query i is
     path_pt[i, :path_len[i]] followed by pos[i] when path_len[i] <= path_cap; path entries
-    past path_len are not written (the tensors start as -1 / 0)."""
+    past path_len are not written (their contents are unspecified)."""
     torch = _torch()
     face = _dev(face, torch.int32)
     nq = face.numel()
@@ -302,10 +302,10 @@ def exp_map_trace(mesh: Mesh, face, bary, v, length=None, mesh_id=None, *, path_
            "bary": torch.empty(nq, 3, device=dev), "pos": torch.empty(nq, 3, device=dev),
            "dir": torch.empty(nq, 3, device=dev), "status": torch.empty(nq, dtype=torch.int32, device=dev),
            "ncross": torch.empty(nq, dtype=torch.int32, device=dev),
-           "path_face": torch.full((nq, path_cap), -1, dtype=torch.int32, device=dev),
+           "path_face": torch.empty(nq, path_cap, dtype=torch.int32, device=dev),
            "path_len": torch.empty(nq, dtype=torch.int32, device=dev)}
     if want_points:
-        out["path_pt"] = torch.zeros(nq, path_cap, 3, device=dev)
+        out["path_pt"] = torch.empty(nq, path_cap, 3, device=dev)
     if want_hash:
         out["hash"] = torch.empty(nq, dtype=torch.int64, device=dev)
     if workspace is None:

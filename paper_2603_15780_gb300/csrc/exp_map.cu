@@ -94,9 +94,18 @@ struct FwdJob {
     __device__ __forceinline__ void finish() { walker_finish<NW>(*a, q, w, cw); }
 };
 
-template <int NW, bool ESC, bool HOLE = false>
+template <int NW, bool ESC>
 __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
-    FwdJob<NW, ESC, HOLE> job;
+    FwdJob<NW, ESC, false> job;
+    job.a = &a;
+    run_persistent(a.counter, a.nq, job);
+}
+
+// hole avoidance (boundary_mode 1): the boundary handling needs more registers than the
+// default walk, so it gets its own kernel with a lower residency bound instead of spilling
+template <int NW>
+__global__ void __launch_bounds__(256, 4) k_walk_hole(FwdArgs a) {
+    FwdJob<NW, true, true> job;
     job.a = &a;
     run_persistent(a.counter, a.nq, job);
 }
@@ -107,11 +116,28 @@ __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
 // start point, then each edge crossing point or, after a vertex hit, the vertex).  Inside a
 // face the straightest geodesic is a straight segment, so these points followed by the end
 // point are the polyline of the geodesic.
+//
+// The walk records each entry point in the entered face's own terms -- the fraction along its
+// entry edge, or the start barycentrics -- and a second, fully parallel pass turns these into
+// 3-D points: computing them during the walk would add two dependent gathers (vertex ids, then
+// positions) to every crossing.
 struct TraceOut {
     int32_t cap;
     int32_t *face;  // [nq][cap] local face ids
     float *pt;      // [nq][cap][3] entry points, or NULL
     int32_t *len;   // [nq] faces entered (may exceed cap; entries past cap are dropped)
+    int staged;     // 1: entries are written 8 at a time with 16-byte stores (cap % 4 == 0,
+                    // 16-byte aligned buffers); 0: one entry at a time
+};
+
+// Entries of one lane are collected in shared memory and written 8 at a time: a lane's entries
+// are contiguous in its query's row, so 8 of them fill whole sectors, where single entries
+// written at different times by the lanes of a warp touch a separate sector each.
+#define SG_TRACE_STAGE 8
+struct TraceStage {
+    int face[SG_TRACE_STAGE][256];
+    float a[SG_TRACE_STAGE][256];
+    int code[SG_TRACE_STAGE][256];
 };
 
 template <bool ESC>
@@ -122,11 +148,41 @@ struct TraceJob {
     Carry<0> cw;
     int64_t q;
     int n;
-    __device__ __forceinline__ void rec(float x, float y, float z) {
+    TraceStage *sg;
+    // code 0..2: on local edge `code` at fraction a from its first corner; 3: the start point
+    // (the second pass reads its barycentrics from the query)
+    __device__ __forceinline__ void put(int64_t i, int face, float a, int code) {
+        t->face[i] = face;
+        if (t->pt) { t->pt[3 * i] = a; t->pt[3 * i + 1] = __int_as_float(code); }
+    }
+    __device__ __forceinline__ void flush8(int base) {
+        const int tid = threadIdx.x;
+        const int64_t i = q * t->cap + base;
+        int4 *fo = reinterpret_cast<int4 *>(t->face + i);
+        fo[0] = make_int4(sg->face[0][tid], sg->face[1][tid], sg->face[2][tid], sg->face[3][tid]);
+        fo[1] = make_int4(sg->face[4][tid], sg->face[5][tid], sg->face[6][tid], sg->face[7][tid]);
+        if (t->pt) {
+            float4 *po = reinterpret_cast<float4 *>(t->pt + 3 * i);
+            float a[8], c[8];
+            for (int j = 0; j < 8; ++j) { a[j] = sg->a[j][tid]; c[j] = __int_as_float(sg->code[j][tid]); }
+            po[0] = make_float4(a[0], c[0], 0.f, a[1]);
+            po[1] = make_float4(c[1], 0.f, a[2], c[2]);
+            po[2] = make_float4(0.f, a[3], c[3], 0.f);
+            po[3] = make_float4(a[4], c[4], 0.f, a[5]);
+            po[4] = make_float4(c[5], 0.f, a[6], c[6]);
+            po[5] = make_float4(0.f, a[7], c[7], 0.f);
+        }
+    }
+    __device__ __forceinline__ void rec(float a, int code) {
         if (n < t->cap) {
-            const int64_t i = q * t->cap + n;
-            t->face[i] = w.f - w.foff;
-            if (t->pt) { t->pt[3 * i] = x; t->pt[3 * i + 1] = y; t->pt[3 * i + 2] = z; }
+            const int face = w.f - w.foff;
+            if (t->staged) {
+                const int j = n & (SG_TRACE_STAGE - 1), tid = threadIdx.x;
+                sg->face[j][tid] = face; sg->a[j][tid] = a; sg->code[j][tid] = code;
+                if (j == SG_TRACE_STAGE - 1) flush8(n - (SG_TRACE_STAGE - 1));
+            } else {
+                put(q * t->cap + n, face, a, code);
+            }
         }
         n++;
     }
@@ -134,15 +190,7 @@ struct TraceJob {
         q = a->perm ? (int64_t)__ldg(a->perm + tk) : tk;
         n = 0;
         const bool live = walker_init<0>(a->P, a->in, q, w, cw);
-        if (live && w.Lh > 0.f) {  // Exp_p(0) = p enters no face
-            const float *b = a->in.bary + 3 * q;
-            float b0 = fmaxf(__ldg(b), 0.f), b1 = fmaxf(__ldg(b + 1), 0.f), b2 = fmaxf(__ldg(b + 2), 0.f);
-            const float rs = 1.f / (b0 + b1 + b2);
-            b0 *= rs; b1 *= rs; b2 *= rs;
-            const int4 t3 = __ldg(a->P.fv + w.f);
-            const float4 x0 = __ldg(a->P.V + t3.x), x1 = __ldg(a->P.V + t3.y), x2 = __ldg(a->P.V + t3.z);
-            rec(b0 * x0.x + b1 * x1.x + b2 * x2.x, b0 * x0.y + b1 * x1.y + b2 * x2.y, b0 * x0.z + b1 * x1.z + b2 * x2.z);
-        }
+        if (live && w.Lh > 0.f) rec(0.f, 3);  // Exp_p(0) = p enters no face
         return live;
     }
     __device__ __forceinline__ bool step() {
@@ -152,29 +200,69 @@ struct TraceJob {
             // entered face h / 3 through its local edge k at fraction px from corner k (in the
             // half-edge mode the walker does not keep w.f up to date)
             if (w.mode == SG_MODE_HALF) w.f = w.h / 3;
-            const int k = w.h - 3 * w.f;
-            const int4 t3 = __ldg(a->P.fv + w.f);
-            const float4 xa = __ldg(a->P.V + sel3(k, t3.x, t3.y, t3.z)), xb = __ldg(a->P.V + sel3(nxt(k), t3.x, t3.y, t3.z));
-            rec(fmaf(w.px, xb.x - xa.x, xa.x), fmaf(w.px, xb.y - xa.y, xa.y), fmaf(w.px, xb.z - xa.z, xa.z));
+            rec(w.px, w.h - 3 * w.f);
         } else if (!done && w.mode >= 3 && w.mode < 6) {
             // a vertex transport left the walker on corner mode-3 of face w.f
-            const int4 t3 = __ldg(a->P.fv + w.f);
-            const float4 xv = __ldg(a->P.V + sel3(w.mode - 3, t3.x, t3.y, t3.z));
-            rec(xv.x, xv.y, xv.z);
+            rec(0.f, w.mode - 3);
         }
         return done;
     }
     __device__ __forceinline__ void finish() {
         walker_finish<0>(*a, q, w, cw);
         t->len[q] = n;
+        if (t->staged) {  // entries still in the stage
+            const int m = min(n, t->cap), rem = m & (SG_TRACE_STAGE - 1), tid = threadIdx.x;
+            for (int j = 0; j < rem; ++j) put(q * t->cap + (m - rem) + j, sg->face[j][tid], sg->a[j][tid], sg->code[j][tid]);
+        }
     }
 };
 
+// Entries of the trace: from the face's own terms to 3-D points, in place.  One warp per query
+// (its entries are contiguous, so the lanes read and write them together).
+__global__ void __launch_bounds__(256) k_trace_points(int64_t nq, int32_t cap, const int32_t *__restrict__ len,
+                                                      const int32_t *__restrict__ path_face, float *pt,
+                                                      const int32_t *__restrict__ mesh_id,
+                                                      const float *__restrict__ bary,
+                                                      const int32_t *__restrict__ face_off, const int4 *__restrict__ fv,
+                                                      const float4 *__restrict__ V) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += nwarps) {
+        const int n = min(__ldg(len + q), cap);
+        if (n <= 0) continue;
+        const int foff = __ldg(face_off + (mesh_id ? __ldg(mesh_id + q) : 0));
+        for (int i = lane; i < n; i += 32) {
+            const int64_t e = q * cap + i;
+            const int4 t3 = __ldg(fv + foff + __ldg(path_face + e));
+            float *o = pt + 3 * e;
+            const float a = o[0];
+            const int code = __float_as_int(o[1]);
+            float w0, w1, w2;  // weights of the three corners
+            if (code == 3) {
+                const float b0 = fmaxf(__ldg(bary + 3 * q), 0.f), b1 = fmaxf(__ldg(bary + 3 * q + 1), 0.f);
+                const float b2 = fmaxf(__ldg(bary + 3 * q + 2), 0.f);
+                const float rs = 1.f / (b0 + b1 + b2);
+                w0 = b0 * rs; w1 = b1 * rs; w2 = b2 * rs;
+            } else {
+                w0 = code == 0 ? 1.f - a : (code == 2 ? a : 0.f);
+                w1 = code == 1 ? 1.f - a : (code == 0 ? a : 0.f);
+                w2 = code == 2 ? 1.f - a : (code == 1 ? a : 0.f);
+            }
+            const float4 x0 = __ldg(V + t3.x), x1 = __ldg(V + t3.y), x2 = __ldg(V + t3.z);
+            o[0] = w0 * x0.x + w1 * x1.x + w2 * x2.x;
+            o[1] = w0 * x0.y + w1 * x1.y + w2 * x2.y;
+            o[2] = w0 * x0.z + w1 * x1.z + w2 * x2.z;
+        }
+    }
+}
+
 template <bool ESC>
 __global__ void __launch_bounds__(256, 4) k_trace_persistent(FwdArgs a, TraceOut t) {
+    __shared__ TraceStage stage;
     TraceJob<ESC> job;
     job.a = &a;
     job.t = &t;
+    job.sg = &stage;
     run_persistent(a.counter, a.nq, job);
 }
 
@@ -334,11 +422,11 @@ cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
     int64_t need = (a.nq + o.block - 1) / o.block;
     if (o.boundary_mode) {  // hole avoidance: its own instantiation, FP64 classification
         if (o.blocks_per_sm <= 0) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk_persistent<NW, true, true>, o.block, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk_hole<NW>, o.block, 0);
             per = std::max(per, 1);
         }
         int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(need, 1));
-        k_walk_persistent<NW, true, true><<<(unsigned)grid, o.block, 0, s>>>(a);
+        k_walk_hole<NW><<<(unsigned)grid, o.block, 0, s>>>(a);
         return cudaGetLastError();
     }
     int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(need, 1));
@@ -670,7 +758,9 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
     a.P.want_hash = out_hash != nullptr;
     a.out_face = out_face; a.out_bary = out_bary; a.out_pos = out_pos; a.out_dir = out_dir;
     a.out_w = nullptr; a.out_status = out_status; a.out_ncross = out_ncross; a.out_hash = out_hash;
-    TraceOut t{path_cap, out_path_face, path_cap > 0 ? out_path_pt : nullptr, out_path_len};
+    TraceOut t{path_cap, out_path_face, path_cap > 0 ? out_path_pt : nullptr, out_path_len, 0};
+    t.staged = path_cap % 4 == 0 && ((uintptr_t)out_path_face % 16) == 0 &&
+               (!t.pt || ((uintptr_t)t.pt % 16) == 0);
     void *own_ws = nullptr;
     sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.sort != 0 && r.kernel != SG_KERNEL_PLAIN, s, a, &own_ws);
     if (st != SG_OK) {
@@ -689,6 +779,12 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
     int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>((nq + r.block - 1) / r.block, 1));
     if (esc) k_trace_persistent<true><<<(unsigned)grid, r.block, 0, s>>>(a, t);
     else k_trace_persistent<false><<<(unsigned)grid, r.block, 0, s>>>(a, t);
+    if (t.pt) {
+        const int64_t blocks = std::min<int64_t>((nq + 7) / 8, (int64_t)sms * 16);  // 8 warps (queries) per block
+        k_trace_points<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(nq, path_cap, out_path_len, out_path_face,
+                                                                              t.pt, mesh_id, bary, m->d_face_off,
+                                                                              m->d_fv, m->d_V);
+    }
     cudaError_t e = cudaGetLastError();
     if (own_ws) cudaFreeAsync(own_ws, s);
     if (e != cudaSuccess) {

@@ -152,8 +152,10 @@ __device__ __forceinline__ bool hole_vertex(Walker &w, const WalkParams &P, int 
         int bg = -1, bcg = 0;
         unsigned bfl = 0u;
         float bux = 0.f, buy = 0.f, berr = 3.0e38f, serr = 3.0e38f;
-        int nb = 0, ebf[2] = {0, 0}, ebc[2] = {0, 0}, ebo[2] = {0, 0};
-        unsigned ebfl[2] = {0u, 0u};
+        // the boundary edges at v0 (face, corner of v0, corner of the other end, flip), in
+        // scalars rather than arrays so that they stay in registers
+        int nb = 0, ebf0 = 0, ebc0 = 0, ebo0 = 0, ebf1 = 0, ebc1 = 0, ebo1 = 0;
+        unsigned ebfl0 = 0u, ebfl1 = 0u;
         // does face g (record Rg, v0 on its corner cg, orientation fl relative to f0) receive D?
         auto consider = [&](int g, const FaceRec &Rg, int cg, unsigned fl) {
             float e1x, e1y, e1z, e2x, e2y, e2z;
@@ -187,7 +189,9 @@ __device__ __forceinline__ bool hole_vertex(Walker &w, const WalkParams &P, int 
             for (int guard = 0; guard < 4096; ++guard) {
                 const int nbv = nbr_of(Rc, e);
                 if (nbv < 0) {  // boundary edge at v0
-                    if (nb < 2) { ebf[nb] = cur; ebc[nb] = cur_c; ebo[nb] = (e == cur_c) ? nxt(e) : e; ebfl[nb] = fl; }
+                    const int oc = (e == cur_c) ? nxt(e) : e;
+                    if (nb == 0) { ebf0 = cur; ebc0 = cur_c; ebo0 = oc; ebfl0 = fl; }
+                    else if (nb == 1) { ebf1 = cur; ebc1 = cur_c; ebo1 = oc; ebfl1 = fl; }
                     ++nb;
                     break;
                 }
@@ -220,13 +224,13 @@ __device__ __forceinline__ bool hole_vertex(Walker &w, const WalkParams &P, int 
         nb = nb > 2 ? 2 : nb;
         int k = 0;
         if (nb == 2) {
-            const int4 t0 = __ldg(P.fv + ebf[0]);
-            const int o0 = sel3(ebo[0], t0.x, t0.y, t0.z);
+            const int4 t0 = __ldg(P.fv + ebf0);
+            const int o0 = sel3(ebo0, t0.x, t0.y, t0.z);
             if (came_from >= 0) {
                 k = (o0 == came_from) ? 1 : 0;
             } else {
-                const int4 t1 = __ldg(P.fv + ebf[1]);
-                const int o1 = sel3(ebo[1], t1.x, t1.y, t1.z);
+                const int4 t1 = __ldg(P.fv + ebf1);
+                const int o1 = sel3(ebo1, t1.x, t1.y, t1.z);
                 const float4 xv = __ldg(P.V + v0), x0 = __ldg(P.V + o0), x1 = __ldg(P.V + o1);
                 const float a0x = x0.x - xv.x, a0y = x0.y - xv.y, a0z = x0.z - xv.z;
                 const float a1x = x1.x - xv.x, a1y = x1.y - xv.y, a1z = x1.z - xv.z;
@@ -236,8 +240,8 @@ __device__ __forceinline__ bool hole_vertex(Walker &w, const WalkParams &P, int 
                 if (fabsf(d1 - d0) < tau) w.st |= SG_ST_NEAR_VERTEX;
             }
         }
-        const int fb = ebf[k], cb = ebc[k], co = ebo[k];
-        if (ebfl[k]) w.st ^= SG_PARITY_BIT;
+        const int fb = k ? ebf1 : ebf0, cb = k ? ebc1 : ebc0, co = k ? ebo1 : ebo0;
+        if (k ? ebfl1 : ebfl0) w.st ^= SG_PARITY_BIT;
         if (fb != w.f) {
             w.f = fb;
             w.R = load_rec(P.rec, fb);

@@ -56,3 +56,15 @@ def test_product_code_does_not_reference_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "om_" not in txt, f
+
+
+def test_header_is_plain_c_and_cxx():
+    """include/sgeo.h is a C-ABI header: it compiles alone as C99 and as C++11, with no torch or
+    CUDA headers."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "sgeo.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++11")):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not available")
+        subprocess.check_call([cc, "-fsyntax-only", std, "-Wall", "-Werror", "-x", lang, hdr])

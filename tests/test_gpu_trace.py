@@ -90,11 +90,21 @@ def test_traced_polyline_length_and_truncation():
         poly = np.concatenate([full["path_pt"][i, :n], full["pos"][i][None]]).astype(np.float64)
         length = np.linalg.norm(np.diff(poly, axis=0), axis=1).sum()
         assert abs(length - L[i]) <= 2e-5 * max(L[i], 1.0), (i, length, L[i])
-    # a small cap keeps the first entries and still reports the full count
+    # a small cap keeps the first entries and still reports the full count (entries past the
+    # path length are not written, so only the written prefix is compared)
     small = run_trace(mesh, q, 4)
     assert np.array_equal(small["path_len"], full["path_len"])
-    assert np.array_equal(small["path_face"], full["path_face"][:, :4])
-    assert np.array_equal(small["path_pt"], full["path_pt"][:, :4])
+    for i in range(len(q.face)):
+        n = min(int(full["path_len"][i]), 4)
+        assert np.array_equal(small["path_face"][i, :n], full["path_face"][i, :n])
+        assert np.array_equal(small["path_pt"][i, :n], full["path_pt"][i, :n])
+    # a cap that is not a multiple of 4 takes the one-entry-at-a-time store path
+    odd = run_trace(mesh, q, 13)
+    assert np.array_equal(odd["path_len"], full["path_len"])
+    for i in range(len(q.face)):
+        n = min(int(full["path_len"][i]), 13)
+        assert np.array_equal(odd["path_face"][i, :n], full["path_face"][i, :n])
+        assert np.array_equal(odd["path_pt"][i, :n], full["path_pt"][i, :n])
     # cap 0: no path storage at all, counts only
     none = run_trace(mesh, q, 0)
     assert np.array_equal(none["path_len"], full["path_len"])
