@@ -46,6 +46,14 @@
 #include "walk.cuh"
 
 #define SG_BWD_MAX_W 4
+// lanes of a warp that must be idle before the re-walk refills them together
+#ifndef SG_REWALK_REFILL
+#define SG_REWALK_REFILL 16
+#endif
+// the same for the literal GFD walks
+#ifndef SG_LITERAL_REFILL
+#define SG_LITERAL_REFILL 16
+#endif
 
 struct BwdArgs {
     WalkParams P;
@@ -361,7 +369,7 @@ template <bool GFD, bool GRADV>
 __global__ void __launch_bounds__(128, 7) k_bwd_rewalk(BwdArgs A) {
     RewalkJob<GFD, GRADV> job;
     job.A = &A;
-    run_persistent(A.ntask + 1, A.nq, job);
+    run_persistent<RewalkJob<GFD, GRADV>, SG_REWALK_REFILL>(A.ntask + 1, A.nq, job);
 }
 
 // ------------------------------------------------------------------ chord / literal walks
@@ -504,7 +512,7 @@ template <bool HOLE>
 __global__ void __launch_bounds__(128) k_bwd_literal(BwdArgs A) {
     LiteralJob<HOLE> job;
     job.A = &A;
-    run_persistent(A.ntask + 2, (int64_t)*A.ntask, job);
+    run_persistent<LiteralJob<HOLE>, SG_LITERAL_REFILL>(A.ntask + 2, (int64_t)*A.ntask, job);
 }
 
 __global__ void __launch_bounds__(256) k_bwd_assemble(BwdArgs A) {

@@ -21,6 +21,14 @@
 #include "walk.cuh"
 
 #define SG_MAX_W 4
+// lanes of a warp that must be idle before the forward walk refills them together
+#ifndef SG_WALK_REFILL
+#define SG_WALK_REFILL 12
+#endif
+// lanes of a warp with a pending hole-avoidance boundary event before those events run together
+#ifndef SG_HOLE_BATCH
+#define SG_HOLE_BATCH 24
+#endif
 
 struct FwdArgs {
     WalkParams P;
@@ -90,7 +98,17 @@ struct FwdJob {
         q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
         return walker_init<NW>(a->P, a->in, q, w, cw);
     }
-    __device__ __forceinline__ bool step() { return walker_step<ESC, HOLE>(w, a->P); }
+    __device__ __forceinline__ bool step() {
+        if (HOLE) {
+            // boundary events of hole avoidance wait until several lanes have one (or every
+            // stepping lane does), then run together
+            const bool pend = w.mode >= SG_MODE_HOLE_EDGE;
+            const unsigned act = __activemask();
+            const unsigned pm = __ballot_sync(act, pend);
+            if (pend && __popc(pm) < SG_HOLE_BATCH && pm != act) return false;
+        }
+        return walker_step<ESC, HOLE>(w, a->P);
+    }
     __device__ __forceinline__ void finish() { walker_finish<NW>(*a, q, w, cw); }
 };
 
@@ -98,7 +116,7 @@ template <int NW, bool ESC>
 __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
     FwdJob<NW, ESC, false> job;
     job.a = &a;
-    run_persistent(a.counter, a.nq, job);
+    run_persistent<FwdJob<NW, ESC, false>, SG_WALK_REFILL>(a.counter, a.nq, job);
 }
 
 // hole avoidance (boundary_mode 1): the boundary handling needs more registers than the
@@ -107,7 +125,7 @@ template <int NW>
 __global__ void __launch_bounds__(256, 4) k_walk_hole(FwdArgs a) {
     FwdJob<NW, true, true> job;
     job.a = &a;
-    run_persistent(a.counter, a.nq, job);
+    run_persistent<FwdJob<NW, true, true>, SG_WALK_REFILL>(a.counter, a.nq, job);
 }
 
 // ------------------------------------------------------------------ geodesic tracing
@@ -263,7 +281,7 @@ __global__ void __launch_bounds__(256, 4) k_trace_persistent(FwdArgs a, TraceOut
     job.a = &a;
     job.t = &t;
     job.sg = &stage;
-    run_persistent(a.counter, a.nq, job);
+    run_persistent<TraceJob<ESC>, SG_WALK_REFILL>(a.counter, a.nq, job);
 }
 
 // ------------------------------------------------------------------ start-face counting sort

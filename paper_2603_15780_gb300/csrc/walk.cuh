@@ -78,6 +78,10 @@ struct WalkParams {
 // vertex transport, 6 free start -- in these R holds the face record and p, d are in the face
 // frame.  Every walk ends in a face mode.
 #define SG_MODE_HALF 7
+// hole avoidance: the walk reached the boundary on local edge mode-8 (at p) or on corner
+// mode-11 of face f, and the boundary handling is pending (see hole_resolve)
+#define SG_MODE_HOLE_EDGE 8
+#define SG_MODE_HOLE_VERTEX 11
 struct Walker {
     int f, h, mode, steps, ncross;
     float px, py, dx, dy;
@@ -285,9 +289,10 @@ __device__ __forceinline__ bool hole_vertex(Walker &w, const WalkParams &P, int 
 
 // The walk reached boundary edge j of face w.f at (w.px, w.py) (face frame, w.R the face
 // record): slide along it toward the endpoint the direction points to (corner j+1 when
-// d . (P_{j+1} - P_j) >= 0, else corner j), then handle that boundary vertex.  Returns true
-// when the walk resumes.
-__device__ __forceinline__ bool hole_edge(Walker &w, const WalkParams &P, int j) {
+// d . (P_{j+1} - P_j) >= 0, else corner j).  Returns false when the length ran out on the edge;
+// true when the walker reached that endpoint, which is then corner *c of w.f, with *came the
+// vertex it slid from.
+__device__ __forceinline__ bool hole_edge(Walker &w, const WalkParams &P, int j, int *c, int *came) {
     w.st |= SG_ST_HOLE;
     const FaceRec &R = w.R;
     const float ax = corner_x(R, j), ay = corner_y(R, j), bx = corner_x(R, nxt(j)), by = corner_y(R, nxt(j));
@@ -314,12 +319,25 @@ __device__ __forceinline__ bool hole_edge(Walker &w, const WalkParams &P, int j)
         w.Ll += err;
     }
     w.steps++;
+    const int4 t3 = __ldg(P.fv + w.f);
+    w.px = corner_x(R, tgt); w.py = corner_y(R, tgt); w.mode = 3 + tgt;
+    *c = tgt;
+    *came = sel3(oth, t3.x, t3.y, t3.z);
+    return true;
+}
+
+// Applies a pending boundary event of hole avoidance.  The step code only marks the event
+// (modes 8..13), so that a walk kernel can apply the events of several lanes together: each
+// is a chain of dependent gathers around a vertex fan, and lanes waiting one by one on such
+// chains would serialise the warp.  Returns true when the walk ended.
+__device__ __forceinline__ bool hole_resolve(Walker &w, const WalkParams &P) {
+    // D: the direction, in 3-D, that the walker has on reaching the boundary
     float e1x, e1y, e1z, e2x, e2y, e2z;
     frm_axes(P, w.f, e1x, e1y, e1z, e2x, e2y, e2z);
     const float Dx = w.dx * e1x + w.dy * e2x, Dy = w.dx * e1y + w.dy * e2y, Dz = w.dx * e1z + w.dy * e2z;
-    const int4 t3 = __ldg(P.fv + w.f);
-    w.px = corner_x(R, tgt); w.py = corner_y(R, tgt); w.mode = 3 + tgt;
-    return hole_vertex(w, P, tgt, sel3(oth, t3.x, t3.y, t3.z), Dx, Dy, Dz);
+    int c = w.mode - SG_MODE_HOLE_VERTEX, came = -1;
+    if (w.mode < SG_MODE_HOLE_VERTEX && !hole_edge(w, P, w.mode - SG_MODE_HOLE_EDGE, &c, &came)) return true;
+    return !hole_vertex(w, P, c, came, Dx, Dy, Dz);
 }
 
 // Vertex transport: the walker reached corner c of face w.f with direction d.
@@ -337,10 +355,9 @@ __device__ __forceinline__ bool vertex_transport(Walker &w, int c, const WalkPar
     float cx = corner_x(w.R, c), cy = corner_y(w.R, c);
     w.px = cx; w.py = cy;
     if (th < 0.f) {  // boundary vertex: original rule stops here (Sec. 4), or hole avoidance
-        if (HOLE) {
-            float e1x, e1y, e1z, e2x, e2y, e2z;
-            frm_axes(P, w.f, e1x, e1y, e1z, e2x, e2y, e2z);
-            return hole_vertex(w, P, c, -1, w.dx * e1x + w.dy * e2x, w.dx * e1y + w.dy * e2y, w.dx * e1z + w.dy * e2z);
+        if (HOLE) {  // handled by hole_resolve on a later call
+            w.mode = SG_MODE_HOLE_VERTEX + c;
+            return true;
         }
         w.st |= SG_ST_BOUNDARY;
         return false;
@@ -523,7 +540,10 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     if (link < 0) {  // boundary edge: original rule stops (Sec. 4), or hole avoidance
         half_to_face(w, P, qx, qy);
         const int k = w.h - 3 * w.f;
-        if (HOLE) return !hole_edge(w, P, right ? nxt(k) : prv(k));
+        if (HOLE) {  // handled by hole_resolve on a later call
+            w.mode = SG_MODE_HOLE_EDGE + (right ? nxt(k) : prv(k));
+            return false;
+        }
         w.st |= SG_ST_BOUNDARY;
         return true;
     }
@@ -560,6 +580,7 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
 // One step of Alg. geodesic_step.  Returns true when the walk is finished.
 template <bool ESC, bool HOLE = false, class Hook = NoHook>
 __device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook &&hook = Hook()) {
+    if (HOLE && w.mode >= SG_MODE_HOLE_EDGE) return hole_resolve(w, P);  // a pending boundary event
     if (w.steps >= P.max_steps) {
         if (w.mode == SG_MODE_HALF) half_to_face(w, P, w.px * hl(w.R), 0.f);
         w.st |= SG_ST_MAX_STEPS;
@@ -665,7 +686,10 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
     const int nb = nbr_of(R, j);
     if (nb < 0) {  // boundary edge: original rule stops (Sec. 4), or hole avoidance
         w.px = qx; w.py = qy;
-        if (HOLE) return !hole_edge(w, P, j);
+        if (HOLE) {  // handled by hole_resolve on a later call
+            w.mode = SG_MODE_HOLE_EDGE + j;
+            return false;
+        }
         w.st |= SG_ST_BOUNDARY;
         return true;
     }
@@ -852,14 +876,14 @@ __device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
 // (true: done), void finish().
 #define SG_REFILL_LANES 8
 
-template <class Job>
+template <class Job, int REFILL = SG_REFILL_LANES>
 __device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job) {
     bool live = false, pending = false, exhausted = false;
     const unsigned FULL = 0xffffffffu;
     while (true) {
         unsigned idle = __ballot_sync(FULL, !live);
         if (exhausted && idle == FULL) break;
-        if (!exhausted && __popc(idle) >= SG_REFILL_LANES) {
+        if (!exhausted && __popc(idle) >= REFILL) {
             bool dry = false;
             if (!live) {
                 if (pending) {
