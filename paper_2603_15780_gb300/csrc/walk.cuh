@@ -867,7 +867,7 @@ __device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
 }
 
 // Lanes pull task indices t < n from *counter.  A lane whose task has ended keeps its state
-// in registers until SG_REFILL_LANES lanes of the warp are idle; then all idle lanes finish
+// in registers until REFILL lanes of the warp are idle (each kernel sets its own threshold); then all idle lanes finish
 // (write results), take new tickets and initialise together, so the long init/finish code
 // runs with many lanes active instead of stalling the warp for one lane every few steps.
 // Once the counter passes n, lanes finish as soon as they are done and the warp leaves when
@@ -875,6 +875,9 @@ __device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
 // ballots use the full mask).  Job: bool init(t) (true: a walk to step), bool step()
 // (true: done), void finish().
 #define SG_REFILL_LANES 8
+#ifndef SG_STEPS_PER_CHECK
+#define SG_STEPS_PER_CHECK 2
+#endif
 
 template <class Job, int REFILL = SG_REFILL_LANES>
 __device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job) {
@@ -900,14 +903,13 @@ __device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job 
             }
             exhausted = __any_sync(FULL, dry);
         }
-        // two steps per refill check halve the loop overhead
-        if (live && job.step()) {
-            live = false;
-            pending = true;
-        }
-        if (live && job.step()) {
-            live = false;
-            pending = true;
+        // several steps per refill check divide the loop overhead
+#pragma unroll
+        for (int k = 0; k < SG_STEPS_PER_CHECK; ++k) {
+            if (live && job.step()) {
+                live = false;
+                pending = true;
+            }
         }
         if (exhausted && pending) {
             job.finish();
