@@ -492,7 +492,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1048576)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", type=int, default=2)
-    ap.add_argument("--sort", type=int, default=1)
+    ap.add_argument("--sort", type=int, default=-1, help="1 on, 0 off, -1 the library's automatic choice")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--fp64", type=int, default=1)
     ap.add_argument("--json-out", default=None)
@@ -664,6 +664,19 @@ def main():
         e2e = {"value": nq / (np.mean(e_ms) * 1e-3), "unit": "geodesics/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # ---- kernels the library launches per step: the walk (plus 5 sort/scan kernels when the
+    # queries are sorted), EP, the GFD re-walk, chords, literal walks and assemble, and the grad_V
+    # edge expansion and flush.  The automatic sort is on only when the mesh's records (128 B per
+    # face) exceed half of L2, as the library decides.
+    if args.kernel == 1:
+        sort_on = False
+    elif args.sort >= 0:
+        sort_on = bool(args.sort)
+    else:
+        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+        sort_on = nq >= 65536 and 128 * mesh.n_faces > l2 // 2
+    launches_per_step = 8 + (5 if sort_on else 0)
+
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     peak, peak_kind = peaks()
     # forward walk: one 32-B half-edge record per crossing; per query the inputs (face, bary,
@@ -692,7 +705,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "icosphere-s6-noisy 81920F 1Mq fwd+EP+GFD+gradV", "global_batch": world * nq,
                        "faces": int(len(F)), "queries_per_gpu": nq, "l2": "flushed between steps (512 MB write)",
-                       "kernel": "persistent" if args.kernel == 2 else "plain", "sort": bool(args.sort),
+                       "kernel": "persistent" if args.kernel == 2 else "plain", "sort": sort_on,
                        "fp64_classification": bool(args.fp64)},
             "crossings_per_s": world * ncross / (float(np.mean(ktimes["walk"])) * 1e-3),
             "fwd_geodesics_per_s": world * nq / (fwd_ms * 1e-3),
@@ -700,7 +713,7 @@ def main():
             "crossings_per_query": ncross / nq,
             "flag_fraction": {"near_vertex": float(((st & 4) != 0).mean()), "near_edge": float(((st & 8) != 0).mean()),
                               "fp64": float(((st & 32) != 0).mean())},
-            "gpu_launches": args.steps * 13,  # per step: 5 sort/scan + walk, EP, re-walk + chords + literal + assemble, grad_V edges + flush
+            "gpu_launches": args.steps * launches_per_step,
             "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1

@@ -72,7 +72,9 @@ typedef struct sg_opts {
     int32_t max_steps;      /* loop cap per query (Alg. gpu_parallel MAX_STEPS); <= 0: 1<<20 */
     int32_t kernel;         /* SG_KERNEL_*; AUTO = persistent */
     int32_t sort;           /* 1: order queries by (mesh, start face) before walking; 0: no;
-                               <0: auto (on from 65536 queries) */
+                               <0: auto -- on for batches of >= 65536 queries on meshes whose
+                               walk records (128 B per face) exceed half of L2, off otherwise
+                               (records that stay in L2 are gathered as fast in any order) */
     int32_t block;          /* threads per block; <= 0: 256 */
     int32_t blocks_per_sm;  /* persistent kernel residency; <= 0: as many as fit */
     int32_t fp64_escalate;  /* 1: re-evaluate near-vertex classification in FP64 (persistent only) */

@@ -50,6 +50,13 @@
 #ifndef SG_REWALK_REFILL
 #define SG_REWALK_REFILL 16
 #endif
+// minimum resident blocks per SM the chord and literal kernels are compiled for
+#ifndef SG_CHORDS_MINB
+#define SG_CHORDS_MINB 7
+#endif
+#ifndef SG_LITERAL_MINB
+#define SG_LITERAL_MINB 1
+#endif
 // the same for the literal GFD walks
 #ifndef SG_LITERAL_REFILL
 #define SG_LITERAL_REFILL 16
@@ -428,7 +435,7 @@ __device__ __forceinline__ void rmap(float x, float y, float d0x, float d0y, con
 }
 
 template <bool HOLE>
-__global__ void __launch_bounds__(128) k_bwd_chords(BwdArgs A) {
+__global__ void __launch_bounds__(128, SG_CHORDS_MINB) k_bwd_chords(BwdArgs A) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= A.nq) return;
     const WalkParams &P = A.P;
@@ -509,7 +516,7 @@ struct LiteralJob {
 };
 
 template <bool HOLE>
-__global__ void __launch_bounds__(128) k_bwd_literal(BwdArgs A) {
+__global__ void __launch_bounds__(128, SG_LITERAL_MINB) k_bwd_literal(BwdArgs A) {
     LiteralJob<HOLE> job;
     job.A = &A;
     run_persistent<LiteralJob<HOLE>, SG_LITERAL_REFILL>(A.ntask + 2, (int64_t)*A.ntask, job);

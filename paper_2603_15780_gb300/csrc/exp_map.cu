@@ -401,11 +401,25 @@ WsLayout ws_layout(int64_t nF, int64_t nq, bool sort) {
     return L;
 }
 
-// Below this batch size the start-face sort costs more (five small launches) than the gather
-// coherence it buys, so the automatic choice (sort < 0) leaves it off.
+// The automatic choice (sort < 0) orders queries by start face only when it pays: for batches
+// of at least SG_SORT_MIN_BATCH queries on meshes whose walk records (128 B per face: face and
+// half-edge records) exceed half of L2.  When the records stay in L2 the gathers hit L2 in any
+// order and the sort's five launches are pure cost (measured: icosphere s6 and torus 262k walks
+// are as fast or faster unsorted; a 4.2M-face heightfield is 12% faster sorted).
 #define SG_SORT_MIN_BATCH 65536
 
-sg_opts resolve(const sg_opts *o, int64_t nq) {
+int l2_bytes() {
+    static int cached = -1;
+    if (cached < 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess) { cudaGetLastError(); v = 0; }
+        cached = v > 0 ? v : (64 << 20);
+    }
+    return cached;
+}
+
+sg_opts resolve(const sg_opts *o, int64_t nq, int64_t nF) {
     sg_opts r;
     sg_opts_default(&r);
     if (o) r = *o;
@@ -415,7 +429,7 @@ sg_opts resolve(const sg_opts *o, int64_t nq) {
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
     if (r.tau_snap <= 0.f) r.tau_snap = r.precision == 64 ? 1e-12f : 1e-6f;
     if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
-    if (r.sort < 0) r.sort = nq >= SG_SORT_MIN_BATCH ? 1 : 0;
+    if (r.sort < 0) r.sort = (nq >= SG_SORT_MIN_BATCH && 128 * nF > (int64_t)l2_bytes() / 2) ? 1 : 0;
     if (r.kernel == SG_KERNEL_PLAIN) { r.sort = 0; r.fp64_escalate = 0; }
     return r;
 }
@@ -628,7 +642,7 @@ sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info) {
 
 sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts *o, size_t *bytes) {
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
-    sg_opts r = resolve(o, nq);
+    sg_opts r = resolve(o, nq, m->nF);
     *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT && r.sort).total;
     return SG_OK;
 }
@@ -700,7 +714,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (nq > (int64_t)INT32_MAX - 1024) return SG_ERR_INVALID_ARG;
     if (!face || !bary || !v || !out_face || !out_bary || !out_pos || !out_dir || !out_status) return SG_ERR_INVALID_ARG;
     if (n_w > 0 && !w) return SG_ERR_INVALID_ARG;
-    sg_opts r = resolve(o, nq);
+    sg_opts r = resolve(o, nq, m->nF);
     if (r.kernel != SG_KERNEL_PLAIN && r.kernel != SG_KERNEL_PERSISTENT) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
@@ -768,7 +782,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
     if (!face || !bary || !v || !out_face || !out_bary || !out_pos || !out_dir || !out_status || !out_path_len)
         return SG_ERR_INVALID_ARG;
     if (path_cap > 0 && !out_path_face) return SG_ERR_INVALID_ARG;
-    sg_opts r = resolve(o, nq);
+    sg_opts r = resolve(o, nq, m->nF);
     if (r.boundary_mode || r.precision == 64) return SG_ERR_UNSUPPORTED;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -68,7 +68,7 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     X, F = meshgen.icosphere(2)
     mesh = sg.Mesh(parity.as_f32(X), F)
     nq = 9 * 1024 * 1024          # sorted layout needs > 32 MiB of scratch
-    opts = sg.default_opts()
+    opts = sg.default_opts(sort=1)
     assert sg.workspace_size(mesh, nq, opts) > (32 << 20)
     face = torch.zeros(nq, dtype=torch.int32, device="cuda")
     bary = torch.full((nq, 3), 1.0 / 3.0, device="cuda")
