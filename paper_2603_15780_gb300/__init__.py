@@ -413,7 +413,7 @@ def _autograd_function():
                                  g_bary=None if g_bary is None else g_bary.contiguous(),
                                  g_dir=None if g_dir is None else g_dir.contiguous(),
                                  eps_v=ctx.eps, eps_p=ctx.eps,
-                                 want_grad_V=ctx.needs_input_grad[5] and ctx.has_V)
+                                 want_grad_V=ctx.has_V and ctx.needs_input_grad[5])
             gV = r.get("grad_V")
             return None, None, r["grad_bary"], r["grad_v"], None, gV, None, None
 
