@@ -302,6 +302,31 @@ sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, 
                               float *grad_w, uint32_t *out_status, const sg_opts *o, void *stream);
 
 /*
+ * sg_transport_back -- the adjoint of the parallel transport along each query's geodesic,
+ * which is its inverse: tangent vectors at the end point p' are moved backwards along the
+ * curve to the start point p (App. "Additional Details on Mesh-LBFGS and GCVT": the vector
+ * transport of the Riemannian L-BFGS and its adjoint; Sec. 4 "Parallel Transport").  The
+ * forward transport keeps each vector's signed angle to the walking direction, so for the
+ * forward's face sequence it is a rotation R of the tangent planes and this call applies R^T:
+ * no walk is repeated.  For every tangent a at p and u at p', <R a, u> = <a, R^T u>.
+ *   mesh_id, face, bary, v   the forward inputs (device, as in sg_exp_map; L = |v|)
+ *   end_face, end_dir        the forward outputs for these queries (device)
+ *   end_status               the forward status words (device) or NULL (SG_ST_FLIPPED taken
+ *                            as 0, exact for orientable meshes)
+ *   n_u, u    device float32 [nq][n_u][3] vectors at the end points (0 <= n_u <= 4); their
+ *             components normal to the end face are dropped
+ *   out_u     device float32 [nq][n_u][3], caller-allocated: the vectors at the start points,
+ *             tangent to the start face.  Zero for invalid queries; for a zero vector v the
+ *             path is empty and out_u is u projected onto the start face.
+ * Asynchronous on `stream`; no scratch.  Errors: SG_ERR_INVALID_ARG (NULL array, n_u out of
+ * range), SG_ERR_UNSUPPORTED (opts->precision == 64), SG_ERR_CUDA.
+ */
+sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
+                            const float *bary, const float *v, const int32_t *end_face,
+                            const float *end_dir, const uint32_t *end_status, int32_t n_u,
+                            const float *u, float *out_u, const sg_opts *o, void *stream);
+
+/*
  * sg_exp_map_backward_workspace_size -- bytes of device scratch sg_exp_map_backward needs for
  * nq queries with `estimator` (SG_EST_*) and, if want_grad_V != 0, the vertex gradient: the
  * GFD column table (16 B per query) and literal-walk task list (12 B per query), and

@@ -161,6 +161,30 @@ def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, *, max_steps=0, tau_
     return out
 
 
+def transport_back(mesh: Mesh, face, bary, v, u, length=None, **kw):
+    """The adjoint of the parallel transport Pi along the geodesic Exp_p(v), which is its
+    inverse (App. "Additional Details on Mesh-LBFGS and GCVT": the vector is moved backwards on
+    the curve).  Written from the adjoint's definition <Pi a, u> = <a, Pi* u> for every tangent
+    a at p: with an orthonormal basis (e1, e2) of the start face carried forward to (T1, T2),
+    Pi* u = e1 <T1, u> + e2 <T2, u>.  u [nq, n_u, 3] (or [nq, 3]) at the end points.
+    Returns (Pi* u in u's shape, the forward walk's output dict)."""
+    face = np.ascontiguousarray(face, dtype=np.int32)
+    nq = len(face)
+    X, F = mesh.X, mesh.F
+    x0, x1, x2 = X[F[face, 0]], X[F[face, 1]], X[F[face, 2]]
+    e1 = (x1 - x0) / np.linalg.norm(x1 - x0, axis=1, keepdims=True)
+    n = np.cross(x1 - x0, x2 - x0)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    e2 = np.cross(n, e1)
+    out = exp_map(mesh, face, bary, v, np.stack([e1, e2], axis=1), length, **kw)
+    u = _f64(u)
+    shape = u.shape
+    u = u.reshape(nq, -1, 3)
+    c = np.einsum("qij,qkj->qki", out["w"], u)          # <T_i, u_k>
+    back = c[..., 0:1] * e1[:, None, :] + c[..., 1:2] * e2[:, None, :]
+    return back.reshape(shape), out
+
+
 def ep_backward(mesh: Mesh, face, bary, v, g_pos, *, threads=0, **kw):
     """Extrinsic-proxy VJP (Eq. proxy_func): grad_v; grad_p and grad_bary are zero."""
     face = np.ascontiguousarray(face, dtype=np.int32)

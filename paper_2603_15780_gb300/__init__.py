@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Mesh", "exp_map", "exp_map_backward", "ExpMap", "Opts", "lib", "status_names",
+__all__ = ["Mesh", "exp_map", "exp_map_backward", "transport_back", "ExpMap", "Opts", "lib", "status_names",
            "ST_BOUNDARY", "ST_MAX_STEPS", "ST_NEAR_VERTEX", "ST_NEAR_EDGE", "ST_VERTEX_HIT", "ST_FP64",
            "ST_START_ON_EDGE", "ST_INVALID", "ST_GFD_SPLIT", "ST_FLIPPED", "ST_NO_GRADV",
            "KERNEL_AUTO", "KERNEL_PLAIN", "KERNEL_PERSISTENT", "EST_EP", "EST_GFD", "SgError"]
@@ -34,7 +34,7 @@ EST_EP, EST_GFD = 0, 1
 EXPORTED = ["sg_opts_default", "sg_status_string", "sg_mesh_create", "sg_mesh_create_batched",
             "sg_mesh_destroy", "sg_mesh_get_info", "sg_exp_map_workspace_size", "sg_exp_map",
             "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc", "sg_exp_map_backward_workspace_size",
-            "sg_mesh_update_vertices", "sg_exp_map_trace"]
+            "sg_mesh_update_vertices", "sg_exp_map_trace", "sg_transport_back"]
 
 
 def status_names(st: int) -> list[str]:
@@ -98,6 +98,8 @@ def lib():
             L.sg_exp_map_backward.argtypes = [P, C.c_int32, C.c_float, C.c_float, C.c_int64, P, P, P, P,
                                               P, P, P, P, P, P, P, C.c_int32, P, P, P, P, P, P, P,
                                               C.POINTER(Opts), P]
+            L.sg_transport_back.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, C.c_int32, P, P,
+                                            C.POINTER(Opts), P]
             for f in EXPORTED:
                 if f not in ("sg_opts_default",):
                     getattr(L, f).restype = getattr(L, f).restype or C.c_int
@@ -381,6 +383,34 @@ def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_bary, e
                                    C.byref(o), C.c_void_p(s.cuda_stream))
     _check(rc, "sg_exp_map_backward")
     return res
+
+
+def transport_back(mesh: Mesh, face, bary, v, end, u, mesh_id=None, *, opts: Opts | None = None, stream=None):
+    """sg_transport_back: move tangent vectors u [nq, n_u, 3] (or [nq, 3]) at the end points of
+    the geodesics Exp_p(v) back to their start points, the adjoint (= inverse) of the forward
+    parallel transport.  `end` is the forward's output dict (face, dir, status).  Returns a
+    tensor of u's shape."""
+    torch = _torch()
+    face = _dev(face, torch.int32)
+    nq = face.numel()
+    bary = _dev(bary, torch.float32, (nq, 3))
+    v = _dev(v, torch.float32, (nq, 3))
+    end_face = _dev(end["face"], torch.int32, (nq,))
+    end_dir = _dev(end["dir"], torch.float32, (nq, 3))
+    end_status = _dev(end.get("status"), torch.int32, (nq,))
+    u = _dev(u, torch.float32)
+    shape = u.shape
+    n_u = u.numel() // (3 * max(nq, 1))
+    u = u.reshape(nq, n_u, 3)
+    mesh_id = _dev(mesh_id, torch.int32, (nq,))
+    out = torch.empty(nq, n_u, 3, device=face.device)
+    o = opts if opts is not None else default_opts()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().sg_transport_back(mesh.handle, nq, _ptr(mesh_id), _ptr(face), _ptr(bary), _ptr(v), _ptr(end_face),
+                                 _ptr(end_dir), _ptr(end_status), n_u, _ptr(u), _ptr(out), C.byref(o),
+                                 C.c_void_p(s.cuda_stream))
+    _check(rc, "sg_transport_back")
+    return out.reshape(shape)
 
 
 def _autograd_function():

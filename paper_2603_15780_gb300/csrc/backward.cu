@@ -596,8 +596,9 @@ __global__ void __launch_bounds__(256) k_bwd_transport(BwdArgs A) {
     const WalkParams &P = A.P;
     Walker w;
     Carry<0> cw;
-    const bool live = walker_init<0>(P, A.in, q, w, cw);
-    const bool valid = live && !(w.st & SG_ST_INVALID);
+    walker_init<0>(P, A.in, q, w, cw);
+    // zero-length queries included: their transport is the identity in the start face
+    const bool valid = !(w.st & SG_ST_INVALID);
     F3 gw[SG_BWD_MAX_W];
     for (int k = 0; k < A.n_w; ++k) gw[k] = f3(0.f, 0.f, 0.f);
     if (valid) {
@@ -610,7 +611,11 @@ __global__ void __launch_bounds__(256) k_bwd_transport(BwdArgs A) {
         if (n2 > 0.f) { const float r = rsqrtf(n2); dmx *= r; dmy *= r; }
         const uint32_t est = A.end_status ? __ldg(A.end_status + q) : 0u;
         const float sm = (est & SG_ST_FLIPPED) ? -1.f : 1.f;
-        const float d0x = w.dx, d0y = w.dy;
+        // a zero vector v has no direction: the forward measured carried vectors against e1
+        // at both ends of its empty path
+        const bool nod = w.dx == 0.f && w.dy == 0.f;
+        const float d0x = nod ? 1.f : w.dx, d0y = nod ? 0.f : w.dy;
+        if (nod) { dmx = 1.f; dmy = 0.f; }
         // R^T g for a tangent g at the end, as a start-frame 2-vector (along, across d0)
         auto back = [&](F3 g, float &al, float &ac) {
             const float gx = g.x * Fm.e1x + g.y * Fm.e1y + g.z * Fm.e1z;
@@ -804,5 +809,37 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         k_gradv_flush<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, A.gacc, grad_V);
     }
     if (own) cudaFreeAsync(ws, s);
+    return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+// The adjoint of the parallel transport along each query's geodesic, which is its inverse
+// (App. "Additional Details on Mesh-LBFGS and GCVT": the vector is moved backwards on the
+// curve).  For a fixed face sequence the transport is a rotation of the tangent planes that
+// keeps each vector's signed angle to the walking direction, so the inverse is the rotation's
+// transpose: the transport kernel's R^T applied to u, with no walk.
+extern "C" sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
+                                       const float *bary, const float *v, const int32_t *end_face,
+                                       const float *end_dir, const uint32_t *end_status, int32_t n_u,
+                                       const float *u, float *out_u, const sg_opts *o, void *stream) {
+    if (!m || nq < 0) return SG_ERR_INVALID_ARG;
+    if (n_u < 0 || n_u > SG_BWD_MAX_W) return SG_ERR_INVALID_ARG;
+    if (nq == 0 || n_u == 0) return SG_OK;
+    if (nq > (int64_t)(INT32_MAX / 4) - 1024) return SG_ERR_INVALID_ARG;
+    if (!face || !bary || !v || !end_face || !end_dir || !u || !out_u) return SG_ERR_INVALID_ARG;
+    sg_opts r;
+    sg_opts_default(&r);
+    if (o) r = *o;
+    if (r.precision == 64) return SG_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    BwdArgs A{};
+    A.P.rec = m->d_rec; A.P.fv = m->d_fv; A.P.frm = m->d_frm; A.P.half = m->d_half; A.P.V = m->d_V; A.P.face_off = m->d_face_off;
+    A.P.lref = m->d_lref;
+    A.P.max_steps = 1; A.P.tau_near = 1e-4f; A.P.tau_snap = 1e-6f; A.P.want_hash = 0;
+    A.in.n_mesh = m->n_mesh; A.in.mesh_id = mesh_id; A.in.face = face; A.in.bary = bary; A.in.v = v;
+    A.in.length = nullptr; A.in.w = nullptr;
+    A.nq = nq;
+    A.end_face = end_face; A.end_dir = end_dir; A.end_status = end_status;
+    A.n_w = n_u; A.g_w = u; A.grad_w = out_u;
+    k_bwd_transport<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }

@@ -61,9 +61,11 @@ __device__ void walker_finish(const FwdArgs &a, int64_t q, const Walker &w, cons
     a.out_dir[3 * q + 2] = w.dx * F.e1z + w.dy * F.e2z;
     if (NW > 0 && a.out_w) {
         const float sg = (w.st & SG_PARITY_BIT) ? -1.f : 1.f;
+        const bool nod = w.dx == 0.f && w.dy == 0.f;   // zero vector v: components against e1
+        const float rx = nod ? 1.f : w.dx, ry = nod ? 0.f : w.dy;
         for (int k = 0; k < NW; ++k) {
             float c = cw.c[k], s = sg * cw.s[k];
-            float u1 = c * w.dx - s * w.dy, u2 = c * w.dy + s * w.dx;
+            float u1 = c * rx - s * ry, u2 = c * ry + s * rx;
             float *o = a.out_w + (3 * NW) * q + 3 * k;
             o[0] = u1 * F.e1x + u2 * F.e2x;
             o[1] = u1 * F.e1y + u2 * F.e2y;

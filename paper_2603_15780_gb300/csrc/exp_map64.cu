@@ -300,12 +300,13 @@ struct Job64 {
         if (!(L >= 0.0 && L <= 1.0e300) || !(Lv <= 1.0e300) || (Lv == 0.0 && L > 0.0)) { w.st |= SG_ST_INVALID; return false; }
         if (Lv > 0.0) { w.dx = v1 / Lv; w.dy = v2 / Lv; }
         w.L = L;
+        const double rx = Lv > 0.0 ? w.dx : 1.0, ry = Lv > 0.0 ? w.dy : 0.0;  // zero v: against e1
         for (int k = 0; k < NW; ++k) {
             const float *wp = in.w + (3 * NW) * q + 3 * k;
             const double wx = __ldg(wp), wy = __ldg(wp + 1), wz = __ldg(wp + 2);
             const double w1 = wx * fr[0] + wy * fr[1] + wz * fr[2], w2 = wx * fr[3] + wy * fr[4] + wz * fr[5];
-            cc[k] = w1 * w.dx + w2 * w.dy;
-            cs[k] = w.dx * w2 - w.dy * w1;
+            cc[k] = w1 * rx + w2 * ry;
+            cs[k] = rx * w2 - ry * w1;
         }
         const int zeros = (b0 == 0.0) + (b1 == 0.0) + (b2 == 0.0);
         if (zeros) w.st |= SG_ST_START_ON_EDGE;
@@ -343,9 +344,11 @@ struct Job64 {
         A.out_dir[3 * q + 2] = (float)(w.dx * fr[2] + w.dy * fr[5]);
         if (NW > 0 && A.out_w) {
             const double sg = (w.st & SG_PARITY_BIT) ? -1.0 : 1.0;
+            const bool nod = w.dx == 0.0 && w.dy == 0.0;
+            const double rx = nod ? 1.0 : w.dx, ry = nod ? 0.0 : w.dy;
             for (int k = 0; k < NW; ++k) {
                 const double c = cc[k], s = sg * cs[k];
-                const double u1 = c * w.dx - s * w.dy, u2 = c * w.dy + s * w.dx;
+                const double u1 = c * rx - s * ry, u2 = c * ry + s * rx;
                 float *o = A.out_w + (3 * NW) * q + 3 * k;
                 o[0] = (float)(u1 * fr[0] + u2 * fr[3]);
                 o[1] = (float)(u1 * fr[1] + u2 * fr[4]);

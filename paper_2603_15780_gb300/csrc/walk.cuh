@@ -823,13 +823,17 @@ __device__ bool walker_init(const WalkParams &P, const QueryIn &a, int64_t q, Wa
     }
     if (Lv > 0.f) { w.dx = v1 / Lv; w.dy = v2 / Lv; } else { w.dx = w.dy = 0.f; }
     w.Lh = L;
+    // carried vectors as components along d and perp(d) = (-dy, dx); a zero vector v walks
+    // nothing and carries them unchanged, measured against e1 instead (reading: transport
+    // along an empty path is the identity)
+    const float rx = Lv > 0.f ? w.dx : 1.f, ry = Lv > 0.f ? w.dy : 0.f;
     for (int k = 0; k < NW; ++k) {
         const float *wp = a.w + (3 * NW) * q + 3 * k;
         float wx = __ldg(wp), wy = __ldg(wp + 1), wz = __ldg(wp + 2);
         float w1 = wx * F.e1x + wy * F.e1y + wz * F.e1z;
         float w2 = wx * F.e2x + wy * F.e2y + wz * F.e2z;
-        cw.c[k] = w1 * w.dx + w2 * w.dy;   // component along d
-        cw.s[k] = w.dx * w2 - w.dy * w1;   // component along perp(d) = (-dy, dx)
+        cw.c[k] = w1 * rx + w2 * ry;
+        cw.s[k] = rx * w2 - ry * w1;
     }
     int zeros = (b0 == 0.f) + (b1 == 0.f) + (b2 == 0.f);
     if (zeros) w.st |= SG_ST_START_ON_EDGE;

@@ -45,6 +45,7 @@ def test_null_arguments_rejected_without_gpu_work():
     assert L.sg_exp_map_backward(None, 0, 1e-4, 1e-4, 1, *([None] * 11), 0, *([None] * 7), C.byref(o), None) == 1
     assert L.sg_exp_map_trace(None, 1, None, None, None, None, None, 8, *([None] * 10), C.byref(o), None) == 1
     assert L.sg_mesh_update_vertices(None, None, None) == 1
+    assert L.sg_transport_back(None, 1, *([None] * 7), 1, None, None, C.byref(o), None) == 1
     n = C.c_size_t()
     assert L.sg_exp_map_workspace_size(None, 1, None, C.byref(n)) == 1
 

@@ -685,3 +685,63 @@ def test_non_orientable_meshes_gauss_bonnet_and_transport():
     ok &= (bk["status"] & (oracle.NEAR_VERTEX | oracle.NEAR_EDGE)) == 0
     p0 = start_points(X, F, q.face, q.bary)
     assert np.abs(bk["pos"] - p0)[ok].max() < 1e-9
+
+
+# --------------------------------------------------------------------------- inverse transport
+@pytest.mark.parametrize("which", ["torus", "klein"])
+def test_inverse_transport_is_the_reverse_walk(which):
+    """App. 'Additional Details on Mesh-LBFGS and GCVT': the adjoint of the parallel transport
+    moves a vector backwards on the curve.  The oracle's adjoint (from its definition with the
+    carried start basis) must equal an independent walk from p' along -d' for the same length
+    carrying u, on orientable and non-orientable meshes; it inverts the forward transport and
+    is the identity on a flat mesh."""
+    rng = np.random.default_rng(43)
+    if which == "torus":
+        X, F = meshgen.torus(40, 20, 1.0, 0.4, 0.003, rng)
+        q = meshgen.sample_queries(X, F, 500, rng, 0.0, 2.0, 2)
+    else:
+        X, F = meshgen.klein_bottle(64, 32)
+        q = meshgen.sample_queries(X, F, 500, rng, 1.0, 8.0, 2)
+    m = oracle.Mesh(X, F)
+    u = rng.normal(size=(len(q.face), 2, 3))
+    back, fw = oracle.transport_back(m, q.face, q.bary, q.v, u)
+    L = np.linalg.norm(q.v, axis=1)
+    bk = oracle.exp_map(m, fw["face"], fw["bary"], -fw["dir"] * L[:, None], u)
+    ok = ((fw["status"] | bk["status"]) & (oracle.NEAR_VERTEX | oracle.NEAR_EDGE | oracle.BOUNDARY)) == 0
+    assert ok.mean() > 0.8
+    assert np.array_equal(bk["face"][ok], q.face[ok])
+    assert np.abs(bk["w"] - back)[ok].max() < 1e-9
+    # inverse of the forward transport: Pi* (Pi w) = w projected onto the start face
+    fw2 = oracle.exp_map(m, q.face, q.bary, q.v, q.w)
+    rt, _ = oracle.transport_back(m, q.face, q.bary, q.v, fw2["w"])
+    x0, x1, x2 = X[F[q.face, 0]], X[F[q.face, 1]], X[F[q.face, 2]]
+    n = np.cross(x1 - x0, x2 - x0)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    wp = q.w - np.einsum("qkj,qj->qk", q.w, n)[..., None] * n[:, None, :]
+    assert np.abs(rt - wp)[ok].max() < 1e-10
+
+
+def test_inverse_transport_flat_and_empty_path():
+    """On a flat mesh parallel transport is the identity, so is its inverse; a zero vector v
+    walks an empty path and carries every vector unchanged (projected onto the face)."""
+    rng = np.random.default_rng(44)
+    X, F = meshgen.flat_grid(13, rng, jitter=0.3)
+    m = oracle.Mesh(X, F)
+    q = meshgen.sample_queries(X, F, 300, rng, 0.0, 0.4, 0)
+    u = np.c_[rng.normal(size=(300, 2)), np.zeros(300)]
+    back, fw = oracle.transport_back(m, q.face, q.bary, q.v, u)
+    ok = (fw["status"] & (oracle.NEAR_VERTEX | oracle.BOUNDARY)) == 0
+    assert ok.mean() > 0.5
+    assert np.abs(back - u)[ok].max() < 1e-12
+    # zero vector: out = u projected onto the start face, on a curved mesh
+    Xs, Fs = meshgen.icosphere(2, 0.0, rng)
+    ms = oracle.Mesh(Xs, Fs)
+    qs = meshgen.sample_queries(Xs, Fs, 50, rng, 0.1, 0.2, 0)
+    us = rng.normal(size=(50, 3))
+    w0 = oracle.exp_map(ms, qs.face, qs.bary, np.zeros((50, 3)), us[:, None, :])
+    b0, _ = oracle.transport_back(ms, qs.face, qs.bary, np.zeros((50, 3)), us)
+    n = np.cross(Xs[Fs[qs.face, 1]] - Xs[Fs[qs.face, 0]], Xs[Fs[qs.face, 2]] - Xs[Fs[qs.face, 0]])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    up = us - np.einsum("qj,qj->q", us, n)[:, None] * n
+    assert np.abs(w0["w"][:, 0] - up).max() < 1e-14
+    assert np.abs(b0 - up).max() < 1e-14
