@@ -99,6 +99,27 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def gather_ceilings(sg, ncross, ktimes):
+    """The walks' record reads against the device's own 32-B gather ceilings, measured after the
+    timed region by sg_probe_gather on an L2-resident 16 MiB table (the icosphere's half-edge and
+    face records take 10.5 MB): the L2 streaming read rate, independent random record gathers,
+    and chains of dependent gathers at each walk kernel's occupancy (one gather in flight per
+    thread, as in a walk), each with the walks' two 16-B loads per record and with one 256-bit
+    load.  Rates are of record bytes only (32 B per crossing)."""
+    tb = 16 << 20
+    W = sg.PROBE_LD256
+    out = {"table_MiB": tb >> 20, "stream_GBps": sg.probe_gather(sg.PROBE_STREAM, tb, 4, 256, 100),
+           "random_GBps": {"2x16B": sg.probe_gather(sg.PROBE_RANDOM, tb, 4, 256, 256),
+                           "1x32B": sg.probe_gather(sg.PROBE_RANDOM | W, tb, 4, 256, 256)}}
+    for k, key, bps, thr in (("k_walk_persistent", "walk", 4, 256), ("k_bwd_rewalk", "rewalk", 7, 128)):
+        rec = ncross * RECORD_BYTES / (float(np.mean(ktimes[key])) * 1e-3) / 1e9
+        c16 = sg.probe_gather(sg.PROBE_CHAIN, tb, bps, thr, 256)
+        c32 = sg.probe_gather(sg.PROBE_CHAIN | W, tb, bps, thr, 256)
+        out[k] = {"record_GBps": rec, "chain_GBps": {"2x16B": c16, "1x32B": c32},
+                  "frac_of_chain": {"2x16B": rec / c16, "1x32B": rec / c32}}
+    return out
+
+
 def load_workload(scale=1.0):
     import meshgen
     wl = meshgen.workload(WORKLOAD_INDEX, scale=scale)
@@ -491,6 +512,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=262144)
     ap.add_argument("--cpu-sample", type=int, default=1048576)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the 32-B gather ceilings measured after the timed steps")
     ap.add_argument("--kernel", type=int, default=2)
     ap.add_argument("--sort", type=int, default=-1, help="1 on, 0 off, -1 the library's automatic choice")
     ap.add_argument("--block", type=int, default=0)
@@ -699,6 +721,7 @@ def main():
                 "algorithmic_bytes_per_launch": int(kern[dom][0]), "launch_ms": kern[dom][1]}
     kernels = {k: {"ms": t, "algorithmic_GBps": b / (t * 1e-3) / 1e9, "frac_of_hbm": b / (t * 1e-3) / 1e9 / peak}
                for k, (b, t) in kern.items()}
+    l2_gather = None if args.no_probe else gather_ceilings(sg, ncross, ktimes)
 
     line = {"metric": METRIC, "value": value, "unit": "geodesics/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -715,6 +738,8 @@ def main():
                               "fp64": float(((st & 32) != 0).mean())},
             "gpu_launches": args.steps * launches_per_step,
             "roofline": roofline, "kernels": kernels, "clocks": clocks, "e2e": e2e}
+    if l2_gather is not None:
+        line["l2_gather"] = l2_gather
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         n, dt, _ = oracle_sample(args.cpu_sample, threads)

@@ -31,9 +31,17 @@ struct FaceRec {
     float l01, x2x, x2y, il1, il2;
 };
 
+// One 32-byte record = one L2 sector, read as two 16-byte loads.  (A single 256-bit load
+// doubles the device's dependent-gather ceiling, but the walks are bound by instruction issue,
+// not by gathers, and the forward walk ran 5% slower with it.)
+__device__ __forceinline__ void ld_rec32(const int4 *__restrict__ p, int4 &a, int4 &b) {
+    a = __ldg(p);
+    b = __ldg(p + 1);
+}
+
 __device__ __forceinline__ FaceRec load_rec(const int4 *__restrict__ rec, int f) {
-    int4 a = __ldg(rec + 2 * f);
-    int4 b = __ldg(rec + 2 * f + 1);
+    int4 a, b;
+    ld_rec32(rec + 2 * f, a, b);
     FaceRec r;
     r.n0 = a.x; r.n1 = a.y; r.n2 = a.z;
     r.l01 = __int_as_float(a.w);
