@@ -196,8 +196,11 @@ struct StraddleHook {
     float ub, vb;                // e_u / e_v offsets across d0 (start frame)
     float uq, vq;                // offsets along d0 over those across (0 when ub, vb = 0)
     float tol;                   // tau_near l_ref (1 + tphi^2), at least tau_near l_ref / cos(phi)
+    float sbound;                // every region below lies within |sig| <= sbound
     unsigned split;
     __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy, float px, float py) {
+        // nearly every vertex passed lies far from the eps-wide regions: reject on |sig| first
+        if (fabsf(sig_loc) > sbound) return;
         float tau = (Ltot - (w.Lh + w.Ll)) + (cx - px) * w.dx + (cy - py) * w.dy;
         float sig = (w.st & SG_PARITY_BIT) ? -sig_loc : sig_loc;
         if (tau < -tol || tau > Ltot + tol) return;
@@ -286,7 +289,7 @@ struct RewalkJob {
     const BwdArgs *A;
     Walker w;
     RewalkHook<GFD, GRADV> H;
-    int64_t q;
+    int32_t q;          // nq < 2^29 (checked at the entry point): one register
     bool valid;
 
     __device__ __forceinline__ bool init(int64_t t) {
@@ -312,6 +315,9 @@ struct RewalkJob {
             H.S.vb = A->eps_p * (-evx * d0y + evy * d0x);
             H.S.uq = H.S.ub != 0.f ? ua / H.S.ub : 0.f;
             H.S.vq = H.S.vb != 0.f ? va / H.S.vb : 0.f;
+            // the wedge needs sig < tau tphi + tol with tau <= Ltot + tol; the parallelograms
+            // |sig| < |ub| + tol, |vb| + tol (with a margin for the bound's own rounding)
+            H.S.sbound = 1.0001f * (fmaxf(fmaxf(fabsf(H.S.ub), fabsf(H.S.vb)), (L + H.S.tol) * H.S.tphi) + H.S.tol);
         }
         if (GRADV && H.gradv) {
             EndAdj E = end_adjoint(*A, q, w.foff);
