@@ -247,15 +247,15 @@ struct GradHook {
     float2 *eacc;
     float a, bs;        // gbar_i = a d_i + bs * s_i * perp(d_i)
     __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &G) {
-        const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;
+        const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;                // |e| e
         const float il = rsqrtf(fmaf(exr, exr, eyr * eyr));
-        const float ex = exr * il, ey = eyr * il;                       // e; n = (ey, -ex)
         const float yx = fmaf(c.Lr, w.dx, c.qx) - c.x0, yy = fmaf(c.Lr, w.dy, c.qy) - c.y0;  // y - A
-        const float ya = yx * ex + yy * ey, yc = yx * ey - yy * ex;
         const float sb = (w.st & SG_PARITY_BIT) ? -bs : bs;             // old-frame parity
         const float gx = a * w.dx - sb * w.dy, gy = a * w.dy + sb * w.dx;
-        const float ge = gx * ex + gy * ey, gn = gx * ey - gy * ex;
-        const float kB = il * (ge * yc - gn * ya);
+        // with n = (ey, -ex): (g.e)((y-A).n) - (g.n)((y-A).e) = -(g x (y-A)) for any unit e, so
+        // K = il (gy yx - gx yy); g_n = il (g x |e| e) needs no normalised e
+        const float kB = il * fmaf(gy, yx, -gx * yy);
+        const float gn = il * fmaf(gx, eyr, -gy * exr);
         const float kA = -(gn + kB);
         // the twin half-edge runs B -> A (A -> B when flipped); its record holds the edge id and
         // whether it is the edge's canonical half-edge
