@@ -564,7 +564,7 @@ def main():
     opts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
                            block=args.block if args.block > 0 else None)
     ws = torch.empty(sg.workspace_size(mesh, nq, opts), dtype=torch.uint8, device=dev)
-    bopts = sg.default_opts()
+    bopts = sg.default_opts(sort=args.sort)
     bws = torch.empty(sg.backward_workspace_size(mesh, "gfd", nq, True), dtype=torch.uint8, device=dev)
     # per-kernel events recorded by the library around its walk kernels (forward walk, GFD re-walk)
     kev = {k: [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for k in ("walk", "rewalk")}
@@ -576,7 +576,7 @@ def main():
     popts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
                             block=args.block if args.block > 0 else None)
     popts.prof_events = ctypes.addressof(kh["walk"])
-    pbopts = sg.default_opts()
+    pbopts = sg.default_opts(sort=args.sort)
     pbopts.prof_events = ctypes.addressof(kh["rewalk"])
     out = {"face": torch.empty(nq, dtype=torch.int32, device=dev), "bary": torch.empty(nq, 3, device=dev),
            "pos": torch.empty(nq, 3, device=dev), "dir": torch.empty(nq, 3, device=dev),
@@ -686,18 +686,20 @@ def main():
         e2e = {"value": nq / (np.mean(e_ms) * 1e-3), "unit": "geodesics/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    # ---- kernels the library launches per step: the walk (plus 5 sort/scan kernels when the
-    # queries are sorted), EP, the GFD re-walk, chords, literal walks and assemble, and the grad_V
-    # edge expansion and flush.  The automatic sort is on only when the mesh's records (128 B per
-    # face) exceed half of L2, as the library decides.
+    # ---- kernels the library launches per step: the walk, EP, the GFD re-walk, chords, literal
+    # walks and assemble, and the grad_V edge expansion and flush; plus the query order, as the
+    # library decides it: by start face (5 sort/scan kernels) when the mesh's records (128 B per
+    # face) exceed half of L2, else by walk length (2 kernels), for the forward and again for the
+    # backward re-walk (which uses the length order whenever the batch is large enough).
     if args.kernel == 1:
-        sort_on = False
+        sort_mode = 0
     elif args.sort >= 0:
-        sort_on = bool(args.sort)
+        sort_mode = args.sort
     else:
         l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-        sort_on = nq >= 65536 and 128 * mesh.n_faces > l2 // 2
-    launches_per_step = 8 + (5 if sort_on else 0)
+        sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
+    bwd_lorder = args.sort == 2 or (args.sort < 0 and nq >= 65536)
+    launches_per_step = 8 + {0: 0, 1: 5, 2: 2}[sort_mode] + (2 if bwd_lorder else 0)
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     peak, peak_kind = peaks()
@@ -728,7 +730,9 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "icosphere-s6-noisy 81920F 1Mq fwd+EP+GFD+gradV", "global_batch": world * nq,
                        "faces": int(len(F)), "queries_per_gpu": nq, "l2": "flushed between steps (512 MB write)",
-                       "kernel": "persistent" if args.kernel == 2 else "plain", "sort": sort_on,
+                       "kernel": "persistent" if args.kernel == 2 else "plain",
+                       "query_order": {0: "input", 1: "start face", 2: "walk length"}[sort_mode],
+                       "bwd_query_order": "walk length" if bwd_lorder else "input",
                        "fp64_classification": bool(args.fp64)},
             "crossings_per_s": world * ncross / (float(np.mean(ktimes["walk"])) * 1e-3),
             "fwd_geodesics_per_s": world * nq / (fwd_ms * 1e-3),

@@ -71,10 +71,15 @@ typedef enum sg_status {
 typedef struct sg_opts {
     int32_t max_steps;      /* loop cap per query (Alg. gpu_parallel MAX_STEPS); <= 0: 1<<20 */
     int32_t kernel;         /* SG_KERNEL_*; AUTO = persistent */
-    int32_t sort;           /* 1: order queries by (mesh, start face) before walking; 0: no;
-                               <0: auto -- on for batches of >= 65536 queries on meshes whose
-                               walk records (128 B per face) exceed half of L2, off otherwise
-                               (records that stay in L2 are gathered as fast in any order) */
+    int32_t sort;           /* order in which the persistent kernels take the queries:
+                               0: input order; 1: by (mesh, start face); 2: by walk length,
+                               longest first (L or |v| over l_ref, an eighth of an octave per
+                               bucket: lanes of a warp then finish together and idle less);
+                               <0: auto -- for batches of >= 65536 queries, 1 on meshes whose
+                               walk records (128 B per face) exceed half of L2 (locality of the
+                               gathers), else 2; input order for smaller batches.  Outputs are
+                               always in input order.  sg_exp_map_backward's re-walk uses the
+                               length order when sort is 2, or auto with >= 65536 queries. */
     int32_t block;          /* threads per block; <= 0: 256 */
     int32_t blocks_per_sm;  /* persistent kernel residency; <= 0: as many as fit */
     int32_t fp64_escalate;  /* 1: re-evaluate near-vertex classification in FP64 (persistent only) */
@@ -329,9 +334,9 @@ sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id
 /*
  * sg_exp_map_backward_workspace_size -- bytes of device scratch sg_exp_map_backward needs for
  * nq queries with `estimator` (SG_EST_*) and, if want_grad_V != 0, the vertex gradient: the
- * GFD column table (16 B per query) and literal-walk task list (12 B per query), and
- * a float4 accumulator per vertex for grad_V.  Pass it as o->workspace; without it the
- * library allocates stream-ordered scratch itself.
+ * GFD column table (16 B per query) and literal-walk task list (12 B per query), a float4
+ * accumulator per vertex for grad_V, and the re-walk's length order (5 B per query).  Pass it
+ * as o->workspace; without it the library allocates stream-ordered scratch itself.
  */
 sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_t estimator, int64_t nq,
                                              int32_t want_grad_V, size_t *bytes);

@@ -84,6 +84,7 @@ struct BwdArgs {
     float *cols;        // [nq][4] column contractions: par, perp, u, v (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) columns recomputed by literal walks (scratch)
     int32_t *ntask;     // task counter (scratch)
+    const int32_t *perm;  // re-walk queue position -> query (length order), or NULL
 };
 
 struct F3 {
@@ -293,7 +294,7 @@ struct RewalkJob {
     bool valid;
 
     __device__ __forceinline__ bool init(int64_t t) {
-        q = t;
+        q = A->perm ? __ldg(A->perm + t) : (int32_t)t;
         const WalkParams &P = A->P;
         Carry<0> cw;
         bool live = walker_init<0>(P, A->in, q, w, cw);
@@ -694,13 +695,23 @@ unsigned persistent_grid(K kernel, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
 }
 struct BwdLayout {
-    size_t gacc, eacc, cols, tasks, ntask, gpos, total;
+    size_t gacc, eacc, cols, tasks, ntask, gpos, lcounts, lkeys, perm, total;
 };
-BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool grad_V) {
+// The re-walk takes its queries longest first (the forward's length order, rebuilt here) for
+// batches of at least this many queries, unless opts.sort is 0.
+#define SG_BWD_LORDER_MIN 65536
+bool bwd_lorder(const sg_opts &r, int64_t nq) { return r.sort == 2 || (r.sort < 0 && nq >= SG_BWD_LORDER_MIN); }
+
+BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool grad_V, bool lorder) {
     BwdLayout L{};
     size_t o = 0;
     L.ntask = o; o = align_up(o + 64, 256);
     L.gpos = o; o = align_up(o + sizeof(float) * 3 * (size_t)std::max<int64_t>(nq, 1), 256);
+    if (lorder) {
+        L.lcounts = o; o = align_up(o + sizeof(int32_t) * 2 * SG_LBUCKETS, 256);
+        L.lkeys = o; o = align_up(o + (size_t)std::max<int64_t>(nq, 1), 256);
+        L.perm = o; o = align_up(o + sizeof(int32_t) * (size_t)std::max<int64_t>(nq, 1), 256);
+    }
     if (grad_V) {
         L.gacc = o; o = align_up(o + sizeof(float4) * (size_t)nV, 256);
         L.eacc = o; o = align_up(o + sizeof(float2) * (size_t)std::max<int64_t>(nE, 1), 256);
@@ -718,7 +729,8 @@ extern "C" sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_
                                                         int32_t want_grad_V, size_t *bytes) {
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
     if (estimator != SG_EST_EP && estimator != SG_EST_GFD) return SG_ERR_INVALID_ARG;
-    *bytes = bwd_layout(m->nV, m->nE, nq, estimator, want_grad_V != 0).total;
+    // room for the length order whatever the options (the layout without it is smaller)
+    *bytes = bwd_layout(m->nV, m->nE, nq, estimator, want_grad_V != 0, true).total;
     return SG_OK;
 }
 
@@ -759,7 +771,8 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.out_status = out_status;
     A.eps_v = eps_v; A.eps_p = eps_p;
 
-    BwdLayout Lw = bwd_layout(m->nV, m->nE, nq, estimator, grad_V != nullptr);
+    const bool lorder = (estimator == SG_EST_GFD || grad_V) && bwd_lorder(r, nq);  // only the re-walk uses it
+    BwdLayout Lw = bwd_layout(m->nV, m->nE, nq, estimator, grad_V != nullptr, lorder);
     void *ws = nullptr;
     bool own = false;
     if (r.workspace) {
@@ -777,6 +790,11 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     }
     if (estimator == SG_EST_GFD) { A.cols = (float *)(base + Lw.cols); A.tasks = (int32_t *)(base + Lw.tasks); }
     cudaMemsetAsync(A.ntask, 0, 64, s);
+    if (lorder) {
+        int32_t *perm = (int32_t *)(base + Lw.perm);
+        sg_length_order(m, A.in, nq, (uint8_t *)(base + Lw.lkeys), (int32_t *)(base + Lw.lcounts), perm, s);
+        A.perm = perm;
+    }
     const unsigned gq256 = (unsigned)((nq + 255) / 256);
     if (g_bary) {  // fold the end-barycentric gradient into an effective g_pos
         float *geff = (float *)(base + Lw.gpos);

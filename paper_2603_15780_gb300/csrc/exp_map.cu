@@ -318,6 +318,85 @@ __global__ void k_sort_scatter(int64_t nq, const int32_t *__restrict__ mesh_id, 
     }
 }
 
+// ------------------------------------------------------------------ length order
+// Walks of similar length end together, so a warp whose lanes hold them waits less with idle
+// lanes before it refills.  Key: an eighth of an octave of L / l_ref per bucket, longest walks
+// first (the short ones then fill the tail of the queue); invalid queries last.  L is the given
+// length, else |v| (its ambient norm: a key, not the walked length).
+__device__ __forceinline__ int length_key(const QueryIn &in, const float *__restrict__ lref, int64_t i) {
+    const int m = in.mesh_id ? __ldg(in.mesh_id + i) : 0;
+    if (m < 0 || m >= in.n_mesh) return SG_LBUCKETS - 1;
+    float L;
+    if (in.length) {
+        L = __ldg(in.length + i);
+    } else {
+        const float x = __ldg(in.v + 3 * i), y = __ldg(in.v + 3 * i + 1), z = __ldg(in.v + 3 * i + 2);
+        L = sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
+    }
+    const float lr = __ldg(lref + m);
+    if (!(L > 0.f) || !(L <= 3.0e38f) || !(lr > 0.f)) return SG_LBUCKETS - 1;
+    const float t = fminf(fmaxf(fmaf(8.f, __log2f(L / lr), 128.f), 0.f), (float)(SG_LBUCKETS - 2));
+    return SG_LBUCKETS - 2 - (int)t;
+}
+
+__global__ void __launch_bounds__(256) k_lorder_hist(int64_t nq, QueryIn in, const float *__restrict__ lref,
+                                                     uint8_t *__restrict__ keys, int32_t *__restrict__ counts) {
+    __shared__ int32_t h[SG_LBUCKETS];
+    for (int b = threadIdx.x; b < SG_LBUCKETS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = length_key(in, lref, i);
+        keys[i] = (uint8_t)k;
+        atomicAdd(&h[k], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < SG_LBUCKETS; b += blockDim.x)
+        if (h[b]) atomicAdd(counts + b, h[b]);
+}
+
+// counts[0, 256) the bucket totals, counts[256, 512) zeroed cursors.  Each block takes chunks of
+// 256 x SG_LCHUNK queries, ranks them within the chunk per bucket in shared memory, reserves one
+// range per (chunk, bucket) with a single global atomic and writes the permutation.
+#define SG_LCHUNK 8
+__global__ void __launch_bounds__(256) k_lorder_scatter(int64_t nq, const uint8_t *__restrict__ keys,
+                                                        int32_t *__restrict__ counts, int32_t *__restrict__ perm) {
+    __shared__ int32_t start[SG_LBUCKETS], lh[SG_LBUCKETS], base[SG_LBUCKETS];
+    if (threadIdx.x < 32) {  // exclusive scan of the totals: 8 buckets per lane
+        const int lane = threadIdx.x;
+        int32_t v[SG_LBUCKETS / 32], sum = 0;
+        for (int j = 0; j < SG_LBUCKETS / 32; ++j) { v[j] = counts[lane * (SG_LBUCKETS / 32) + j]; sum += v[j]; }
+        int32_t x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        int32_t e = x - sum;
+        for (int j = 0; j < SG_LBUCKETS / 32; ++j) { start[lane * (SG_LBUCKETS / 32) + j] = e; e += v[j]; }
+    }
+    const int64_t chunk = (int64_t)blockDim.x * SG_LCHUNK;
+    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < nq; c0 += (int64_t)gridDim.x * chunk) {
+        for (int b = threadIdx.x; b < SG_LBUCKETS; b += blockDim.x) lh[b] = 0;
+        __syncthreads();
+        int k[SG_LCHUNK], r[SG_LCHUNK];
+#pragma unroll
+        for (int j = 0; j < SG_LCHUNK; ++j) {
+            const int64_t i = c0 + (int64_t)j * blockDim.x + threadIdx.x;
+            k[j] = i < nq ? (int)keys[i] : 0;
+            r[j] = i < nq ? atomicAdd(&lh[k[j]], 1) : 0;
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < SG_LBUCKETS; b += blockDim.x)
+            if (lh[b]) base[b] = start[b] + atomicAdd(counts + SG_LBUCKETS + b, lh[b]);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < SG_LCHUNK; ++j) {
+            const int64_t i = c0 + (int64_t)j * blockDim.x + threadIdx.x;
+            if (i < nq) perm[base[k[j]] + r[j]] = (int32_t)i;
+        }
+        __syncthreads();
+    }
+}
+
 #define SCAN_BLOCK 1024
 #define SCAN_ITEMS 4
 #define SCAN_TILE (SCAN_BLOCK * SCAN_ITEMS)
@@ -385,29 +464,34 @@ thread_local char g_err[256];
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-    size_t counter, counts, sums, perm, total;
+    size_t counter, counts, sums, keys, perm, total;
 };
 
-WsLayout ws_layout(int64_t nF, int64_t nq, bool sort) {
+// sort: 0 none, 1 by (mesh, start face), 2 by walk length
+WsLayout ws_layout(int64_t nF, int64_t nq, int sort) {
     WsLayout L{};
     size_t o = 0;
     L.counter = o; o = align_up(o + 64, 256);
-    if (sort) {
+    if (sort == 1) {
         int64_t nk = nF + 1;
         int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
         L.counts = o; o = align_up(o + sizeof(int32_t) * nk, 256);
         L.sums = o; o = align_up(o + sizeof(int32_t) * ntiles, 256);
+        L.perm = o; o = align_up(o + sizeof(int32_t) * std::max<int64_t>(nq, 1), 256);
+    } else if (sort == 2) {
+        L.counts = o; o = align_up(o + sizeof(int32_t) * 2 * SG_LBUCKETS, 256);
+        L.keys = o; o = align_up(o + (size_t)std::max<int64_t>(nq, 1), 256);
         L.perm = o; o = align_up(o + sizeof(int32_t) * std::max<int64_t>(nq, 1), 256);
     }
     L.total = o;
     return L;
 }
 
-// The automatic choice (sort < 0) orders queries by start face only when it pays: for batches
-// of at least SG_SORT_MIN_BATCH queries on meshes whose walk records (128 B per face: face and
-// half-edge records) exceed half of L2.  When the records stay in L2 the gathers hit L2 in any
-// order and the sort's five launches are pure cost (measured: icosphere s6 and torus 262k walks
-// are as fast or faster unsorted; a 4.2M-face heightfield is 12% faster sorted).
+// The automatic choice (sort < 0), for batches of at least SG_SORT_MIN_BATCH queries: by start
+// face on meshes whose walk records (128 B per face: face and half-edge records) exceed half of
+// L2 (a 4.2M-face heightfield walks 12% faster so ordered), else by walk length.  Records that
+// stay in L2 are gathered as fast in any order (icosphere s6 and torus walks are as fast or
+// faster without the start-face order), but lanes holding walks of similar length idle less.
 #define SG_SORT_MIN_BATCH 65536
 
 int l2_bytes() {
@@ -431,7 +515,8 @@ sg_opts resolve(const sg_opts *o, int64_t nq, int64_t nF) {
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
     if (r.tau_snap <= 0.f) r.tau_snap = r.precision == 64 ? 1e-12f : 1e-6f;
     if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
-    if (r.sort < 0) r.sort = (nq >= SG_SORT_MIN_BATCH && 128 * nF > (int64_t)l2_bytes() / 2) ? 1 : 0;
+    if (r.sort < 0)
+        r.sort = nq < SG_SORT_MIN_BATCH ? 0 : (128 * nF > (int64_t)l2_bytes() / 2 ? 1 : 2);
     if (r.kernel == SG_KERNEL_PLAIN) { r.sort = 0; r.fp64_escalate = 0; }
     return r;
 }
@@ -645,7 +730,8 @@ sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info) {
 sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts *o, size_t *bytes) {
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
     sg_opts r = resolve(o, nq, m->nF);
-    *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT && r.sort).total;
+    if (r.sort < 0 || r.sort > 2) return SG_ERR_INVALID_ARG;
+    *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT ? r.sort : 0).total;
     return SG_OK;
 }
 
@@ -668,7 +754,7 @@ FwdArgs fwd_args(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int
 // of queries by (mesh, start face).  Uses the caller's workspace or stream-ordered scratch
 // (*own_ws = the pointer to free after the walk).
 sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const sg_opts &r,
-                        bool sort, cudaStream_t s, FwdArgs &a, void **own_ws) {
+                        int sort, cudaStream_t s, FwdArgs &a, void **own_ws) {
     *own_ws = nullptr;
     WsLayout L = ws_layout(m->nF, nq, sort);
     void *ws = nullptr;
@@ -682,7 +768,11 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
     char *base = (char *)ws;
     a.counter = (int32_t *)(base + L.counter);
     if (cudaMemsetAsync(a.counter, 0, 64, s) != cudaSuccess) return SG_ERR_CUDA;
-    if (sort) {
+    if (sort == 2) {
+        int32_t *perm = (int32_t *)(base + L.perm);
+        sg_length_order(m, a.in, nq, (uint8_t *)(base + L.keys), (int32_t *)(base + L.counts), perm, s);
+        a.perm = perm;
+    } else if (sort == 1) {
         int32_t *counts = (int32_t *)(base + L.counts);
         int32_t *sums = (int32_t *)(base + L.sums);
         int32_t *perm = (int32_t *)(base + L.perm);
@@ -705,6 +795,18 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
 
 }  // namespace
 
+void sg_length_order(const sg_mesh *m, const QueryIn &in, int64_t nq, uint8_t *keys, int32_t *counts, int32_t *perm,
+                     cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * SG_LBUCKETS, s);
+    const int64_t g1 = std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 4);
+    k_lorder_hist<<<(unsigned)std::max<int64_t>(g1, 1), 256, 0, s>>>(nq, in, m->d_lref, keys, counts);
+    const int64_t g2 = std::min<int64_t>((nq + 256 * SG_LCHUNK - 1) / (256 * SG_LCHUNK), (int64_t)sms * 4);
+    k_lorder_scatter<<<(unsigned)std::max<int64_t>(g2, 1), 256, 0, s>>>(nq, keys, counts, perm);
+}
+
 extern "C" {
 
 sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const float *bary,
@@ -718,6 +820,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (n_w > 0 && !w) return SG_ERR_INVALID_ARG;
     sg_opts r = resolve(o, nq, m->nF);
     if (r.kernel != SG_KERNEL_PLAIN && r.kernel != SG_KERNEL_PERSISTENT) return SG_ERR_INVALID_ARG;
+    if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode && r.kernel == SG_KERNEL_PLAIN) return SG_ERR_UNSUPPORTED;
@@ -732,7 +835,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     const bool persistent = r.kernel == SG_KERNEL_PERSISTENT;
     void *own_ws = nullptr;
     if (persistent) {
-        sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.sort != 0, s, a, &own_ws);
+        sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.sort, s, a, &own_ws);
         if (st != SG_OK) {
             if (own_ws) cudaFreeAsync(own_ws, s);
             return st;
@@ -786,6 +889,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
     if (path_cap > 0 && !out_path_face) return SG_ERR_INVALID_ARG;
     sg_opts r = resolve(o, nq, m->nF);
     if (r.boundary_mode || r.precision == 64) return SG_ERR_UNSUPPORTED;
+    if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a = fwd_args(m, nq, mesh_id, face, bary, v, length, nullptr, r);
@@ -796,7 +900,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
     t.staged = path_cap % 4 == 0 && ((uintptr_t)out_path_face % 16) == 0 &&
                (!t.pt || ((uintptr_t)t.pt % 16) == 0);
     void *own_ws = nullptr;
-    sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.sort != 0 && r.kernel != SG_KERNEL_PLAIN, s, a, &own_ws);
+    sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.kernel != SG_KERNEL_PLAIN ? r.sort : 0, s, a, &own_ws);
     if (st != SG_OK) {
         if (own_ws) cudaFreeAsync(own_ws, s);
         return st;

@@ -750,6 +750,11 @@ struct SgFwdIO {
     int32_t *counter;
 };
 sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s);
+// Length order of a batch (exp_map.cu): perm[0 .. nq) = the queries longest walk first, in
+// buckets of an eighth of an octave of L / l_ref.  Scratch: keys (nq bytes), counts (512 int32).
+#define SG_LBUCKETS 256
+void sg_length_order(const sg_mesh *m, const QueryIn &in, int64_t nq, uint8_t *keys, int32_t *counts, int32_t *perm,
+                     cudaStream_t s);
 cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const sg_opts &r, cudaStream_t s);
 
 struct Frame3 {

@@ -32,10 +32,10 @@ def _bad_batch():
     return X, F, q, np.arange(7)
 
 
-VARIANTS = [dict(), dict(kernel=1), dict(sort=0), dict(boundary_mode=1), dict(precision=64)]
+VARIANTS = [dict(), dict(kernel=1), dict(sort=0), dict(sort=2), dict(boundary_mode=1), dict(precision=64)]
 
 
-@pytest.mark.parametrize("kw", VARIANTS, ids=["persistent", "plain", "unsorted", "hole", "fp64"])
+@pytest.mark.parametrize("kw", VARIANTS, ids=["persistent", "plain", "unsorted", "length-order", "hole", "fp64"])
 def test_bad_queries_are_invalid_and_the_rest_walk(kw):
     X, F, q, bad = _bad_batch()
     X32 = parity.as_f32(X)
@@ -60,10 +60,12 @@ def test_bad_lengths_and_mesh_ids():
     mid[0], mid[1] = -1, 2
     L = np.full(64, 0.5, np.float32)
     L[2], L[3] = -1.0, np.nan
-    out = sg().exp_map(mesh, q.face, parity.as_f32(q.bary), parity.as_f32(q.v), length=L, mesh_id=mid)
-    st = out["status"].cpu().numpy()
-    assert np.all(st[:4] & oracle.INVALID)
-    assert not np.any(st[4:] & oracle.INVALID)
+    for sort in (0, 1, 2):   # invalid mesh ids and lengths take the last bucket of the length order
+        out = sg().exp_map(mesh, q.face, parity.as_f32(q.bary), parity.as_f32(q.v), length=L, mesh_id=mid,
+                           sort=sort)
+        st = out["status"].cpu().numpy()
+        assert np.all(st[:4] & oracle.INVALID)
+        assert not np.any(st[4:] & oracle.INVALID)
 
 
 def test_backward_of_invalid_queries_is_zero():

@@ -25,10 +25,12 @@ KERNELS = [
     dict(kernel=1),                                  # plain: one thread per query, FP32
     dict(kernel=2, sort=1, fp64_escalate=1),         # persistent, sorted, FP64 classification
     dict(kernel=2, sort=0, fp64_escalate=0, block=128),
+    dict(kernel=2, sort=2, fp64_escalate=1),         # persistent, longest walks first
 ]
 
 
-@pytest.mark.parametrize("kw", KERNELS, ids=["plain", "persistent-sorted-fp64", "persistent-unsorted"])
+@pytest.mark.parametrize("kw", KERNELS, ids=["plain", "persistent-sorted-fp64", "persistent-unsorted",
+                                             "persistent-length-order"])
 def test_icosphere_s3_full_workload(kw):
     """Workload 0 in full: icosphere s3, 4096 queries, one carried vector."""
     wl = meshgen.workload(0)
