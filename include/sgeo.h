@@ -295,7 +295,9 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
  *   grad_w     float32 [nq][n_w][3]  dL/dw = R^T g_w (parallel transport is a rotation of the
  *                               tangent planes for a fixed face sequence; exact)
  *   out_status uint32 [nq]      SG_ST_* of the extra walks (GFD) or of the re-walk
- * Asynchronous on `stream`.
+ * Asynchronous on `stream`.  Errors: SG_ERR_INVALID_ARG (bad estimator, eps <= 0 for GFD, a
+ * required array NULL, nq above 536,869,887), SG_ERR_UNSUPPORTED (precision 64), SG_ERR_OOM
+ * (no workspace given and none could be allocated), SG_ERR_CUDA.
  */
 sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, float eps_p,
                               int64_t nq, const int32_t *mesh_id, const int32_t *face,

@@ -18,13 +18,13 @@
 //                  e_u, e_v); a perturbation that sweeps a vertex (or any perturbation of a
 //                  walk that stopped on the boundary) is appended to a task list.  The same
 //                  re-walk accumulates grad_V (below).
-//   k_bwd_chords   evaluates every column as the 3-D chord of a short walk from p' along
-//                  R delta, summed segment by segment (exact for unswept perturbations, no
-//                  cancellation against |p'|);
-//   k_bwd_literal  overwrites the swept columns with the paper's literal walk
+//   k_bwd_literal  evaluates the swept columns by the paper's literal walk
 //                  (Exp(p, v + eps e_perp), or Exp(p_u, v_u) after Exp(p, eps e_u) carrying v),
 //                  differences taken in face-local coordinates;
-//   k_bwd_assemble contracts the columns into grad_v, grad_p, grad_bary.
+//   k_bwd_assemble evaluates every other column as the 3-D chord of a short walk from p'
+//                  along R delta, summed segment by segment (exact for unswept
+//                  perturbations, no cancellation against |p'|), and contracts the columns
+//                  into grad_v, grad_p, grad_bary.
 //
 // grad_V (vertex positions; not in the paper): the a.e. derivative of p' with the face
 // sequence fixed.  The end point is a chain of rigid 2-D maps T (one per crossing) applied
@@ -51,9 +51,11 @@
 #ifndef SG_REWALK_REFILL
 #define SG_REWALK_REFILL 24
 #endif
-// minimum resident blocks per SM the chord and literal kernels are compiled for
-#ifndef SG_CHORDS_MINB
-#define SG_CHORDS_MINB 7
+// minimum resident blocks per SM the assemble and literal kernels are compiled for (assemble,
+// fwd+EP+GFD+grad_V step on 1M queries: 5 blocks 1.600 ms without spills, 6 1.602, 7 1.603;
+// the chord walk inlined four times instead of called: 1.625 / 1.617 / 1.610)
+#ifndef SG_ASSEMBLE_MINB
+#define SG_ASSEMBLE_MINB 5
 #endif
 #ifndef SG_LITERAL_MINB
 #define SG_LITERAL_MINB 1
@@ -82,7 +84,8 @@ struct BwdArgs {
     float4 *gacc;       // [nV] vertex-gradient accumulator (scratch)
     float2 *eacc;       // [nE] per interior edge (start, end) coefficients, canonical orientation (scratch)
     const int2 *edges;  // [nE] (canonical half-edge, twin)
-    float *cols;        // [nq][4] column contractions: par, perp, u, v (scratch)
+    float *cols;        // [nq][4] column contractions: par, perp, u, v; until the chords are
+                        // evaluated the par slot holds the re-walk's swept-column mask (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) columns recomputed by literal walks (scratch)
     int32_t *ntask;     // task counter (scratch)
     const int32_t *perm;  // re-walk queue position -> query (length order), or NULL
@@ -369,6 +372,7 @@ struct RewalkJob {
             // is the chord from p' in every case (Round 2 of the paper's batching).
             unsigned split = H.S.split;
             if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) split = 7u;
+            A->cols[4 * (int64_t)q] = __uint_as_float(split);  // read by k_bwd_assemble
             if (split) {
                 st |= SG_ST_GFD_SPLIT;
                 int base = atomicAdd(A->ntask, __popc(split));
@@ -410,29 +414,36 @@ __device__ F3 pos_diff(const WalkParams &P, const Walker &a, const Walker &b) {
     return (vpos(P, ta.x) - vpos(P, tb.x)) + lift(Fa, a.px, a.py) - lift(Fb, b.px, b.py);
 }
 
-// 3-D chord of a walk of length `len` from the walker's position along unit 2-D direction u
-// (face frame), as the cancellation-free difference of the end and start positions
+__device__ __forceinline__ float contract(F3 c, const EndAdj &E, float eps) {
+    return dot3(c - dot3(c, E.nm) * E.nm, E.g) / eps;
+}
+
+// A walk of length `len` from the end state w0 along unit 2-D direction u (face frame); its
+// 3-D chord is the cancellation-free difference of its end and start positions, contracted.
 template <bool HOLE>
-__device__ F3 short_chord(const WalkParams &P, const Walker &w0, float ux, float uy, float len) {
-    // a chord that ends inside the end face, farther than tau_near l_ref from its edges, is the
-    // lifted step itself (no walk, and no cancellation of the two end positions)
-    {
-        const FaceRec &R = w0.R;
-        const float x = fmaf(len, ux, w0.px), y = fmaf(len, uy, w0.py);
-        const float tol = P.tau_near * w0.lref;
-        const float e1 = ((R.x2x - R.l01) * y - R.x2y * (x - R.l01)) * R.il1;
-        const float e2 = (R.x2y * x - R.x2x * y) * R.il2;
-        if (y > tol && e1 > tol && e2 > tol) return lift(load_frm(P, w0.f), len * ux, len * uy);
-    }
+__device__ __noinline__ float chord_walk(const WalkParams &P, const Walker &w0, const EndAdj &E, float ux, float uy,
+                                         float len) {
     Walker w = w0;
     w.dx = ux; w.dy = uy; w.Lh = len; w.Ll = 0.f; w.mode = 6; w.steps = 0;
     while (!walker_step<true, HOLE>(w, P)) {
     }
-    return pos_diff(P, w, w0);
+    return contract(pos_diff(P, w, w0), E, len);
 }
 
-__device__ __forceinline__ float contract(F3 c, const EndAdj &E, float eps) {
-    return dot3(c - dot3(c, E.nm) * E.nm, E.g) / eps;
+// Contracted chord (p'' - p') / len of a walk of length `len` from the end state along u.  A
+// chord that ends inside the end face, farther than tau_near l_ref from its edges, is the step
+// len u itself, and its contraction u . gm = (u.d') a + (u.perp d') b needs no walk.
+template <bool HOLE>
+__device__ __forceinline__ float chord_col(const WalkParams &P, const Walker &w0, const EndAdj &E, float ux, float uy,
+                                           float len) {
+    const FaceRec &R = w0.R;
+    const float x = fmaf(len, ux, w0.px), y = fmaf(len, uy, w0.py);
+    const float tol = P.tau_near * w0.lref;
+    const float e1 = ((R.x2x - R.l01) * y - R.x2y * (x - R.l01)) * R.il1;
+    const float e2 = (R.x2y * x - R.x2x * y) * R.il2;
+    if (y > tol && e1 > tol && e2 > tol)
+        return fmaf(fmaf(ux, E.dmx, uy * E.dmy), E.a, fmaf(uy, E.dmx, -ux * E.dmy) * E.b);
+    return chord_walk<HOLE>(P, w0, E, ux, uy, len);
 }
 
 // R x for a start-frame 2-D vector x: (x.d0) d' + s (x.perp d0) perp d'
@@ -440,33 +451,6 @@ __device__ __forceinline__ void rmap(float x, float y, float d0x, float d0y, con
     float al = x * d0x + y * d0y, be = -x * d0y + y * d0x;
     ox = al * E.dmx - E.sm * be * E.dmy;
     oy = al * E.dmy + E.sm * be * E.dmx;
-}
-
-template <bool HOLE>
-__global__ void __launch_bounds__(128, SG_CHORDS_MINB) k_bwd_chords(BwdArgs A) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= A.nq) return;
-    const WalkParams &P = A.P;
-    Walker w;
-    Carry<0> cw;
-    bool live = walker_init<0>(P, A.in, q, w, cw);
-    float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (live && !(w.st & SG_ST_INVALID)) {
-        const float d0x = w.dx, d0y = w.dy;
-        const float evx = w.R.x2x * w.R.il2, evy = w.R.x2y * w.R.il2;
-        EndAdj E = end_adjoint(A, q, w.foff);
-        Walker we;
-        end_walker(A, q, w, E, we);
-        float ux, uy;
-        col.x = contract(short_chord<HOLE>(P, we, E.dmx, E.dmy, A.eps_v), E, A.eps_v);
-        rmap(-d0y, d0x, d0x, d0y, E, ux, uy);
-        col.y = contract(short_chord<HOLE>(P, we, ux, uy, A.eps_v), E, A.eps_v);
-        rmap(1.f, 0.f, d0x, d0y, E, ux, uy);
-        col.z = contract(short_chord<HOLE>(P, we, ux, uy, A.eps_p), E, A.eps_p);
-        rmap(evx, evy, d0x, d0y, E, ux, uy);
-        col.w = contract(short_chord<HOLE>(P, we, ux, uy, A.eps_p), E, A.eps_p);
-    }
-    *reinterpret_cast<float4 *>(A.cols + 4 * q) = col;
 }
 
 // literal walk of one swept perturbation (task = q << 2 | k): k = 1 walks Exp(p, v + eps e_perp);
@@ -530,7 +514,10 @@ __global__ void __launch_bounds__(128, SG_LITERAL_MINB) k_bwd_literal(BwdArgs A)
     run_persistent<LiteralJob<HOLE>, SG_LITERAL_REFILL>(A.ntask + 2, (int64_t)*A.ntask, job);
 }
 
-__global__ void __launch_bounds__(256) k_bwd_assemble(BwdArgs A) {
+// Columns the re-walk found unswept are chords from p' (the par column always is); the swept
+// ones were written by k_bwd_literal.  Then the columns are contracted into the gradients.
+template <bool HOLE>
+__global__ void __launch_bounds__(128, SG_ASSEMBLE_MINB) k_bwd_assemble(BwdArgs A) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= A.nq) return;
     const WalkParams &P = A.P;
@@ -540,6 +527,27 @@ __global__ void __launch_bounds__(256) k_bwd_assemble(BwdArgs A) {
     F3 gv = f3(0.f, 0.f, 0.f), gp = gv, gb = gv;
     if (live && !(w.st & SG_ST_INVALID)) {
         float4 c = *reinterpret_cast<const float4 *>(A.cols + 4 * q);
+        const unsigned split = __float_as_uint(c.x);
+        {
+            const float d0x = w.dx, d0y = w.dy;
+            EndAdj E = end_adjoint(A, q, w.foff);
+            Walker we;
+            end_walker(A, q, w, E, we);
+            float ux, uy;
+            c.x = chord_col<HOLE>(P, we, E, E.dmx, E.dmy, A.eps_v);
+            if (!(split & 1u)) {
+                rmap(-d0y, d0x, d0x, d0y, E, ux, uy);
+                c.y = chord_col<HOLE>(P, we, E, ux, uy, A.eps_v);
+            }
+            if (!(split & 2u)) {
+                rmap(1.f, 0.f, d0x, d0y, E, ux, uy);
+                c.z = chord_col<HOLE>(P, we, E, ux, uy, A.eps_p);
+            }
+            if (!(split & 4u)) {
+                rmap(w.R.x2x * w.R.il2, w.R.x2y * w.R.il2, d0x, d0y, E, ux, uy);
+                c.w = chord_col<HOLE>(P, we, E, ux, uy, A.eps_p);
+            }
+        }
         Fr2 F0 = load_frm(P, w.f);
         gv = c.x * lift(F0, w.dx, w.dy) + c.y * lift(F0, -w.dy, w.dx);
         F3 eu = lift(F0, 1.f, 0.f), ev = lift(F0, w.R.x2x * w.R.il2, w.R.x2y * w.R.il2);
@@ -818,13 +826,12 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         else k_bwd_rewalk<true, false><<<persistent_grid(k_bwd_rewalk<true, false>, nq), 128, 0, s>>>(A);
         if (pev) cudaEventRecord(pev[1], s);
         if (r.boundary_mode) {
-            k_bwd_chords<true><<<g128, 128, 0, s>>>(A);
             k_bwd_literal<true><<<persistent_grid(k_bwd_literal<true>, 3 * nq), 128, 0, s>>>(A);
+            k_bwd_assemble<true><<<g128, 128, 0, s>>>(A);
         } else {
-            k_bwd_chords<false><<<g128, 128, 0, s>>>(A);
             k_bwd_literal<false><<<persistent_grid(k_bwd_literal<false>, 3 * nq), 128, 0, s>>>(A);
+            k_bwd_assemble<false><<<g128, 128, 0, s>>>(A);
         }
-        k_bwd_assemble<<<g256, 256, 0, s>>>(A);
     }
     if ((g_dir && grad_v) || (A.n_w > 0)) k_bwd_transport<<<g256, 256, 0, s>>>(A);
     if (grad_V) {
