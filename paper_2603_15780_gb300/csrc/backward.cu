@@ -88,6 +88,8 @@ struct BwdArgs {
                         // evaluated the par slot holds the re-walk's swept-column mask (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) columns recomputed by literal walks (scratch)
     int32_t *ntask;     // task counter (scratch)
+    int4 *rst;          // [nq][2] where the literal walks of a split query restart (scratch):
+                        // {half-edge | parity << 30 (-1: from the start), s, dx, dy}, {Lh, Ll, -, -}
     const int32_t *perm;  // re-walk queue position -> query (length order), or NULL
 };
 
@@ -196,42 +198,61 @@ __global__ void __launch_bounds__(256) k_ep_backward(BwdArgs A) {
 
 // ------------------------------------------------------------------ re-walk hooks
 // Straddle test of the GFD perturbations against the corners the base walk meets.
+// The perturbed rays run in the base ray's face strip until the first corner they sweep, so the
+// literal walks of a split query can restart on the entry edge of the face where the first such
+// corner was met; the hook stores the base walker's state there (bit 3 of `split`).
+#define SG_SPLIT_RESTART 8u
 struct StraddleHook {
+    const BwdArgs *A;
     float Ltot, tphi;            // e_perp wedge: tan of its opening angle, eps_v / L
     float ub, vb;                // e_u / e_v offsets across d0 (start frame)
     float uq, vq;                // offsets along d0 over those across (0 when ub, vb = 0)
     float tol;                   // tau_near l_ref (1 + tphi^2), at least tau_near l_ref / cos(phi)
     float sbound;                // every region below lies within |sig| <= sbound
     unsigned split;
-    __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy, float px, float py) {
+    // RECORD: the walker sits on a half-edge (the apex test of the hot step), where a first
+    // swept corner stores the restart state
+    template <bool RECORD>
+    __device__ __forceinline__ void test_at(const Walker &w, int32_t q, float sig_loc, float cx, float cy, float px,
+                                            float py) {
         // nearly every vertex passed lies far from the eps-wide regions: reject on |sig| first
         if (fabsf(sig_loc) > sbound) return;
         float tau = (Ltot - (w.Lh + w.Ll)) + (cx - px) * w.dx + (cy - py) * w.dy;
         float sig = (w.st & SG_PARITY_BIT) ? -sig_loc : sig_loc;
         if (tau < -tol || tau > Ltot + tol) return;
-        if (sig > -tol && sig - tau * tphi < tol) split |= 1u;
+        unsigned nb = 0u;
+        if (sig > -tol && sig - tau * tphi < tol) nb |= 1u;
         if (ub > 0.f ? (sig > -tol && sig < ub + tol) : (sig < tol && sig > ub - tol)) {
             float s = tau - sig * uq;
-            if (s > -tol && s < Ltot + tol) split |= 2u;
+            if (s > -tol && s < Ltot + tol) nb |= 2u;
         }
         if (vb > 0.f ? (sig > -tol && sig < vb + tol) : (sig < tol && sig > vb - tol)) {
             float s = tau - sig * vq;
-            if (s > -tol && s < Ltot + tol) split |= 4u;
+            if (s > -tol && s < Ltot + tol) nb |= 4u;
         }
+        if (RECORD && nb && !split) {
+            // first swept corner, met on a half-edge: the state on its entry edge
+            const int hp = w.h | ((w.st & SG_PARITY_BIT) ? (1 << 30) : 0);
+            int4 *r = A->rst + 2 * (int64_t)q;
+            r[0] = make_int4(hp, __float_as_int(w.px), __float_as_int(w.dx), __float_as_int(w.dy));
+            *reinterpret_cast<float2 *>(r + 1) = make_float2(w.Lh, w.Ll);
+            nb |= SG_SPLIT_RESTART;
+        }
+        split |= nb;
     }
-    __device__ __forceinline__ void test(const Walker &w, float sig_loc, int k) {
-        test_at(w, sig_loc, corner_x(w.R, k), corner_y(w.R, k), w.px, w.py);
+    __device__ __forceinline__ void test(const Walker &w, int32_t q, float sig_loc, int k) {
+        test_at<false>(w, q, sig_loc, corner_x(w.R, k), corner_y(w.R, k), w.px, w.py);
     }
-    __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode) {
+    __device__ __forceinline__ void on_face(const Walker &w, int32_t q, float s0, float s1, float s2, int mode) {
         if (mode < 3) {
             int a = prv(mode);
-            test(w, sel3(a, s0, s1, s2), a);
+            test(w, q, sel3(a, s0, s1, s2), a);
         } else if (mode < 6) {
             int c = mode - 3;
-            test(w, sel3(nxt(c), s0, s1, s2), nxt(c));
-            test(w, sel3(prv(c), s0, s1, s2), prv(c));
+            test(w, q, sel3(nxt(c), s0, s1, s2), nxt(c));
+            test(w, q, sel3(prv(c), s0, s1, s2), prv(c));
         } else {
-            test(w, s0, 0); test(w, s1, 1); test(w, s2, 2);
+            test(w, q, s0, 0); test(w, q, s1, 1); test(w, q, s2, 2);
         }
     }
 };
@@ -249,9 +270,8 @@ struct StraddleHook {
 // orientation, read from the twin half-edge record that the crossing loads anyway);
 // k_gradv_edges turns them into vertex gradients once.  For coplanar faces N_old + N_new = 0.
 struct GradHook {
-    float2 *eacc;
     float a, bs;        // gbar_i = a d_i + bs * s_i * perp(d_i)
-    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &G) {
+    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &G, float2 *eacc) {
         const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;                // |e| e
         const float il = rsqrtf(fmaf(exr, exr, eyr * eyr));
         const float yx = fmaf(c.Lr, w.dx, c.qx) - c.x0, yy = fmaf(c.Lr, w.dy, c.qy) - c.y0;  // y - A
@@ -273,17 +293,19 @@ struct GradHook {
 
 template <bool GFD, bool GRADV>
 struct RewalkHook {
+    const BwdArgs *A;   // the kernel's arguments (parameter space, not a register)
     StraddleHook S;
     GradHook G;
     bool gradv;
+    int32_t q;          // the query (nq < 2^29, checked at the entry point): one register
     __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode, int) {
-        if (GFD) S.on_face(w, s0, s1, s2, mode);
+        if (GFD) S.on_face(w, q, s0, s1, s2, mode);
     }
     __device__ __forceinline__ void on_apex(const Walker &w, float sC, float cx, float cy, float px, float py) {
-        if (GFD) S.test_at(w, sC, cx, cy, px, py);
+        if (GFD) S.template test_at<true>(w, q, sC, cx, cy, px, py);
     }
     __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &R) {
-        if (GRADV && gradv) G.on_cross(w, c, R);
+        if (GRADV && gradv) G.on_cross(w, c, R, A->eacc);
     }
     __device__ __forceinline__ void on_vertex(const Walker &, int) {}
 };
@@ -294,11 +316,11 @@ struct RewalkJob {
     const BwdArgs *A;
     Walker w;
     RewalkHook<GFD, GRADV> H;
-    int32_t q;          // nq < 2^29 (checked at the entry point): one register
     bool valid;
 
     __device__ __forceinline__ bool init(int64_t t) {
-        q = A->perm ? __ldg(A->perm + t) : (int32_t)t;
+        const int32_t q = H.q = A->perm ? __ldg(A->perm + t) : (int32_t)t;
+        H.A = A;
         const WalkParams &P = A->P;
         Carry<0> cw;
         bool live = walker_init<0>(P, A->in, q, w, cw);
@@ -309,6 +331,7 @@ struct RewalkJob {
         if (GRADV && !H.gradv) w.st |= SG_ST_NO_GRADV;  // the walker never touches this bit
         const float L = w.Lh, d0x = w.dx, d0y = w.dy;
         if (GFD) {
+            H.S.A = A;
             H.S.tphi = A->eps_v / L;
             H.S.Ltot = L;
             H.S.tol = P.tau_near * w.lref * (1.f + H.S.tphi * H.S.tphi);
@@ -326,7 +349,6 @@ struct RewalkJob {
         }
         if (GRADV && H.gradv) {
             EndAdj E = end_adjoint(*A, q, w.foff);
-            H.G.eacc = A->eacc;
             H.G.a = E.a;
             H.G.bs = E.sm * E.b;
             // start face: p0 = sum b_k P_k -> grad x_k += b_k F0 gbar0; tilt term if v has a
@@ -350,6 +372,7 @@ struct RewalkJob {
     }
     __device__ __forceinline__ bool step() { return walker_step<true>(w, A->P, H); }
     __device__ __forceinline__ void finish() {
+        const int32_t q = H.q;
         if (!valid) {
             if (A->out_status) A->out_status[q] = (w.st & ~SG_PARITY_BIT) | (GRADV ? SG_ST_NO_GRADV : 0u);
             return;
@@ -370,9 +393,10 @@ struct RewalkJob {
             // A walk that stopped at the boundary or at MAX_STEPS, or slid along the boundary
             // (hole avoidance), takes literal walks for all perturbed columns; the par column
             // is the chord from p' in every case (Round 2 of the paper's batching).
-            unsigned split = H.S.split;
+            unsigned split = H.S.split & 7u;
             if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) split = 7u;
             A->cols[4 * (int64_t)q] = __uint_as_float(split);  // read by k_bwd_assemble
+            if (split && !(H.S.split & SG_SPLIT_RESTART)) A->rst[2 * (int64_t)q] = make_int4(-1, 0, 0, 0);
             if (split) {
                 st |= SG_ST_GFD_SPLIT;
                 int base = atomicAdd(A->ntask, __popc(split));
@@ -463,6 +487,58 @@ struct LiteralJob {
     int k, phase;
     float L, d0x, d0y, ux, uy;
 
+    // Restart on the entry edge (half-edge h, fraction s, base direction d, remaining length
+    // Lrem) of the face where the base walk met its first swept corner.  Up to there the
+    // perturbed ray ran in the base ray's development, where it is a rigid image of the
+    // perturbed start ray: for e_perp the ray turned by phi (sin phi = eps_v / L', L' = |v +
+    // eps_v e_perp|), for e_u / e_v the ray shifted by delta = a d0 + b perp(d0).  With tau = L
+    // - Lrem the base distance walked and sm the parity, it crosses the entry edge at
+    //   e_perp: x' = x - tau sm sin(phi) / d'_y,  Lrem' = Lrem + (L' - L) - tau (d_y - d'_y) / d'_y
+    //   shift:  x' = x - sm b / d_y,              Lrem' = Lrem + a + sm b d_x / d_y
+    // (no cancellation: every correction is formed from the small quantities themselves).
+    // Returns false when the record says "from the start" or the crossing leaves the edge.
+    __device__ __forceinline__ bool restart(int kk) {
+        const int4 r0 = __ldg(A->rst + 2 * q);
+        if (r0.x < 0) return false;
+        const float2 r1 = __ldg(reinterpret_cast<const float2 *>(A->rst + 2 * q + 1));
+        const int h = r0.x & ((1 << 30) - 1);
+        const float sm = (r0.x & (1 << 30)) ? -1.f : 1.f;
+        const float bdx = __int_as_float(r0.z), bdy = __int_as_float(r0.w);
+        const float Lh0 = r1.x, Ll0 = r1.y;
+        const FaceRec G = load_rec(A->P.half, h);
+        const float l = hl(G), x = __int_as_float(r0.y) * l;
+        float ndx = bdx, ndy = bdy, xp, dl;
+        if (kk == 1) {
+            const float ev = A->eps_v;
+            const float Lp = sqrtf(fmaf(L, L, ev * ev));
+            const float sn = ev / Lp, cs = L / Lp, dL = ev * ev / (Lp + L);
+            const float tau = L - (Lh0 + Ll0);
+            ndx = cs * bdx - sm * sn * bdy;
+            ndy = cs * bdy + sm * sn * bdx;
+            if (!(ndy > 0.f)) return false;
+            xp = x - tau * sm * sn / ndy;
+            dl = dL - tau * (bdy * dL / Lp - sm * sn * bdx) / ndy;
+        } else {
+            const float ex = kk == 2 ? 1.f : w.R.x2x * w.R.il2, ey = kk == 2 ? 0.f : w.R.x2y * w.R.il2;
+            const float a = A->eps_p * (ex * d0x + ey * d0y), b = A->eps_p * (ey * d0x - ex * d0y);
+            if (!(bdy > 0.f)) return false;
+            xp = x - sm * b / bdy;
+            dl = a + sm * b * bdx / bdy;
+        }
+        const float sp = xp / l;
+        if (!(sp >= 0.f && sp <= 1.f)) return false;
+        w.h = h; w.R = G; w.mode = SG_MODE_HALF;
+        w.px = sp; w.py = 0.f; w.dx = ndx; w.dy = ndy;
+        {   // Lh + Ll += dl, compensated
+            const float sum = Lh0 + dl, bb = sum - Lh0;
+            w.Lh = sum;
+            w.Ll = Ll0 + ((Lh0 - (sum - bb)) + (dl - bb));
+        }
+        w.st = sm < 0.f ? SG_PARITY_BIT : 0u;
+        w.steps = 0;
+        return true;
+    }
+
     __device__ __forceinline__ bool init(int64_t t) {
         const int32_t task = A->tasks[t];
         q = task >> 2;
@@ -470,6 +546,10 @@ struct LiteralJob {
         Carry<0> cw;
         walker_init<0>(A->P, A->in, q, w, cw);
         L = w.Lh; d0x = w.dx; d0y = w.dy;
+        if (restart(k)) {
+            phase = 1;
+            return true;
+        }
         if (k == 1) {
             float vx = L * d0x - A->eps_v * d0y, vy = L * d0y + A->eps_v * d0x;
             float Lp = sqrtf(vx * vx + vy * vy);
@@ -704,7 +784,7 @@ unsigned persistent_grid(K kernel, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
 }
 struct BwdLayout {
-    size_t gacc, eacc, cols, tasks, ntask, gpos, lcounts, lkeys, perm, total;
+    size_t gacc, eacc, cols, tasks, rst, ntask, gpos, lcounts, lkeys, perm, total;
 };
 // The re-walk takes its queries longest first (the forward's length order, rebuilt here) for
 // batches of at least this many queries, unless opts.sort is 0.
@@ -728,6 +808,7 @@ BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool
     if (estimator == SG_EST_GFD) {
         L.cols = o; o = align_up(o + sizeof(float) * 4 * (size_t)std::max<int64_t>(nq, 1), 256);
         L.tasks = o; o = align_up(o + sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(nq, 1), 256);
+        L.rst = o; o = align_up(o + sizeof(int4) * 2 * (size_t)std::max<int64_t>(nq, 1), 256);
     }
     L.total = o;
     return L;
@@ -797,7 +878,11 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         A.gacc = (float4 *)(base + Lw.gacc);
         A.eacc = (float2 *)(base + Lw.eacc);
     }
-    if (estimator == SG_EST_GFD) { A.cols = (float *)(base + Lw.cols); A.tasks = (int32_t *)(base + Lw.tasks); }
+    if (estimator == SG_EST_GFD) {
+        A.cols = (float *)(base + Lw.cols);
+        A.tasks = (int32_t *)(base + Lw.tasks);
+        A.rst = (int4 *)(base + Lw.rst);
+    }
     cudaMemsetAsync(A.ntask, 0, 64, s);
     if (lorder) {
         int32_t *perm = (int32_t *)(base + Lw.perm);
