@@ -31,17 +31,27 @@ struct FaceRec {
     float l01, x2x, x2y, il1, il2;
 };
 
-// One 32-byte record = one L2 sector, read as two 16-byte loads.  (A single 256-bit load
-// doubles the device's dependent-gather ceiling, but the walks are bound by instruction issue,
-// not by gathers, and the forward walk ran 5% slower with it.)
+// One 32-byte record = one L2 sector, read as two 16-byte loads or, with W, as one 256-bit
+// load (sm_100 and later).  The wide load halves the L2 requests per record and doubles the
+// device's dependent-gather ceiling, but costs the forward walk, which is bound by instruction
+// issue, 5%; walks whose L2 tag lookups are the limit (the backward re-walk, which also sends
+// one atomic per crossing) use it.
+template <bool W = false>
 __device__ __forceinline__ void ld_rec32(const int4 *__restrict__ p, int4 &a, int4 &b) {
-    a = __ldg(p);
-    b = __ldg(p + 1);
+    if (W) {
+        asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+            : "l"(p));
+    } else {
+        a = __ldg(p);
+        b = __ldg(p + 1);
+    }
 }
 
+template <bool W = false>
 __device__ __forceinline__ FaceRec load_rec(const int4 *__restrict__ rec, int f) {
     int4 a, b;
-    ld_rec32(rec + 2 * f, a, b);
+    ld_rec32<W>(rec + 2 * f, a, b);
     FaceRec r;
     r.n0 = a.x; r.n1 = a.y; r.n2 = a.z;
     r.l01 = __int_as_float(a.w);
@@ -449,6 +459,15 @@ struct Cross {
 };
 
 // Observer of a walk (the backward pass hooks into the same step code as the forward).
+// Whether a walk with this hook reads the half-edge record of each crossing with one 256-bit load.
+#ifndef SG_WIDE_DEFAULT
+#define SG_WIDE_DEFAULT 0
+#endif
+template <class Hook>
+struct WideRecords {
+    static constexpr bool value = SG_WIDE_DEFAULT != 0;
+};
+
 struct NoHook {
     // general step: sigma of the three corners after classification, entry mode, snapped corner
     __device__ __forceinline__ void on_face(const Walker &, float, float, float, int, int) {}
@@ -559,7 +578,7 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     const float ex = x1 - x0, ey = y1 - y0;
     const float da = fmaf(w.dx, ex, w.dy * ey);   // |e| (d . e_hat)
     const float dc = fmaf(w.dx, ey, -w.dy * ex);  // |e| (d . n_out)
-    const FaceRec G = load_rec(P.half, hn);
+    const FaceRec G = load_rec<WideRecords<Hook>::value>(P.half, hn);
     // |(da, dc)| = |e|: one reciprocal square root normalises it (rsqrtf's error, a few 1e-7,
     // does not accumulate: every step renormalises the direction it receives)
     const float re = rsqrtf(fmaf(da, da, dc * dc));
@@ -707,7 +726,7 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
     const float da = fmaf(w.dx, ex, w.dy * ey);
     const float dc = fmaf(w.dx, ey, -w.dy * ex);  // d . (ey, -ex)
     const int hn = 3 * g + kp;
-    const FaceRec G = load_rec(P.half, hn);
+    const FaceRec G = load_rec<WideRecords<Hook>::value>(P.half, hn);
     float ndx = fl ? da : -da, ndy = dc;
     renorm(ndx, ndy);
     hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, 0.f, 0.f, hl(G), 0.f, ndx, ndy,
