@@ -310,16 +310,6 @@ struct RewalkHook {
     __device__ __forceinline__ void on_vertex(const Walker &, int) {}
 };
 
-// the re-walk's L2 tag lookups are near their limit (one atomic per crossing besides the
-// record): one 256-bit load per record halves the record requests
-#ifndef SG_REWALK_WIDE
-#define SG_REWALK_WIDE 1
-#endif
-template <bool GFD, bool GRADV>
-struct WideRecords<RewalkHook<GFD, GRADV>> {
-    static constexpr bool value = SG_REWALK_WIDE != 0;
-};
-
 // ------------------------------------------------------------------ kernel 1: re-walk
 template <bool GFD, bool GRADV>
 struct RewalkJob {
