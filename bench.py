@@ -293,7 +293,8 @@ def run_multimesh(args):
 def run_config(args, index):
     """Forward throughput and accuracy on one of the single-mesh workloads: 0 (icosphere s3, 4096
     queries, 1 carried vector), 1 (torus 262k faces, 4M queries, 2 carried vectors) or 4 (sliver
-    heightfield 4.2M faces, 16M queries; also EP / GFD backward and the FP64 walk).  Variants: the
+    heightfield 4.2M faces, 16M queries; also EP / GFD backward and the FP64 and double-float
+    walks).  Variants: the
     persistent kernel (start-face sort, FP64 classification) and the plain one-thread-per-query
     FP32 kernel; accuracy of each against the FP64 oracle on a sample of 2000 queries."""
     import torch
@@ -343,16 +344,18 @@ def run_config(args, index):
         outs[name] = out
     sub64 = None
     if index == 4:
-        # the full-precision walk on the first 1M queries
+        # the full-precision walks (FP64, double-float) on the first 1M queries
         n64 = min(nq, 1 << 20)
         sub64 = n64
-        o64 = sg.default_opts(precision=64)
-        out = sg.exp_map(mesh, face[:n64], bary[:n64], v[:n64], opts=o64)
-        ws = out.pop("_workspace", None)
-        t = timed(lambda: sg.exp_map(mesh, face[:n64], bary[:n64], v[:n64], opts=o64, workspace=ws, out=out), 3)
-        nc = int(out["ncross"].sum().item())
-        res["fp64"] = {"ms": t, "queries": n64, "geodesics_per_s": n64 / (t * 1e-3), "crossings_per_s": nc / (t * 1e-3)}
-        outs["fp64"] = out
+        for pname, prec in (("fp64", 64), ("double_float", 48)):
+            o64 = sg.default_opts(precision=prec)
+            out = sg.exp_map(mesh, face[:n64], bary[:n64], v[:n64], opts=o64)
+            ws = out.pop("_workspace", None)
+            t = timed(lambda: sg.exp_map(mesh, face[:n64], bary[:n64], v[:n64], opts=o64, workspace=ws, out=out), 3)
+            nc = int(out["ncross"].sum().item())
+            res[pname] = {"ms": t, "queries": n64, "geodesics_per_s": n64 / (t * 1e-3),
+                          "crossings_per_s": nc / (t * 1e-3)}
+            outs[pname] = out
         # backward at full size (EP, GFD) on the persistent forward's outputs
         po = outs["persistent"]
         g = T(q.g_pos)
@@ -370,7 +373,8 @@ def run_config(args, index):
     om = oracle.Mesh(X32.astype(np.float64), F)
     f64 = lambda a: np.asarray(a, np.float32).astype(np.float64)
     acc = {}
-    for name, o_kw in (("persistent", {}), ("plain", {}), ("fp64", {"tau_snap": 1e-12})):
+    for name, o_kw in (("persistent", {}), ("plain", {}), ("fp64", {"tau_snap": 1e-12}),
+                       ("double_float", {"tau_snap": 1e-12})):
         if name not in outs:
             continue
         ref = oracle.exp_map(om, q.face[idx], f64(q.bary[idx]), f64(q.v[idx]),
@@ -403,7 +407,8 @@ def run_features(args):
     entry (CUDA events, L2 flushed between steps, median of the timed steps):
       trace      sg_exp_map_trace on the icosphere-s6 workload (1M queries, 64 path entries)
                  against sg_exp_map on the same queries;
-      fp64       the full-precision walk on the same workload against the FP32 walk;
+      fp64       the full-precision walks (FP64, double-float) on the same workload against the
+                 FP32 walk;
       hole       hole avoidance on the icosphere s6 with 8% of its faces removed (1M queries)
                  against the stopping walk;
       update     sg_mesh_update_vertices on the icosphere s6 (81,920 faces);
@@ -452,6 +457,12 @@ def run_features(args):
     ws64 = out64.pop("_workspace")
     t64 = timed(lambda: sg.exp_map(mesh, face, bary, v, opts=o64, workspace=ws64, out=out64))
     res["fp64"] = {"ms": t64, "geodesics_per_s": nq / (t64 * 1e-3), "vs_fp32": t64 / t_fwd}
+    o48 = sg.default_opts(precision=48)
+    out48 = sg.exp_map(mesh, face, bary, v, opts=o48)
+    ws48 = out48.pop("_workspace")
+    t48 = timed(lambda: sg.exp_map(mesh, face, bary, v, opts=o48, workspace=ws48, out=out48))
+    res["double_float"] = {"ms": t48, "geodesics_per_s": nq / (t48 * 1e-3), "vs_fp32": t48 / t_fwd,
+                           "vs_fp64": t64 / t48}
     # update: positions with fresh radial noise
     rng = np.random.default_rng(5)
     Vn = T(X32 * (1.0 + 0.003 * rng.standard_normal((len(X32), 1))).astype(np.float32))

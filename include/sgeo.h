@@ -84,7 +84,7 @@ typedef struct sg_opts {
     int32_t blocks_per_sm;  /* persistent kernel residency; <= 0: as many as fit */
     int32_t fp64_escalate;  /* 1: re-evaluate near-vertex classification in FP64 (persistent only) */
     float tau_near;         /* flag radius / l_ref for NEAR_VERTEX, NEAR_EDGE and the FP64 band; <= 0: 1e-4 */
-    float tau_snap;         /* vertex-snap radius / l_ref; <= 0: 1e-6 (precision 32), 1e-12 (64) */
+    float tau_snap;         /* vertex-snap radius / l_ref; <= 0: 1e-6 (precision 32), 1e-12 (48, 64) */
     void *workspace;        /* optional device scratch (see sg_exp_map_workspace_size); NULL: the
                                library allocates stream-ordered scratch itself */
     size_t workspace_bytes;
@@ -104,7 +104,14 @@ typedef struct sg_opts {
                                trace, the backward, boundary_mode 1 and the plain kernel reject
                                it with SG_ERR_UNSUPPORTED).  The first FP64 call on a mesh
                                allocates and derives its FP64 geometry (synchronous cudaMalloc,
-                               88 B per face and 8 B per vertex, kept by the mesh). */
+                               88 B per face and 8 B per vertex, kept by the mesh);
+                               48: the double-float walk, the same accuracy class as 64 on the
+                               FP32 pipes: every crossing in double-float arithmetic (each value
+                               an unevaluated sum of two FP32 numbers, about 48 significant
+                               bits; one 32-byte record per crossing), the rare events (start,
+                               vertex hits, boundary, end) in FP64; the same restrictions as 64,
+                               and its first call on a mesh also allocates 96 B per face of
+                               double-float records. */
 } sg_opts;
 
 /* Fills `o` with the defaults described above. */
@@ -296,7 +303,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
  *                               tangent planes for a fixed face sequence; exact)
  *   out_status uint32 [nq]      SG_ST_* of the extra walks (GFD) or of the re-walk
  * Asynchronous on `stream`.  Errors: SG_ERR_INVALID_ARG (bad estimator, eps <= 0 for GFD, a
- * required array NULL, nq above 536,869,887), SG_ERR_UNSUPPORTED (precision 64), SG_ERR_OOM
+ * required array NULL, nq above 536,869,887), SG_ERR_UNSUPPORTED (precision 48 or 64), SG_ERR_OOM
  * (no workspace given and none could be allocated), SG_ERR_CUDA.
  */
 sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, float eps_p,
@@ -326,7 +333,7 @@ sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, 
  *             tangent to the start face.  Zero for invalid queries; for a zero vector v the
  *             path is empty and out_u is u projected onto the start face.
  * Asynchronous on `stream`; no scratch.  Errors: SG_ERR_INVALID_ARG (NULL array, n_u out of
- * range), SG_ERR_UNSUPPORTED (opts->precision == 64), SG_ERR_CUDA.
+ * range), SG_ERR_UNSUPPORTED (opts->precision 48 or 64), SG_ERR_CUDA.
  */
 sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
                             const float *bary, const float *v, const int32_t *end_face,

@@ -513,7 +513,7 @@ sg_opts resolve(const sg_opts *o, int64_t nq, int64_t nF) {
     if (r.block <= 0) r.block = 256;
     if (r.precision <= 0) r.precision = 32;
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
-    if (r.tau_snap <= 0.f) r.tau_snap = r.precision == 64 ? 1e-12f : 1e-6f;
+    if (r.tau_snap <= 0.f) r.tau_snap = r.precision >= 48 ? 1e-12f : 1e-6f;
     if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
     if (r.sort < 0)
         r.sort = nq < SG_SORT_MIN_BATCH ? 0 : (128 * nF > (int64_t)l2_bytes() / 2 ? 1 : 2);
@@ -700,6 +700,7 @@ sg_status sg_mesh_destroy(sg_mesh *m) {
     cudaFree(m->d_rec64);
     cudaFree(m->d_frm64);
     cudaFree(m->d_th64);
+    cudaFree(m->d_half48);
     delete m;
     return SG_OK;
 }
@@ -824,8 +825,8 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode && r.kernel == SG_KERNEL_PLAIN) return SG_ERR_UNSUPPORTED;
-    if (r.precision != 32 && r.precision != 64) return SG_ERR_INVALID_ARG;
-    if (r.precision == 64 && (r.boundary_mode || r.kernel == SG_KERNEL_PLAIN)) return SG_ERR_UNSUPPORTED;
+    if (r.precision != 32 && r.precision != 48 && r.precision != 64) return SG_ERR_INVALID_ARG;
+    if (r.precision >= 48 && (r.boundary_mode || r.kernel == SG_KERNEL_PLAIN)) return SG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a = fwd_args(m, nq, mesh_id, face, bary, v, length, w, r);
     a.P.want_hash = out_hash != nullptr;
@@ -841,9 +842,10 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
             return st;
         }
     }
-    if (r.precision == 64) {
-        // the FP64 geometry is a lazily built cache of the mesh (hence the const_cast)
-        sg_status st = sg_geom64_prepare(const_cast<sg_mesh *>(m), s);
+    if (r.precision >= 48) {
+        // the FP64 geometry (and the double-float records) are a lazily built cache of the mesh
+        // (hence the const_cast)
+        sg_status st = sg_geom64_prepare(const_cast<sg_mesh *>(m), s, r.precision == 48);
         if (st != SG_OK) {
             if (own_ws) cudaFreeAsync(own_ws, s);
             return st;
@@ -888,7 +890,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
         return SG_ERR_INVALID_ARG;
     if (path_cap > 0 && !out_path_face) return SG_ERR_INVALID_ARG;
     sg_opts r = resolve(o, nq, m->nF);
-    if (r.boundary_mode || r.precision == 64) return SG_ERR_UNSUPPORTED;
+    if (r.boundary_mode || r.precision >= 48) return SG_ERR_UNSUPPORTED;
     if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

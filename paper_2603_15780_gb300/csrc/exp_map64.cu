@@ -10,6 +10,13 @@
 //
 // The FP64 geometry is derived on the device from the mesh's vertex positions (converted to
 // FP64) the first time a call asks for it, and again after sg_mesh_update_vertices.
+//
+// The double-float walk (sg_opts.precision = 48) reaches the same accuracy class on the FP32
+// pipes: its hot step is the FP32 walk's half-edge step (one 32-byte record per crossing, in the
+// entry edge's frame) with every quantity an unevaluated sum hi + lo of two FP32 numbers, about
+// 48 significant bits.  GB300 runs FP64 at a small fraction of its FP32 rate, so the double-float
+// step, several times the FP32 step's instructions, is still far faster than the FP64 step.  Rare
+// events (the start, vertex hits, the boundary, the end) use the FP64 face-frame code below.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +33,7 @@ struct R64 {
 
 struct P64 {
     const int4 *__restrict__ rec;     // FP32 records: neighbour links
+    const int4 *__restrict__ half48;  // [3 nF][2] double-float half-edge records (precision 48)
     const double *__restrict__ rec64; // [nF][6] l01, x2x, x2y, 1/l12, 1/l20, -
     const double *__restrict__ frm64; // [nF][6] e1, e2
     const double *__restrict__ th64;  // [nV] theta, negated on the boundary
@@ -47,11 +55,16 @@ __device__ __forceinline__ int nb64(const R64 &r, int k) { return sel3(k, r.n0, 
 __device__ __forceinline__ double cx64(const R64 &r, int k) { return sel3(k, 0.0, r.l01, r.x2x); }
 __device__ __forceinline__ double cy64(const R64 &r, int k) { return sel3(k, 0.0, 0.0, r.x2y); }
 
+// Walker state.  In the double-float half-edge mode (mode SG48_HALF) the FP64 registers hold
+// double-float pairs instead (dpack): f = the half-edge id h, px = the fraction s along the entry
+// edge, (dx, dy) = the direction in the edge frame, L = the remaining length, and R = the
+// half-edge record (l01 = l, x2x = cx, x2y = cy, n0 = linkR, n1 = linkL).
 struct W64 {
     int f, foff, mode, steps, ncross;
     uint32_t st;
     uint64_t hash;
     double px, py, dx, dy, L, lref;
+    float nearf, snapf;  // tau_near l_ref, tau_snap l_ref (double-float mode)
     R64 R;
 };
 
@@ -246,6 +259,220 @@ __device__ bool step64(W64 &w, const P64 &P) {
     return false;
 }
 
+// ------------------------------------------------------------------ double-float walk
+// Error-free transformations: Knuth's two-sum (TAOCP vol. 2, sec. 4.2.2), Dekker's fast two-sum
+// (Dekker 1971, |a| >= |b|) and the exact product by one fused multiply-add.  Built on them, the
+// double-float sum, product and quotient keep about 2^-46 relative error.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = a * b;
+    return DF{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+// the sum with both parts summed exactly: accurate under cancellation (c - x near a vertex)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    const DF t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    DF p = two_prod(a.hi, b.hi);
+    p.lo = fmaf(a.hi, b.lo, p.lo);
+    p.lo = fmaf(a.lo, b.hi, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+// quotient by long division: two FP32 quotient digits, each from the exact remainder
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = a.hi / b.hi;
+    const DF r = df_sub(a, df_mul(b, DF{q1, 0.f}));
+    const float q2 = r.hi / b.hi;
+    const DF r2 = df_sub(r, df_mul(b, DF{q2, 0.f}));
+    const float q3 = r2.hi / b.hi;
+    const DF q = fast_two_sum(q1, q2);
+    return df_add(q, DF{q3, 0.f});
+}
+// 1/sqrt(n): the FP32 estimate refined by one Newton step r + r (1 - n r^2) / 2, which squares
+// its relative error
+__device__ __forceinline__ DF df_rsqrt(DF n) {
+    const float r = rsqrtf(n.hi);
+    const DF e = df_sub(DF{1.f, 0.f}, df_mul(n, two_prod(r, r)));
+    return fast_two_sum(r, 0.5f * r * e.hi);
+}
+__device__ __forceinline__ DF df_from(double x) {
+    const float hi = (float)x;
+    return DF{hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ bool df_ge(DF a, DF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+// a double-float pair in one double register pair (the low word holds hi), so the half-edge mode
+// reuses the FP64 state's registers
+__device__ __forceinline__ double dpack(DF a) { return __hiloint2double(__float_as_int(a.lo), __float_as_int(a.hi)); }
+__device__ __forceinline__ DF dunpack(double d) {
+    return DF{__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d))};
+}
+
+#define SG48_HALF 7
+
+// the double-float half-edge record h into R: one 32-byte sector, one 256-bit load
+__device__ __forceinline__ void load48(R64 &R, const P64 &P, int h) {
+    int4 a, b;
+    ld_rec32<true>(P.half48 + 2 * h, a, b);
+    R.l01 = dpack(DF{__int_as_float(a.x), __int_as_float(a.y)});
+    R.x2x = dpack(DF{__int_as_float(a.z), __int_as_float(a.w)});
+    R.x2y = dpack(DF{__int_as_float(b.x), __int_as_float(b.y)});
+    R.n0 = b.z;
+    R.n1 = b.w;
+}
+
+// Leave the half-edge mode: the point (xe, ye) and direction (ex, ey) of the edge frame of w.f
+// (a half-edge id) into the FP64 face frame of its face.
+__device__ __forceinline__ void leave48(W64 &w, const P64 &P, DF xe, DF ye, DF ex, DF ey) {
+    const int h = w.f, f = h / 3, k = h - 3 * f;
+    const R64 F = load64(P, f);
+    double ca = 1.0, sa = 0.0;
+    if (k == 1) { ca = (F.x2x - F.l01) * F.il1; sa = F.x2y * F.il1; }
+    else if (k == 2) { ca = -F.x2x * F.il2; sa = -F.x2y * F.il2; }
+    const double x = df_to(xe), y = df_to(ye), dx = df_to(ex), dy = df_to(ey);
+    w.px = cx64(F, k) + ca * x - sa * y;
+    w.py = cy64(F, k) + sa * x + ca * y;
+    w.dx = ca * dx - sa * dy;
+    w.dy = sa * dx + ca * dy;
+    w.f = f;
+    w.R = F;
+    w.mode = 6;
+}
+
+// Enter the half-edge mode after a face-frame step crossed into w.f through its local edge
+// w.mode: the position as a fraction along that edge, the direction in the edge's frame.
+__device__ __forceinline__ void enter48(W64 &w, const P64 &P) {
+    const int k = w.mode;
+    const R64 &G = w.R;
+    const double ax = cx64(G, k), ay = cy64(G, k);
+    const double ex = cx64(G, nxt(k)) - ax, ey = cy64(G, nxt(k)) - ay;
+    const double l2 = ex * ex + ey * ey, il = 1.0 / sqrt(l2);
+    const double s = fmin(fmax(((w.px - ax) * ex + (w.py - ay) * ey) / l2, 0.0), 1.0);
+    const double hx = (w.dx * ex + w.dy * ey) * il, hy = (ex * w.dy - ey * w.dx) * il;
+    const int h = 3 * w.f + k;
+    load48(w.R, P, h);
+    w.f = h;
+    w.px = dpack(df_from(s));
+    w.dx = dpack(df_from(hx));
+    w.dy = dpack(df_from(hy));
+    w.L = dpack(df_from(w.L));
+    w.mode = SG48_HALF;
+}
+
+// One crossing in double-float arithmetic: the FP32 walk's half-edge step (orientation tests
+// sigma_A = dy x, sigma_B = -dy (l - x), sigma_C = dx cy - dy (cx - x); exit B -> C when the apex
+// lies left of the ray, else C -> A; the twin's frame has the crossed edge as its x axis).
+template <int NW>
+__device__ bool half48(W64 &w, const P64 &P) {
+    const DF zero{0.f, 0.f}, one{1.f, 0.f};
+    const DF L0 = dunpack(w.R.l01), cx = dunpack(w.R.x2x), cy = dunpack(w.R.x2y);
+    const DF px = dunpack(w.px), dx = dunpack(w.dx), dy = dunpack(w.dy), Lr = dunpack(w.L);
+    const DF x = df_mul(px, L0);
+    const DF sA = df_mul(dy, x);
+    const DF sB = df_neg(df_mul(dy, df_sub(L0, x)));
+    const DF sC = df_sub(df_mul(dx, cy), df_mul(dy, df_sub(cx, x)));
+    const float aC = fabsf(sC.hi);
+    const bool hit = aC <= w.snapf;
+    if (!hit && aC < w.nearf) w.st |= SG_ST_NEAR_VERTEX;
+    const bool right = sC.hi > 0.f;
+    const DF x0 = right ? L0 : cx, y0 = right ? zero : cy;
+    const DF x1 = right ? cx : zero, y1 = right ? cy : zero;
+    DF qx, qy, s;
+    if (hit) {
+        qx = cx; qy = cy;
+        s = right ? one : zero;
+    } else {
+        const DF s0 = right ? sB : sC, s1 = right ? sC : sA;
+        const DF den = df_sub(s0, s1);
+        s = den.hi != 0.f ? df_div(s0, den) : DF{0.5f, 0.f};
+        if (s.hi < 0.f) s = zero;
+        if (df_ge(s, one)) s = one;
+        qx = df_add(x0, df_mul(s, df_sub(x1, x0)));
+        qy = df_add(y0, df_mul(s, df_sub(y1, y0)));
+    }
+    DF t = df_add(df_mul(df_sub(qx, x), dx), df_mul(qy, dy));
+    if (t.hi < 0.f) t = zero;
+    const int k = w.f - 3 * (w.f / 3);
+    if (df_ge(t, Lr)) {
+        // final truncated in-face segment
+        leave48(w, P, df_add(x, df_mul(Lr, dx)), df_mul(Lr, dy), dx, dy);
+        w.L = 0.0;
+        const R64 &R = w.R;
+        const double near = P.tau_near * w.lref;
+        const double d0 = fabs(w.py);
+        const double d1 = fabs((R.x2x - R.l01) * w.py - R.x2y * (w.px - R.l01)) * R.il1;
+        const double d2 = fabs(R.x2x * w.py - R.x2y * w.px) * R.il2;
+        if (fmin(fmin(d0, d1), d2) <= near) w.st |= SG_ST_NEAR_EDGE;
+        return true;
+    }
+    const DF Ln = df_sub(Lr, t);
+    if (hit) {  // the apex is corner k+2 of the face: the straightest rule in FP64
+        leave48(w, P, cx, cy, dx, dy);
+        w.L = df_to(Ln);
+        return !vertex64<NW>(w, prv(k), P);
+    }
+    const int link = right ? w.R.n0 : w.R.n1;
+    if (link < 0) {  // boundary edge: the walk stops (Sec. 4)
+        leave48(w, P, qx, qy, dx, dy);
+        w.L = df_to(Ln);
+        w.st |= SG_ST_BOUNDARY;
+        return true;
+    }
+    const int hn = link >> 1, fl = link & 1;
+    const DF ex = df_sub(x1, x0), ey = df_sub(y1, y0);
+    const DF da = df_add(df_mul(dx, ex), df_mul(dy, ey));   // |e| (d . e_hat)
+    const DF dc = df_sub(df_mul(dx, ey), df_mul(dy, ex));   // |e| (d . n_out)
+    const DF re = df_rsqrt(df_add(df_mul(da, da), df_mul(dc, dc)));
+    const DF ndx = df_mul(fl ? da : df_neg(da), re), ndy = df_mul(dc, re);
+    w.px = dpack(fl ? s : df_sub(one, s));
+    w.dx = dpack(ndx);
+    w.dy = dpack(ndy);
+    w.L = dpack(Ln);
+    load48(w.R, P, hn);
+    w.f = hn;
+    if (fl) w.st ^= SG_PARITY_BIT;
+    w.ncross++;
+    hash64(w, hn / 3, P.want_hash);
+    return false;
+}
+
+// One step of the double-float walk: the half-edge step, or the FP64 face-frame step (start,
+// after a vertex transport), whose crossings enter the half-edge mode.
+template <int NW>
+__device__ __forceinline__ bool step48(W64 &w, const P64 &P) {
+    if (w.mode == SG48_HALF) {
+        if (w.steps >= P.max_steps) {
+            const DF px = dunpack(w.px), L0 = dunpack(w.R.l01);
+            leave48(w, P, df_mul(px, L0), DF{0.f, 0.f}, dunpack(w.dx), dunpack(w.dy));
+            w.L = 0.0;
+            w.st |= SG_ST_MAX_STEPS;
+            return true;
+        }
+        w.steps++;
+        return half48<NW>(w, P);
+    }
+    const bool done = step64<NW>(w, P);
+    if (!done && w.mode < 3) enter48(w, P);
+    return done;
+}
+
 struct Fwd64Args {
     P64 P;
     QueryIn in;
@@ -259,7 +486,7 @@ struct Fwd64Args {
     int32_t *counter;
 };
 
-template <int NW>
+template <int NW, bool DFW = false>
 struct Job64 {
     const Fwd64Args *a;
     W64 w;
@@ -324,9 +551,11 @@ struct Job64 {
             w.mode = 3 + c;
         }
         if (L > 0.0) hash64(w, w.f, P.want_hash);
+        w.nearf = (float)(P.tau_near * w.lref);
+        w.snapf = (float)(P.tau_snap * w.lref);
         return L > 0.0;
     }
-    __device__ __forceinline__ bool step() { return step64<NW>(w, a->P); }
+    __device__ __forceinline__ bool step() { return DFW ? step48<NW>(w, a->P) : step64<NW>(w, a->P); }
     __device__ __forceinline__ void finish() {
         const Fwd64Args &A = *a;
         const R64 &R = w.R;
@@ -366,6 +595,32 @@ __global__ void __launch_bounds__(128) k_walk64(Fwd64Args a) {
     Job64<NW> job;
     job.a = &a;
     run_persistent(a.counter, a.nq, job);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(128) k_walk48(Fwd64Args a) {
+    Job64<NW, true> job;
+    job.a = &a;
+    run_persistent(a.counter, a.nq, job);
+}
+
+// Double-float half-edge records from the FP64 face shapes, in the layout of the FP32 half-edge
+// records (origin at corner k, x along edge k, the face on +y): {l, cx} and {cy, linkR, linkL},
+// each value split into hi + lo; the links are those of the FP32 records.
+__global__ void k_half48(int64_t nH, const int4 *__restrict__ half, const double *__restrict__ rec64, int4 *half48) {
+    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= nH) return;
+    const int64_t f = h / 3;
+    const int k = (int)(h - 3 * f), k1 = nxt(k), k2 = prv(k);
+    const double *r = rec64 + 6 * f;
+    const double Px[3] = {0.0, r[0], r[1]}, Py[3] = {0.0, 0.0, r[2]};
+    const double ex = Px[k1] - Px[k], ey = Py[k1] - Py[k];
+    const double l = sqrt(ex * ex + ey * ey);
+    const double rx = Px[k2] - Px[k], ry = Py[k2] - Py[k];
+    const double cx = (rx * ex + ry * ey) / l, cy = (ex * ry - ey * rx) / l;
+    const DF L = df_from(l), X = df_from(cx), Y = df_from(cy);
+    half48[2 * h] = make_int4(__float_as_int(L.hi), __float_as_int(L.lo), __float_as_int(X.hi), __float_as_int(X.lo));
+    half48[2 * h + 1] = make_int4(__float_as_int(Y.hi), __float_as_int(Y.lo), half[2 * h].w, half[2 * h + 1].x);
 }
 
 // FP64 geometry from the FP32 vertex positions (converted exactly), the same expressions as
@@ -418,8 +673,9 @@ __global__ void k_geom64_sign(int64_t nV, const float4 *__restrict__ V, double *
 
 }  // namespace
 
-// Builds (first use) or refreshes (after a vertex update) the FP64 geometry, on `s`.
-sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s) {
+// Builds (first use) or refreshes (after a vertex update) the FP64 geometry, on `s`; with
+// half48 also the double-float half-edge records of the double-float walk.
+sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s, bool half48) {
     if (!m->d_rec64) {
         const size_t b0 = sizeof(double) * 6 * (size_t)m->nF, b1 = b0, b2 = sizeof(double) * (size_t)m->nV;
         if (cudaMalloc((void **)&m->d_rec64, b0) != cudaSuccess || cudaMalloc((void **)&m->d_frm64, b1) != cudaSuccess ||
@@ -439,6 +695,25 @@ sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s) {
         k_geom64_sign<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, m->d_V, m->d_th64);
         if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
         m->geom64_stale = false;
+        m->half48_stale = true;
+    }
+    if (half48) {
+        if (!m->d_half48) {
+            const size_t b = sizeof(int4) * 6 * (size_t)m->nF;
+            if (cudaMalloc((void **)&m->d_half48, b) != cudaSuccess) {
+                cudaGetLastError();
+                m->d_half48 = nullptr;
+                return SG_ERR_OOM;
+            }
+            m->device_bytes += (int64_t)b;
+            m->half48_stale = true;
+        }
+        if (m->half48_stale) {
+            const int64_t nH = 3 * m->nF;
+            k_half48<<<(unsigned)((nH + 255) / 256), 256, 0, s>>>(nH, m->d_half, m->d_rec64, m->d_half48);
+            if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
+            m->half48_stale = false;
+        }
     }
     return SG_OK;
 }
@@ -446,6 +721,7 @@ sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s) {
 cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const sg_opts &r, cudaStream_t s) {
     Fwd64Args a{};
     a.P.rec = m->d_rec; a.P.rec64 = m->d_rec64; a.P.frm64 = m->d_frm64; a.P.th64 = m->d_th64;
+    a.P.half48 = m->d_half48;
     a.P.fv = m->d_fv; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
     a.P.max_steps = r.max_steps; a.P.want_hash = io.out_hash != nullptr;
     a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
@@ -465,12 +741,22 @@ cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const
         const int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>((io.nq + 127) / 128, 1));
         kern<<<(unsigned)grid, 128, 0, s>>>(a);
     };
-    switch (n_w) {
-        case 0: go(k_walk64<0>); break;
-        case 1: go(k_walk64<1>); break;
-        case 2: go(k_walk64<2>); break;
-        case 3: go(k_walk64<3>); break;
-        default: go(k_walk64<4>); break;
+    if (r.precision == 48) {
+        switch (n_w) {
+            case 0: go(k_walk48<0>); break;
+            case 1: go(k_walk48<1>); break;
+            case 2: go(k_walk48<2>); break;
+            case 3: go(k_walk48<3>); break;
+            default: go(k_walk48<4>); break;
+        }
+    } else {
+        switch (n_w) {
+            case 0: go(k_walk64<0>); break;
+            case 1: go(k_walk64<1>); break;
+            case 2: go(k_walk64<2>); break;
+            case 3: go(k_walk64<3>); break;
+            default: go(k_walk64<4>); break;
+        }
     }
     return cudaGetLastError();
 }

@@ -166,5 +166,6 @@ extern "C" sg_status sg_mesh_update_vertices(sg_mesh *m, const float *V, void *s
     if (cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
     m->updated = true;
     m->geom64_stale = true;
+    m->half48_stale = true;
     return SG_OK;
 }

@@ -69,6 +69,11 @@ struct sg_mesh {
     double *d_frm64 = nullptr;
     double *d_th64 = nullptr;
     bool geom64_stale = true;
+    // double-float half-edge records of the double-float walk, int4[6*nF]: {l, cx} and {cy,
+    // linkR, linkL} of each half-edge with every length split into two FP32 words hi + lo
+    // (built from the FP64 geometry by the walk's first call, refreshed after an update)
+    int4 *d_half48 = nullptr;
+    bool half48_stale = true;
 };
 
 // host-side builder (mesh_build.cpp); fills the host arrays, returns SG_OK or an error

@@ -748,7 +748,7 @@ struct QueryIn {
     const float *__restrict__ w;
 };
 
-// Inputs and outputs of one forward call, handed to the full-precision walk (exp_map64.cu).
+// Inputs and outputs of one forward call, handed to the FP64 and double-float walks (exp_map64.cu).
 struct SgFwdIO {
     QueryIn in;
     int64_t nq;
@@ -760,7 +760,7 @@ struct SgFwdIO {
     const int32_t *perm;
     int32_t *counter;
 };
-sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s);
+sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s, bool half48);
 // Length order of a batch (exp_map.cu): perm[0 .. nq) = the queries longest walk first, in
 // buckets of an eighth of an octave of L / l_ref.  Scratch: keys (nq bytes), counts (512 int32).
 #define SG_LBUCKETS 256

@@ -32,10 +32,11 @@ def _bad_batch():
     return X, F, q, np.arange(7)
 
 
-VARIANTS = [dict(), dict(kernel=1), dict(sort=0), dict(sort=2), dict(boundary_mode=1), dict(precision=64)]
+VARIANTS = [dict(), dict(kernel=1), dict(sort=0), dict(sort=2), dict(boundary_mode=1), dict(precision=64),
+            dict(precision=48)]
 
 
-@pytest.mark.parametrize("kw", VARIANTS, ids=["persistent", "plain", "unsorted", "length-order", "hole", "fp64"])
+@pytest.mark.parametrize("kw", VARIANTS, ids=["persistent", "plain", "unsorted", "length-order", "hole", "fp64", "double-float"])
 def test_bad_queries_are_invalid_and_the_rest_walk(kw):
     X, F, q, bad = _bad_batch()
     X32 = parity.as_f32(X)
