@@ -289,21 +289,30 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+// the sum of two terms of equal sign (no cancellation): one two-sum of the high parts suffices
+__device__ __forceinline__ DF df_add_same_sign(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ DF df_mul(DF a, DF b) {
     DF p = two_prod(a.hi, b.hi);
     p.lo = fmaf(a.hi, b.lo, p.lo);
     p.lo = fmaf(a.lo, b.hi, p.lo);
     return fast_two_sum(p.hi, p.lo);
 }
-// quotient by long division: two FP32 quotient digits, each from the exact remainder
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    DF p = two_prod(a.hi, b);
+    p.lo = fmaf(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+// quotient by long division: two FP32 quotient digits (the second from the remainder, formed
+// in double-float) with one correctly rounded reciprocal of the divisor's high part
 __device__ __forceinline__ DF df_div(DF a, DF b) {
-    const float q1 = a.hi / b.hi;
-    const DF r = df_sub(a, df_mul(b, DF{q1, 0.f}));
-    const float q2 = r.hi / b.hi;
-    const DF r2 = df_sub(r, df_mul(b, DF{q2, 0.f}));
-    const float q3 = r2.hi / b.hi;
-    const DF q = fast_two_sum(q1, q2);
-    return df_add(q, DF{q3, 0.f});
+    const float rb = __frcp_rn(b.hi);
+    const float q1 = a.hi * rb;
+    const DF r = df_sub(a, df_mul_f(b, q1));
+    return fast_two_sum(q1, r.hi * rb);
 }
 // 1/sqrt(n): the FP32 estimate refined by one Newton step r + r (1 - n r^2) / 2, which squares
 // its relative error
@@ -392,20 +401,22 @@ __device__ bool half48(W64 &w, const P64 &P) {
     const bool hit = aC <= w.snapf;
     if (!hit && aC < w.nearf) w.st |= SG_ST_NEAR_VERTEX;
     const bool right = sC.hi > 0.f;
+    // exit edge (x0, y0) -> (x0, y0) + (ex, ey): B -> C or C -> A
     const DF x0 = right ? L0 : cx, y0 = right ? zero : cy;
-    const DF x1 = right ? cx : zero, y1 = right ? cy : zero;
+    const DF ex = right ? df_sub(cx, L0) : df_neg(cx), ey = right ? cy : df_neg(cy);
     DF qx, qy, s;
     if (hit) {
         qx = cx; qy = cy;
         s = right ? one : zero;
     } else {
+        // s0 and s1 have opposite signs: their difference does not cancel
         const DF s0 = right ? sB : sC, s1 = right ? sC : sA;
-        const DF den = df_sub(s0, s1);
+        const DF den = df_add_same_sign(s0, df_neg(s1));
         s = den.hi != 0.f ? df_div(s0, den) : DF{0.5f, 0.f};
         if (s.hi < 0.f) s = zero;
         if (df_ge(s, one)) s = one;
-        qx = df_add(x0, df_mul(s, df_sub(x1, x0)));
-        qy = df_add(y0, df_mul(s, df_sub(y1, y0)));
+        qx = df_add(x0, df_mul(s, ex));
+        qy = df_add(y0, df_mul(s, ey));
     }
     DF t = df_add(df_mul(df_sub(qx, x), dx), df_mul(qy, dy));
     if (t.hi < 0.f) t = zero;
@@ -436,10 +447,9 @@ __device__ bool half48(W64 &w, const P64 &P) {
         return true;
     }
     const int hn = link >> 1, fl = link & 1;
-    const DF ex = df_sub(x1, x0), ey = df_sub(y1, y0);
     const DF da = df_add(df_mul(dx, ex), df_mul(dy, ey));   // |e| (d . e_hat)
     const DF dc = df_sub(df_mul(dx, ey), df_mul(dy, ex));   // |e| (d . n_out)
-    const DF re = df_rsqrt(df_add(df_mul(da, da), df_mul(dc, dc)));
+    const DF re = df_rsqrt(df_add_same_sign(df_mul(da, da), df_mul(dc, dc)));
     const DF ndx = df_mul(fl ? da : df_neg(da), re), ndy = df_mul(dc, re);
     w.px = dpack(fl ? s : df_sub(one, s));
     w.dx = dpack(ndx);
@@ -597,8 +607,13 @@ __global__ void __launch_bounds__(128) k_walk64(Fwd64Args a) {
     run_persistent(a.counter, a.nq, job);
 }
 
+// resident blocks per SM the double-float walk is compiled for (icosphere s6, 1M queries: 4
+// blocks 4.95 ms, 5 blocks 4.59 ms with a few spills, 3 blocks 4.95 ms)
+#ifndef SG_WALK48_MINB
+#define SG_WALK48_MINB 5
+#endif
 template <int NW>
-__global__ void __launch_bounds__(128) k_walk48(Fwd64Args a) {
+__global__ void __launch_bounds__(128, SG_WALK48_MINB) k_walk48(Fwd64Args a) {
     Job64<NW, true> job;
     job.a = &a;
     run_persistent(a.counter, a.nq, job);
