@@ -70,7 +70,11 @@ typedef enum sg_status {
 
 typedef struct sg_opts {
     int32_t max_steps;      /* loop cap per query (Alg. gpu_parallel MAX_STEPS); <= 0: 1<<20 */
-    int32_t kernel;         /* SG_KERNEL_*; AUTO = persistent */
+    int32_t kernel;         /* SG_KERNEL_*; AUTO: the persistent kernel, except that sg_exp_map
+                               walks a batch of fewer than 65,536 queries taken in input order
+                               (FP32 precision, boundary_mode 0) one thread per query with the
+                               persistent kernel's arithmetic (FP64 classification kept): such a
+                               batch fills the persistent grid once, so the queue gains nothing */
     int32_t sort;           /* order in which the persistent kernels take the queries:
                                0: input order; 1: by (mesh, start face); 2: by walk length,
                                longest first (L or |v| over l_ref, an eighth of an octave per

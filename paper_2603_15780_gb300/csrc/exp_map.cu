@@ -77,14 +77,14 @@ __device__ void walker_finish(const FwdArgs &a, int64_t q, const Walker &w, cons
     if (a.out_hash) a.out_hash[q] = w.hash;
 }
 
-template <int NW>
+template <int NW, bool ESC = false>
 __global__ void __launch_bounds__(256) k_walk_plain(FwdArgs a) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.nq) return;
     Walker w;
     Carry<NW> cw;
     if (walker_init<NW>(a.P, a.in, q, w, cw)) {
-        while (!walker_step<false>(w, a.P)) {
+        while (!walker_step<ESC>(w, a.P)) {
         }
     }
     walker_finish<NW>(a, q, w, cw);
@@ -493,6 +493,8 @@ WsLayout ws_layout(int64_t nF, int64_t nq, int sort) {
 // stay in L2 are gathered as fast in any order (icosphere s6 and torus walks are as fast or
 // faster without the start-face order), but lanes holding walks of similar length idle less.
 #define SG_SORT_MIN_BATCH 65536
+// below this many queries the automatic kernel choice walks one thread per query
+#define SG_SMALL_BATCH 65536
 
 int l2_bytes() {
     static int cached = -1;
@@ -525,7 +527,8 @@ template <int NW>
 cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
     if (o.kernel == SG_KERNEL_PLAIN) {
         int64_t grid = (a.nq + o.block - 1) / o.block;
-        k_walk_plain<NW><<<(unsigned)grid, o.block, 0, s>>>(a);
+        if (o.fp64_escalate) k_walk_plain<NW, true><<<(unsigned)grid, o.block, 0, s>>>(a);
+        else k_walk_plain<NW, false><<<(unsigned)grid, o.block, 0, s>>>(a);
         return cudaGetLastError();
     }
     int dev = 0, sms = 0, per = o.blocks_per_sm;
@@ -819,11 +822,17 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (nq > (int64_t)INT32_MAX - 1024) return SG_ERR_INVALID_ARG;
     if (!face || !bary || !v || !out_face || !out_bary || !out_pos || !out_dir || !out_status) return SG_ERR_INVALID_ARG;
     if (n_w > 0 && !w) return SG_ERR_INVALID_ARG;
+    const bool auto_kernel = !o || o->kernel == SG_KERNEL_AUTO;
     sg_opts r = resolve(o, nq, m->nF);
     if (r.kernel != SG_KERNEL_PLAIN && r.kernel != SG_KERNEL_PERSISTENT) return SG_ERR_INVALID_ARG;
     if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
+    // A small batch fills the persistent grid once, so no lane would take a second query: the
+    // automatic choice walks it one thread per query with the persistent kernel's arithmetic
+    // (FP64 classification kept), without the queue and its counter reset.
+    if (auto_kernel && nq < SG_SMALL_BATCH && r.precision == 32 && r.boundary_mode == 0 && r.sort == 0)
+        r.kernel = SG_KERNEL_PLAIN;
     if (r.boundary_mode && r.kernel == SG_KERNEL_PLAIN) return SG_ERR_UNSUPPORTED;
     if (r.precision != 32 && r.precision != 48 && r.precision != 64) return SG_ERR_INVALID_ARG;
     if (r.precision >= 48 && (r.boundary_mode || r.kernel == SG_KERNEL_PLAIN)) return SG_ERR_UNSUPPORTED;
