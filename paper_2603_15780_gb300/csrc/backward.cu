@@ -575,12 +575,10 @@ struct LiteralJob {
         return false;
     }
     __device__ __forceinline__ void finish() {
-        Carry<0> cw;
-        Walker w0;
-        walker_init<0>(A->P, A->in, q, w0, cw);
-        EndAdj E = end_adjoint(*A, q, w0.foff);
+        // the forward's end state (the task's own walker supplies the per-query fields)
+        EndAdj E = end_adjoint(*A, q, w.foff);
         Walker we;
-        end_walker(*A, q, w0, E, we);
+        end_walker(*A, q, w, E, we);
         const float eps = k == 1 ? A->eps_v : A->eps_p;
         A->cols[4 * q + k] = contract(pos_diff(A->P, w, we), E, eps);
         if (A->out_status) atomicOr(A->out_status + q, w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_NEAR_VERTEX));

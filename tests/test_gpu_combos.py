@@ -51,15 +51,16 @@ def test_hole_avoidance_in_a_batch_of_closed_and_holey_meshes():
     assert ((gpu["status"][2000:] & oracle.HOLE) != 0).mean() > 0.2
 
 
-def test_fp64_walk_on_a_klein_bottle():
+@pytest.mark.parametrize("prec", [64, 48], ids=["fp64", "double-float"])
+def test_fp64_walk_on_a_klein_bottle(prec):
     X, F = meshgen.klein_bottle(64, 32)
     X32 = parity.as_f32(X)
     rng = np.random.default_rng(113)
     q = meshgen.sample_queries(X, F, 4000, rng, 0.5, 4.0, 2)
     mesh = sg().Mesh(X32, F)
-    gpu = parity.run_gpu(mesh, q, 2, precision=64)
+    gpu = parity.run_gpu(mesh, q, 2, precision=prec)
     ref, _ = parity.run_oracle(X32, F, q, 2)
-    parity.compare(gpu, ref, meshgen.bbox_diag(X), 2, what="klein fp64", pos_tol=1e-6, dir_tol=1e-5)
+    parity.compare(gpu, ref, meshgen.bbox_diag(X), 2, what=f"klein precision {prec}", pos_tol=1e-6, dir_tol=1e-5)
     assert ((gpu["status"] & 512) != 0).mean() > 0.05
 
 
