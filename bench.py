@@ -780,6 +780,9 @@ def main():
         n, dt, _ = oracle_sample(args.cpu_sample, threads)
         line["cpu_baseline"] = {"value": n / dt, "unit": "geodesics/s", "cores": threads, "kind": "oracle",
                                 "sample": f"first {n} of the 1,048,576 queries, fwd+EP+GFD, {dt:.1f} s"}
+        n1, dt1, _ = oracle_sample(min(args.cpu_sample, 65536), 1)
+        line["cpu_baseline"]["one_core"] = {"value": n1 / dt1, "unit": "geodesics/s", "cores": 1,
+                                            "sample": f"first {n1} queries, fwd+EP+GFD, {dt1:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
         if args.json_out:
