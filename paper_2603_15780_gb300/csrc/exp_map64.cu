@@ -34,6 +34,8 @@ struct R64 {
 struct P64 {
     const int4 *__restrict__ rec;     // FP32 records: neighbour links
     const int4 *__restrict__ half48;  // [3 nF][2] double-float half-edge records (precision 48)
+    const int4 *__restrict__ half;    // FP32 half-edge records (edge rotation for the outputs)
+    const float4 *__restrict__ frm;   // FP32 face frames (3-D axes for the outputs)
     const double *__restrict__ rec64; // [nF][6] l01, x2x, x2y, 1/l12, 1/l20, -
     const double *__restrict__ frm64; // [nF][6] e1, e2
     const double *__restrict__ th64;  // [nV] theta, negated on the boundary
@@ -335,6 +337,8 @@ __device__ __forceinline__ DF dunpack(double d) {
 }
 
 #define SG48_HALF 7
+// the walk ended inside a face in the half-edge mode: px, py hold the end point in the edge frame
+#define SG48_END 8
 
 // the double-float half-edge record h into R: one 32-byte sector, one 256-bit load
 __device__ __forceinline__ void load48(R64 &R, const P64 &P, int h) {
@@ -422,15 +426,20 @@ __device__ bool half48(W64 &w, const P64 &P) {
     if (t.hi < 0.f) t = zero;
     const int k = w.f - 3 * (w.f / 3);
     if (df_ge(t, Lr)) {
-        // final truncated in-face segment
-        leave48(w, P, df_add(x, df_mul(Lr, dx)), df_mul(Lr, dy), dx, dy);
+        // final truncated in-face segment; the end point stays in the edge frame (SG48_END)
+        const DF xe = df_add(x, df_mul(Lr, dx)), ye = df_mul(Lr, dy);
+        // distances to the three edges: A -> B is the x axis; B -> C and C -> A by the cross
+        // product with the edge vector over its FP32 length (a threshold needs no more)
+        const DF bcx = df_sub(cx, L0);
+        const DF cB = df_sub(df_mul(bcx, ye), df_mul(cy, df_sub(xe, L0)));
+        const DF cA = df_sub(df_mul(cx, ye), df_mul(cy, xe));
+        const float nb = sqrtf(fmaf(bcx.hi, bcx.hi, cy.hi * cy.hi)), na = sqrtf(fmaf(cx.hi, cx.hi, cy.hi * cy.hi));
+        if (fabsf(ye.hi) <= w.nearf || fabsf(cB.hi) <= w.nearf * nb || fabsf(cA.hi) <= w.nearf * na)
+            w.st |= SG_ST_NEAR_EDGE;
+        w.px = dpack(xe);
+        w.py = dpack(ye);
         w.L = 0.0;
-        const R64 &R = w.R;
-        const double near = P.tau_near * w.lref;
-        const double d0 = fabs(w.py);
-        const double d1 = fabs((R.x2x - R.l01) * w.py - R.x2y * (w.px - R.l01)) * R.il1;
-        const double d2 = fabs(R.x2x * w.py - R.x2y * w.px) * R.il2;
-        if (fmin(fmin(d0, d1), d2) <= near) w.st |= SG_ST_NEAR_EDGE;
+        w.mode = SG48_END;
         return true;
     }
     const DF Ln = df_sub(Lr, t);
@@ -526,6 +535,12 @@ struct Job64 {
         for (int k = 0; k < NW; ++k) { cc[k] = 0.0; cs[k] = 0.0; }
         w.px = w.py = w.dx = w.dy = 0.0; w.L = 0.0;
         if (bad) { w.st |= SG_ST_INVALID; return false; }
+        w.nearf = (float)(P.tau_near * w.lref);
+        w.snapf = (float)(P.tau_snap * w.lref);
+        if (DFW) {
+            const int r = start48();
+            if (r >= 0) return r != 0;
+        }
         b0 = fmax(b0, 0.0) / sb; b1 = fmax(b1, 0.0) / sb; b2 = fmax(b2, 0.0) / sb;
         w.px = b1 * w.R.l01 + b2 * w.R.x2x;
         w.py = b2 * w.R.x2y;
@@ -561,12 +576,134 @@ struct Job64 {
             w.mode = 3 + c;
         }
         if (L > 0.0) hash64(w, w.f, P.want_hash);
-        w.nearf = (float)(P.tau_near * w.lref);
-        w.snapf = (float)(P.tau_snap * w.lref);
         return L > 0.0;
     }
+
+    // Double-float start: the start point, direction and length in double-float arithmetic, and
+    // the walker placed on the edge through which its ray enters the start face (behind the
+    // start point, the length extended by that distance), so the walk begins in the half-edge
+    // mode with no FP64 division or square root.  Returns 1 (a walk), or -1 for the FP64 start:
+    // a start on an edge or a vertex, a zero, huge or non-finite vector or length, or an
+    // entry-edge corner within the near band of the ray line (the FP64 step classifies those).
+    __device__ __forceinline__ int start48() {
+        const P64 &P = a->P;
+        const QueryIn &in = a->in;
+        const float b0 = __ldg(in.bary + 3 * q), b1 = __ldg(in.bary + 3 * q + 1), b2 = __ldg(in.bary + 3 * q + 2);
+        if (!(b0 > 0.f && b1 > 0.f && b2 > 0.f)) return -1;
+        R64 H;
+        load48(H, P, 3 * w.f);  // the record of edge 0 is the face frame: l01, (x2x, x2y)
+        const DF l01 = dunpack(H.l01), x2x = dunpack(H.x2x), x2y = dunpack(H.x2y);
+        const DF sb = df_add(two_sum(b0, b1), DF{b2, 0.f});
+        const DF rs = df_div(DF{1.f, 0.f}, sb);
+        const DF B1 = df_mul_f(rs, b1), B2 = df_mul_f(rs, b2);
+        const DF px = df_add_same_sign(df_mul(B1, l01), df_mul(B2, x2x)), py = df_mul(B2, x2y);
+        const double *fr = P.frm64 + 6 * w.f;
+        const double vx = __ldg(in.v + 3 * q), vy = __ldg(in.v + 3 * q + 1), vz = __ldg(in.v + 3 * q + 2);
+        const DF V1 = df_from(vx * fr[0] + vy * fr[1] + vz * fr[2]), V2 = df_from(vx * fr[3] + vy * fr[4] + vz * fr[5]);
+        const DF n2 = df_add_same_sign(df_mul(V1, V1), df_mul(V2, V2));
+        if (!(n2.hi > 1e-30f && n2.hi < 1e30f)) return -1;
+        const DF rn = df_rsqrt(n2);
+        const DF dx = df_mul(V1, rn), dy = df_mul(V2, rn);
+        DF L = df_mul(n2, rn);
+        if (in.length) {
+            const float Li = __ldg(in.length + q);
+            if (!(Li > 0.f && Li < 1e30f)) return -1;
+            L = DF{Li, 0.f};
+        }
+        // corners' signed distances to the ray line; the ray enters through edge j with corner j
+        // on its left and corner j+1 on its right
+        const DF zero{0.f, 0.f};
+        const DF s0 = df_sub(df_mul(dy, px), df_mul(dx, py));
+        const DF s1 = df_sub(df_mul(dx, df_neg(py)), df_mul(dy, df_sub(l01, px)));
+        const DF s2 = df_sub(df_mul(dx, df_sub(x2y, py)), df_mul(dy, df_sub(x2x, px)));
+        int j;
+        if (s0.hi > 0.f && s1.hi <= 0.f) j = 0;
+        else if (s1.hi > 0.f && s2.hi <= 0.f) j = 1;
+        else if (s2.hi > 0.f && s0.hi <= 0.f) j = 2;
+        else return -1;
+        const DF sa = j == 0 ? s0 : (j == 1 ? s1 : s2), sbb = j == 0 ? s1 : (j == 1 ? s2 : s0);
+        if (fabsf(sa.hi) < w.nearf || fabsf(sbb.hi) < w.nearf) return -1;
+        const DF ax = j == 0 ? zero : (j == 1 ? l01 : x2x), ay = j == 2 ? x2y : zero;
+        const DF bx = j == 0 ? l01 : (j == 1 ? x2x : zero), by = j == 1 ? x2y : zero;
+        const DF ex = df_sub(bx, ax), ey = df_sub(by, ay);
+        const DF se = df_div(sa, df_add_same_sign(sa, df_neg(sbb)));
+        const DF qx = df_add(ax, df_mul(se, ex)), qy = df_add(ay, df_mul(se, ey));
+        DF tb = df_add(df_mul(df_sub(px, qx), dx), df_mul(df_sub(py, qy), dy));
+        if (tb.hi < 0.f) tb = zero;
+        const DF il = df_rsqrt(df_add_same_sign(df_mul(ex, ex), df_mul(ey, ey)));
+        const DF hx = df_mul(df_add(df_mul(dx, ex), df_mul(dy, ey)), il);
+        const DF hy = df_mul(df_sub(df_mul(ex, dy), df_mul(ey, dx)), il);
+        if (!(hy.hi > 0.f)) return -1;
+        const double rx = df_to(dx), ry = df_to(dy);
+        for (int k = 0; k < NW; ++k) {
+            const float *wp = in.w + (3 * NW) * q + 3 * k;
+            const double wx = __ldg(wp), wy = __ldg(wp + 1), wz = __ldg(wp + 2);
+            const double w1 = wx * fr[0] + wy * fr[1] + wz * fr[2], w2 = wx * fr[3] + wy * fr[4] + wz * fr[5];
+            cc[k] = w1 * rx + w2 * ry;
+            cs[k] = rx * w2 - ry * w1;
+        }
+        hash64(w, w.f, P.want_hash);
+        const int h = 3 * w.f + j;
+        load48(w.R, P, h);
+        w.f = h;
+        w.px = dpack(se);
+        w.py = 0.0;
+        w.dx = dpack(hx);
+        w.dy = dpack(hy);
+        w.L = dpack(df_add_same_sign(L, tb));
+        w.mode = SG48_HALF;
+        return 1;
+    }
     __device__ __forceinline__ bool step() { return DFW ? step48<NW>(w, a->P) : step64<NW>(w, a->P); }
+    // The end of a double-float walk that stopped inside a face in the half-edge mode: the
+    // outputs (float32) from the double-float end point, with FP32 rotations and frames.
+    __device__ __forceinline__ void finish48() {
+        const Fwd64Args &A = *a;
+        const int h = w.f, f = h / 3, k = h - 3 * f;
+        const DF L0 = dunpack(w.R.l01), cx = dunpack(w.R.x2x), cy = dunpack(w.R.x2y);
+        const DF xe = dunpack(w.px), ye = dunpack(w.py);
+        const DF bC = df_div(ye, cy);
+        const DF bB = df_div(df_sub(xe, df_mul(bC, cx)), L0);
+        const DF bA = df_sub(df_sub(DF{1.f, 0.f}, bB), bC);
+        float b[3];
+        b[k] = bA.hi; b[nxt(k)] = bB.hi; b[prv(k)] = bC.hi;
+        const int4 t = __ldg(A.P.fv + f);
+        const float4 x0 = __ldg(A.P.V + t.x), x1 = __ldg(A.P.V + t.y), x2 = __ldg(A.P.V + t.z);
+        A.out_face[q] = f - w.foff;
+        A.out_bary[3 * q] = b[0]; A.out_bary[3 * q + 1] = b[1]; A.out_bary[3 * q + 2] = b[2];
+        A.out_pos[3 * q] = fmaf(b[0], x0.x, fmaf(b[1], x1.x, b[2] * x2.x));
+        A.out_pos[3 * q + 1] = fmaf(b[0], x0.y, fmaf(b[1], x1.y, b[2] * x2.y));
+        A.out_pos[3 * q + 2] = fmaf(b[0], x0.z, fmaf(b[1], x1.z, b[2] * x2.z));
+        // direction: edge frame -> face frame (the edge's rotation) -> 3-D (the face axes)
+        const int4 hr = __ldg(A.P.half + 2 * h + 1);
+        const float ca = __int_as_float(hr.y), sa = __int_as_float(hr.z);
+        const float hx = dunpack(w.dx).hi, hy = dunpack(w.dy).hi;
+        const float rx = ca * hx - sa * hy, ry = sa * hx + ca * hy;
+        const float4 fa = __ldg(A.P.frm + 2 * f), fb = __ldg(A.P.frm + 2 * f + 1);
+        A.out_dir[3 * q] = rx * fa.x + ry * fa.w;
+        A.out_dir[3 * q + 1] = rx * fa.y + ry * fb.x;
+        A.out_dir[3 * q + 2] = rx * fa.z + ry * fb.y;
+        if (NW > 0 && A.out_w) {
+            const float sg = (w.st & SG_PARITY_BIT) ? -1.f : 1.f;
+            for (int i = 0; i < NW; ++i) {
+                const float c = (float)cc[i], s = sg * (float)cs[i];
+                const float u1 = c * rx - s * ry, u2 = c * ry + s * rx;
+                float *o = A.out_w + (3 * NW) * q + 3 * i;
+                o[0] = u1 * fa.x + u2 * fa.w;
+                o[1] = u1 * fa.y + u2 * fb.x;
+                o[2] = u1 * fa.z + u2 * fb.y;
+            }
+        }
+        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u);
+        if (A.out_ncross) A.out_ncross[q] = w.ncross;
+        if (A.out_hash) A.out_hash[q] = w.hash;
+    }
+
     __device__ __forceinline__ void finish() {
+        if (DFW && w.mode == SG48_END) {
+            finish48();
+            return;
+        }
         const Fwd64Args &A = *a;
         const R64 &R = w.R;
         const double b2 = w.py / R.x2y, b1 = (w.px - b2 * R.x2x) / R.l01, b0 = 1.0 - b1 - b2;
@@ -737,6 +874,7 @@ cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const
     Fwd64Args a{};
     a.P.rec = m->d_rec; a.P.rec64 = m->d_rec64; a.P.frm64 = m->d_frm64; a.P.th64 = m->d_th64;
     a.P.half48 = m->d_half48;
+    a.P.half = m->d_half; a.P.frm = m->d_frm;
     a.P.fv = m->d_fv; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
     a.P.max_steps = r.max_steps; a.P.want_hash = io.out_hash != nullptr;
     a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
