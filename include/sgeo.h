@@ -112,8 +112,9 @@ typedef struct sg_opts {
                                48: the double-float walk, the same accuracy class as 64 on the
                                FP32 pipes: every crossing in double-float arithmetic (each value
                                an unevaluated sum of two FP32 numbers, about 48 significant
-                               bits; one 32-byte record per crossing), the rare events (start,
-                               vertex hits, boundary, end) in FP64; the same restrictions as 64,
+                               bits; one 32-byte record per crossing, the start and the end as
+                               well), the rare events (vertex hits, boundary stops, starts on an
+                               edge or vertex) in FP64; the same restrictions as 64,
                                and its first call on a mesh also allocates 96 B per face of
                                double-float records. */
 } sg_opts;

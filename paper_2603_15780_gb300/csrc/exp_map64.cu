@@ -15,8 +15,9 @@
 // pipes: its hot step is the FP32 walk's half-edge step (one 32-byte record per crossing, in the
 // entry edge's frame) with every quantity an unevaluated sum hi + lo of two FP32 numbers, about
 // 48 significant bits.  GB300 runs FP64 at a small fraction of its FP32 rate, so the double-float
-// step, several times the FP32 step's instructions, is still far faster than the FP64 step.  Rare
-// events (the start, vertex hits, the boundary, the end) use the FP64 face-frame code below.
+// step, several times the FP32 step's instructions, is still far faster than the FP64 step.  The
+// start and the end are double-float too; rare events (vertex hits, boundary stops, starts on an
+// edge or vertex, MAX_STEPS) use the FP64 face-frame code below.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -472,8 +473,9 @@ __device__ bool half48(W64 &w, const P64 &P) {
     return false;
 }
 
-// One step of the double-float walk: the half-edge step, or the FP64 face-frame step (start,
-// after a vertex transport), whose crossings enter the half-edge mode.
+// One step of the double-float walk: the half-edge step, or the FP64 face-frame step (after a
+// vertex transport, or from a start the double-float start declined), whose crossings enter the
+// half-edge mode.
 template <int NW>
 __device__ __forceinline__ bool step48(W64 &w, const P64 &P) {
     if (w.mode == SG48_HALF) {
