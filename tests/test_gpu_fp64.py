@@ -88,6 +88,24 @@ def test_double_float_walk_matches_the_fp64_walk():
             assert np.abs(a[k] - b[k])[~flag].max() <= 1e-6, k
 
 
+def test_double_float_walk_on_a_multi_mesh_batch():
+    """Mesh-tagged queries over a CSR batch of a sphere, a torus and a heightfield: the
+    double-float walk against the oracle mesh by mesh."""
+    rng = np.random.default_rng(23)
+    meshes = [meshgen.icosphere(3, 0.003, rng), meshgen.torus(48, 24, 1.0, 0.4, 0.002, rng),
+              meshgen.heightfield(24, rng)[:2]]
+    qs = [meshgen.sample_queries(X, F, 1500, rng, 0.0, 1.0, 1) for X, F in meshes]
+    mesh = sg().Mesh([(parity.as_f32(X), F) for X, F in meshes])
+    q = meshgen.Queries(*(np.concatenate([getattr(x, n) for x in qs]) for n in ("face", "bary", "v", "w", "g_pos")))
+    mid = np.repeat(np.arange(3, dtype=np.int32), 1500)
+    g = parity.run_gpu(mesh, q, 1, mesh_id=mid, precision=48)
+    for m, (X, F) in enumerate(meshes):
+        sl = slice(1500 * m, 1500 * (m + 1))
+        ref, _ = parity.run_oracle(parity.as_f32(X), F, q.take(np.arange(1500 * m, 1500 * (m + 1))), 1)
+        parity.compare({k: v[sl] for k, v in g.items()}, ref, meshgen.bbox_diag(X), 1,
+                       what=f"double-float mesh {m}", pos_tol=1e-6, dir_tol=1e-5)
+
+
 @PRECISIONS
 def test_fp64_geometry_follows_vertex_updates(prec):
     rng = np.random.default_rng(91)
