@@ -717,8 +717,9 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "pipelined": "step k+1 uploads and step k-1 downloads overlap step k; L2 flush inside"}
 
-    # ---- kernels the library launches per step: the walk, EP, the GFD re-walk, literal walks
-    # and assemble (with the chords), and the grad_V edge expansion and flush; plus the query order, as the
+    # ---- kernels the library launches per step: the walk, EP, the GFD re-walk, literal walks,
+    # assemble (with the chords) and its chord-walk pass, and the grad_V edge expansion and
+    # flush; plus the query order, as the
     # library decides it: by start face (5 sort/scan kernels) when the mesh's records (128 B per
     # face) exceed half of L2, else by walk length (2 kernels), for the forward and again for the
     # backward re-walk (which uses the length order whenever the batch is large enough).
@@ -730,7 +731,7 @@ def main():
         l2 = torch.cuda.get_device_properties(dev).L2_cache_size
         sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
     bwd_lorder = args.sort == 2 or (args.sort < 0 and nq >= 65536)
-    launches_per_step = 7 + {0: 0, 1: 5, 2: 2}[sort_mode] + (2 if bwd_lorder else 0)
+    launches_per_step = 8 + {0: 0, 1: 5, 2: 2}[sort_mode] + (2 if bwd_lorder else 0)
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     peak, peak_kind = peaks()

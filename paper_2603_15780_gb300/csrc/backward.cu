@@ -24,7 +24,9 @@
 //   k_bwd_assemble evaluates every other column as the 3-D chord of a short walk from p'
 //                  along R delta, summed segment by segment (exact for unswept
 //                  perturbations, no cancellation against |p'|), and contracts the columns
-//                  into grad_v, grad_p, grad_bary.
+//                  into grad_v, grad_p, grad_bary.  A chord that stays in the end face needs
+//                  no walk; the few queries with one that leaves it are finished by
+//                  k_bwd_assemble_walk.
 //
 // grad_V (vertex positions; not in the paper): the a.e. derivative of p' with the face
 // sequence fixed.  The end point is a chain of rigid 2-D maps T (one per crossing) applied
@@ -51,11 +53,10 @@
 #ifndef SG_REWALK_REFILL
 #define SG_REWALK_REFILL 24
 #endif
-// minimum resident blocks per SM the assemble and literal kernels are compiled for (assemble,
-// fwd+EP+GFD+grad_V step on 1M queries: 5 blocks 1.600 ms without spills, 6 1.602, 7 1.603;
-// the chord walk inlined four times instead of called: 1.625 / 1.617 / 1.610)
+// minimum resident blocks per SM the assemble and literal kernels are compiled for (the assemble
+// pass holds no walk since its chord walks moved to a second pass)
 #ifndef SG_ASSEMBLE_MINB
-#define SG_ASSEMBLE_MINB 5
+#define SG_ASSEMBLE_MINB 8
 #endif
 #ifndef SG_LITERAL_MINB
 #define SG_LITERAL_MINB 1
@@ -87,7 +88,8 @@ struct BwdArgs {
     float *cols;        // [nq][4] column contractions: par, perp, u, v; until the chords are
                         // evaluated the par slot holds the re-walk's swept-column mask (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) columns recomputed by literal walks (scratch)
-    int32_t *ntask;     // task counter (scratch)
+    int32_t *ntask;     // counters (scratch): [0] tasks, [1] re-walk and [2] literal-walk tickets,
+                        // [3] queries the assemble pass deferred (their ids reuse `tasks`)
     int4 *rst;          // [nq][2] where the literal walks of a split query restart (scratch):
                         // {half-edge | parity << 30 (-1: from the start), s, dx, dy}, {Lh, Ll, -, -}
     const int32_t *perm;  // re-walk queue position -> query (length order), or NULL
@@ -456,10 +458,11 @@ __device__ __noinline__ float chord_walk(const WalkParams &P, const Walker &w0, 
 
 // Contracted chord (p'' - p') / len of a walk of length `len` from the end state along u.  A
 // chord that ends inside the end face, farther than tau_near l_ref from its edges, is the step
-// len u itself, and its contraction u . gm = (u.d') a + (u.perp d') b needs no walk.
-template <bool HOLE>
+// len u itself, and its contraction u . gm = (u.d') a + (u.perp d') b needs no walk.  Other
+// chords are walked when WALK, else `ok` is cleared.
+template <bool HOLE, bool WALK>
 __device__ __forceinline__ float chord_col(const WalkParams &P, const Walker &w0, const EndAdj &E, float ux, float uy,
-                                           float len) {
+                                           float len, bool &ok) {
     const FaceRec &R = w0.R;
     const float x = fmaf(len, ux, w0.px), y = fmaf(len, uy, w0.py);
     const float tol = P.tau_near * w0.lref;
@@ -467,7 +470,9 @@ __device__ __forceinline__ float chord_col(const WalkParams &P, const Walker &w0
     const float e2 = (R.x2y * x - R.x2x * y) * R.il2;
     if (y > tol && e1 > tol && e2 > tol)
         return fmaf(fmaf(ux, E.dmx, uy * E.dmy), E.a, fmaf(uy, E.dmx, -ux * E.dmy) * E.b);
-    return chord_walk<HOLE>(P, w0, E, ux, uy, len);
+    if (WALK) return chord_walk<HOLE>(P, w0, E, ux, uy, len);
+    ok = false;
+    return 0.f;
 }
 
 // R x for a start-frame 2-D vector x: (x.d0) d' + s (x.perp d0) perp d'
@@ -594,10 +599,9 @@ __global__ void __launch_bounds__(128, SG_LITERAL_MINB) k_bwd_literal(BwdArgs A)
 
 // Columns the re-walk found unswept are chords from p' (the par column always is); the swept
 // ones were written by k_bwd_literal.  Then the columns are contracted into the gradients.
-template <bool HOLE>
-__global__ void __launch_bounds__(128, SG_ASSEMBLE_MINB) k_bwd_assemble(BwdArgs A) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= A.nq) return;
+// Without WALK a query whose chord leaves the end face is left for a second pass (false).
+template <bool HOLE, bool WALK>
+__device__ __forceinline__ bool assemble_query(const BwdArgs &A, int64_t q) {
     const WalkParams &P = A.P;
     Walker w;
     Carry<0> cw;
@@ -606,26 +610,28 @@ __global__ void __launch_bounds__(128, SG_ASSEMBLE_MINB) k_bwd_assemble(BwdArgs 
     if (live && !(w.st & SG_ST_INVALID)) {
         float4 c = *reinterpret_cast<const float4 *>(A.cols + 4 * q);
         const unsigned split = __float_as_uint(c.x);
+        bool ok = true;
         {
             const float d0x = w.dx, d0y = w.dy;
             EndAdj E = end_adjoint(A, q, w.foff);
             Walker we;
             end_walker(A, q, w, E, we);
             float ux, uy;
-            c.x = chord_col<HOLE>(P, we, E, E.dmx, E.dmy, A.eps_v);
+            c.x = chord_col<HOLE, WALK>(P, we, E, E.dmx, E.dmy, A.eps_v, ok);
             if (!(split & 1u)) {
                 rmap(-d0y, d0x, d0x, d0y, E, ux, uy);
-                c.y = chord_col<HOLE>(P, we, E, ux, uy, A.eps_v);
+                c.y = chord_col<HOLE, WALK>(P, we, E, ux, uy, A.eps_v, ok);
             }
             if (!(split & 2u)) {
                 rmap(1.f, 0.f, d0x, d0y, E, ux, uy);
-                c.z = chord_col<HOLE>(P, we, E, ux, uy, A.eps_p);
+                c.z = chord_col<HOLE, WALK>(P, we, E, ux, uy, A.eps_p, ok);
             }
             if (!(split & 4u)) {
                 rmap(w.R.x2x * w.R.il2, w.R.x2y * w.R.il2, d0x, d0y, E, ux, uy);
-                c.w = chord_col<HOLE>(P, we, E, ux, uy, A.eps_p);
+                c.w = chord_col<HOLE, WALK>(P, we, E, ux, uy, A.eps_p, ok);
             }
         }
+        if (!WALK && !ok) return false;
         Fr2 F0 = load_frm(P, w.f);
         gv = c.x * lift(F0, w.dx, w.dy) + c.y * lift(F0, -w.dy, w.dx);
         F3 eu = lift(F0, 1.f, 0.f), ev = lift(F0, w.R.x2x * w.R.il2, w.R.x2y * w.R.il2);
@@ -639,6 +645,23 @@ __global__ void __launch_bounds__(128, SG_ASSEMBLE_MINB) k_bwd_assemble(BwdArgs 
     if (A.grad_v) st3(A.grad_v, q, gv);
     if (A.grad_p) st3(A.grad_p, q, gp);
     if (A.grad_bary) st3(A.grad_bary, q, gb);
+    return true;
+}
+
+// One thread per query; the few queries with a chord that leaves the end face (a few percent)
+// go to a list for k_bwd_assemble_walk, which keeps the walk's registers out of this kernel.
+template <bool HOLE>
+__global__ void __launch_bounds__(128, SG_ASSEMBLE_MINB) k_bwd_assemble(BwdArgs A) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= A.nq) return;
+    if (!assemble_query<HOLE, false>(A, q)) A.tasks[atomicAdd(A.ntask + 3, 1)] = (int32_t)q;
+}
+
+template <bool HOLE>
+__global__ void __launch_bounds__(128) k_bwd_assemble_walk(BwdArgs A) {
+    const int n = A.ntask[3];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        assemble_query<HOLE, true>(A, A.tasks[i]);
 }
 
 // ------------------------------------------------------------------ end-barycentric upstream
@@ -908,12 +931,17 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         if (grad_V) k_bwd_rewalk<true, true><<<persistent_grid(k_bwd_rewalk<true, true>, nq), 128, 0, s>>>(A);
         else k_bwd_rewalk<true, false><<<persistent_grid(k_bwd_rewalk<true, false>, nq), 128, 0, s>>>(A);
         if (pev) cudaEventRecord(pev[1], s);
+        // the literal walks are done with the task list: the assemble pass reuses it for the
+        // queries it defers (a chord that leaves the end face), counted in ntask[3]
+        const unsigned gw = persistent_grid(k_bwd_assemble_walk<false>, nq / 16 + 1);
         if (r.boundary_mode) {
             k_bwd_literal<true><<<persistent_grid(k_bwd_literal<true>, 3 * nq), 128, 0, s>>>(A);
             k_bwd_assemble<true><<<g128, 128, 0, s>>>(A);
+            k_bwd_assemble_walk<true><<<gw, 128, 0, s>>>(A);
         } else {
             k_bwd_literal<false><<<persistent_grid(k_bwd_literal<false>, 3 * nq), 128, 0, s>>>(A);
             k_bwd_assemble<false><<<g128, 128, 0, s>>>(A);
+            k_bwd_assemble_walk<false><<<gw, 128, 0, s>>>(A);
         }
     }
     if ((g_dir && grad_v) || (A.n_w > 0)) k_bwd_transport<<<g256, 256, 0, s>>>(A);
