@@ -183,8 +183,9 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "icosphere-s6-noisy 81920F, queries L~U[0.1,1]; oracle sample "
-                       f"of {n} queries per step", "global_batch": n},
+            "config": {"workload": "icosphere-s6-noisy 81920F 1Mq fwd+EP+GFD+gradV", "global_batch": n,
+                       "faces": 81920, "sample": f"first {n} of the 1,048,576 queries per step; the oracle "
+                       "computes fwd+EP+GFD (its vertex gradient is checked by finite differences, not timed)"},
             "crossings_per_s": crossings * args.steps / t,
             "cpu_baseline": {"value": value, "unit": "geodesics/s", "cores": threads, "kind": "oracle",
                              "sample": f"first {n} of the 1,048,576 workload queries, fwd+EP+GFD"},
