@@ -29,6 +29,8 @@ METRIC = "face-crossings/sec and geodesics/sec fwd+bwd at 1M queries; frac of L2
 WORKLOAD_INDEX = 2
 EPS = 1e-4
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
+# where the nvidia-smi clock samples of the timed region are written
+CLOCKS_DIR = os.environ.get("SG_BENCH_CLOCKS_DIR", "/tmp")
 RECORD_BYTES = 32
 
 
@@ -245,8 +247,7 @@ def run_multimesh(args):
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
 
-    clk = Clocks(0, os.path.join(ROOT, "gpurun_out", "clocks_mm.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_mm.csv")
+    clk = Clocks(0, os.path.join(CLOCKS_DIR, "clocks_mm.csv"))
     t_plain = timed(run_plain)
     t_graph = timed(g.replay)
     clocks = clk.stop()
@@ -335,8 +336,7 @@ def run_config(args, index):
     variants = {"auto": sg.default_opts(), "persistent": sg.default_opts(kernel=sg.KERNEL_PERSISTENT),
                 "plain": sg.default_opts(kernel=sg.KERNEL_PLAIN, sort=0, fp64_escalate=0)}
     res, outs = {}, {}
-    clk = Clocks(0, os.path.join(ROOT, "gpurun_out", f"clocks_w{index}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_w.csv")
+    clk = Clocks(0, os.path.join(CLOCKS_DIR, f"clocks_w{index}.csv"))
     for name, o in variants.items():
         out = sg.exp_map(mesh, face, bary, v, w, opts=o)
         ws = out.pop("_workspace", None)
@@ -642,8 +642,7 @@ def main():
     ncross = int(out["ncross"].sum().item())
     st = out["status"].cpu().numpy().astype(np.uint32)
 
-    clk = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")) if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else Clocks(local, f"/tmp/clocks_r{rank}.csv")
+    clk = Clocks(local, os.path.join(CLOCKS_DIR, f"clocks_r{rank}.csv"))
     times = np.zeros((args.steps, 4))
     ep_own = np.zeros(args.steps)
     ktimes = {"walk": [], "rewalk": []}
