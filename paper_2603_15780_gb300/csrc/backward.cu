@@ -277,7 +277,7 @@ struct GradHook {
     float a, bs;        // gbar_i = a d_i + bs * s_i * perp(d_i)
     __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &G, float2 *eacc) {
         const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;                // |e| e
-        const float il = rsqrtf(fmaf(exr, exr, eyr * eyr));
+        const float il = c.il;
         const float yx = fmaf(c.Lr, w.dx, c.qx) - c.x0, yy = fmaf(c.Lr, w.dy, c.qy) - c.y0;  // y - A
         const float sb = (w.st & SG_PARITY_BIT) ? -bs : bs;             // old-frame parity
         const float gx = a * w.dx - sb * w.dy, gy = a * w.dy + sb * w.dx;

@@ -457,6 +457,7 @@ struct Cross {
     int g, kp, fl;
     float gax, gay, fx, fy, ndx, ndy;
     float ca0, sa0, ca1, sa1;  // rotations old frame -> old face frame, new frame -> new face frame
+    float il;                  // 1 / |x1 - x0| (the crossed edge's inverse length)
 };
 
 // Observer of a walk (the backward pass hooks into the same step code as the forward).
@@ -541,13 +542,11 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         if (fminf(fminf(d0, d1), d2) <= near) w.st |= SG_ST_NEAR_EDGE;
         return true;
     }
-    {   // compensated L -= t
-        float a = w.Lh, b = -t;
-        float sum = a + b;
-        float bb = sum - a;
-        float err = (a - (sum - bb)) + (b - bb);
+    {   // compensated L -= t: t < Lh + Ll here, so |Lh| >= |t| up to the tiny Ll and Dekker's
+        // fast two-sum gives the exact rounding error of Lh - t
+        const float sum = w.Lh - t;
+        w.Ll += -t - (sum - w.Lh);
         w.Lh = sum;
-        w.Ll += err;
     }
     if (hit) {
         half_to_face(w, P, cx, cy);
@@ -579,7 +578,7 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         const int k = w.h - 3 * (w.h / 3);
         const int g = hn / 3;
         hook.on_cross(w, Cross{right ? nxt(k) : prv(k), x0, y0, x1, y1, qx, qy, w.Lh + w.Ll, g, hn - 3 * g, fl,
-                               0.f, 0.f, hl(G), 0.f, ndx, ndy, hca(R), hsa(R), hca(G), hsa(G)},
+                               0.f, 0.f, hl(G), 0.f, ndx, ndy, hca(R), hsa(R), hca(G), hsa(G), re},
                       G);
     }
     w.px = fl ? s : 1.f - s;
@@ -722,7 +721,7 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
     float ndx = fl ? da : -da, ndy = dc;
     renorm(ndx, ndy);
     hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, 0.f, 0.f, hl(G), 0.f, ndx, ndy,
-                           1.f, 0.f, hca(G), hsa(G)},
+                           1.f, 0.f, hca(G), hsa(G), rsqrtf(fmaf(bx - ax, bx - ax, (by - ay) * (by - ay)))},
                   G);
     w.px = fl ? s : 1.f - s;
     w.py = 0.f;
