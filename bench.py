@@ -525,6 +525,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=262144)
     ap.add_argument("--cpu-sample", type=int, default=1048576)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time the step as eager launches, not a CUDA graph")
     ap.add_argument("--no-probe", action="store_true", help="skip the 32-B gather ceilings measured after the timed steps")
     ap.add_argument("--kernel", type=int, default=2)
     ap.add_argument("--sort", type=int, default=-1, help="1 on, 0 off, -1 the library's automatic choice")
@@ -606,6 +607,7 @@ def main():
     ews = torch.empty(sg.backward_workspace_size(mesh, "ep", nq, False), dtype=torch.uint8, device=dev)
 
     def step(ev=None, epev=None):
+        stream = torch.cuda.current_stream()  # the capture stream while the step is captured
         if ev is not None:
             ev[0].record(stream)
         sg.exp_map(mesh, face, bary, v, out=out, workspace=ws, opts=popts if ev is not None else opts)
@@ -662,8 +664,43 @@ def main():
         ep_own[k] = epev[0].elapsed_time(epev[1])
         for kk, pair in kev.items():
             ktimes[kk].append(pair[0].elapsed_time(pair[1]))
+    eager_ms = float(times.sum()) / args.steps
+
+    # ---- the timed steps: the step captured once as a CUDA graph and replayed (its launches and
+    # memsets leave the host), checked against the eager step's per-query gradients first
+    graph = None
+    if not args.no_graph:
+        cap = torch.cuda.Stream(device=dev)
+        cap.wait_stream(stream)
+        with torch.cuda.stream(cap):
+            for _ in range(2):
+                step()
+        stream.wait_stream(cap)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap):
+            r_graph = step()
+        eager_r = step()
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        for key in ("grad_v", "grad_p", "grad_bary", "status"):
+            if not torch.equal(r_graph[key], eager_r[key]):
+                raise RuntimeError(f"graph replay differs from the eager step in {key}")
+        gms = np.zeros(args.steps)
+        for k in range(args.steps):
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            flush.zero_()  # evicts L2 (not timed); the replay is enqueued behind it
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gms[k] = e0.elapsed_time(e1)
     clocks = clk.stop()
-    total_ms = max_over_ranks(float(times.sum()), world, dev)
+    total_ms = max_over_ranks(float(gms.sum() if graph is not None else times.sum()), world, dev)
     if world > 1:
         dist.barrier()
     ms_step = total_ms / args.steps
@@ -794,11 +831,13 @@ def main():
                        "kernel": "persistent" if args.kernel == 2 else "plain",
                        "query_order": {0: "input", 1: "start face", 2: "walk length"}[sort_mode],
                        "bwd_query_order": "walk length" if bwd_lorder else "input",
-                       "fp64_classification": bool(args.fp64)},
+                       "fp64_classification": bool(args.fp64),
+                       "launch": "eager" if graph is None else "CUDA graph of the step, captured once and replayed"},
             "crossings_per_s": world * ncross / (float(np.mean(ktimes["walk"])) * 1e-3),
             "fwd_geodesics_per_s": world * nq / (fwd_ms * 1e-3),
-            "phase_ms": {"fwd": fwd_ms, "ep_bwd": ep_ms, "gfd_bwd_gradV": gfd_ms,
-                         "note": "ep_bwd runs on a second stream beside gfd_bwd_gradV (its own interval)"},
+            "phase_ms": {"fwd": fwd_ms, "ep_bwd": ep_ms, "gfd_bwd_gradV": gfd_ms, "eager_step": eager_ms,
+                         "note": "eager launches with per-phase events; ep_bwd runs on a second stream beside "
+                                 "gfd_bwd_gradV (its own interval)"},
             "crossings_per_query": ncross / nq,
             "flag_fraction": {"near_vertex": float(((st & 4) != 0).mean()), "near_edge": float(((st & 8) != 0).mean()),
                               "fp64": float(((st & 32) != 0).mean())},

@@ -53,3 +53,72 @@ def test_autotuner_picks_a_valid_configuration():
     st = (out["status"] | ref["status"]).cpu().numpy()
     ok = (st & (sg.ST_NEAR_VERTEX | sg.ST_NEAR_EDGE)) == 0
     assert np.array_equal(out["face"].cpu().numpy()[ok], ref["face"].cpu().numpy()[ok])
+
+
+def test_graph_of_forward_and_both_backwards():
+    """The forward, EP on a second stream and GFD with the vertex gradient, captured as one CUDA
+    graph (memsets, the length orders, the task list and every counter inside) and replayed:
+    the per-query gradients equal the eager calls' bit for bit, the vertex gradient to float
+    rounding (atomic order), and a replay follows new values in the captured input buffers."""
+    import torch
+    import paper_2603_15780_gb300 as sg
+    rng = np.random.default_rng(61)
+    X, F = meshgen.icosphere(5, 0.003, rng)
+    q = meshgen.sample_queries(X, F, 70000, rng, 0.1, 1.0, 0)  # above the length-order threshold
+    mesh = sg.Mesh(parity.as_f32(X), F)
+    T = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    face, bary, v, g = T(q.face, torch.int32), T(q.bary), T(q.v), T(q.g_pos)
+    nq = len(q)
+    ws = torch.empty(sg.workspace_size(mesh, nq), dtype=torch.uint8, device="cuda")
+    bws = torch.empty(sg.backward_workspace_size(mesh, "gfd", nq, True), dtype=torch.uint8, device="cuda")
+    ews = torch.empty(sg.backward_workspace_size(mesh, "ep", nq, False), dtype=torch.uint8, device="cuda")
+    gV = torch.zeros(mesh.n_vertices, 3, device="cuda")
+    side = torch.cuda.Stream()
+
+    def step():
+        cs = torch.cuda.current_stream()
+        o = sg.exp_map(mesh, face, bary, v, workspace=ws)
+        done = torch.cuda.Event()
+        done.record(cs)
+        side.wait_event(done)
+        with torch.cuda.stream(side):
+            ep = sg.exp_map_backward(mesh, "ep", face, bary, v, o["face"], o["bary"], o["dir"], o["status"], g,
+                                     workspace=ews)
+            ep_done = torch.cuda.Event()
+            ep_done.record(side)
+        gV.zero_()
+        r = sg.exp_map_backward(mesh, "gfd", face, bary, v, o["face"], o["bary"], o["dir"], o["status"], g,
+                                grad_V=gV, workspace=bws)
+        cs.wait_event(ep_done)
+        return o, ep, r
+
+    eager = step()
+    torch.cuda.synchronize()
+    eager = [{k: t.clone() for k, t in d.items() if torch.is_tensor(t)} for d in eager]
+    eager_gV = gV.clone()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        step()
+    torch.cuda.current_stream().wait_stream(cap)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        outs = step()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    for ref, got in zip(eager, outs):
+        for k in ("face", "bary", "pos", "status", "grad_v", "grad_p", "grad_bary"):
+            if k in ref:
+                assert torch.equal(ref[k], got[k]), k
+    assert (gV - eager_gV).abs().max().item() <= 1e-5 * eager_gV.abs().max().item()
+    # new upstream gradient in the captured buffer: the replay follows it
+    g.mul_(-2.0)
+    graph.replay()
+    r2 = sg.exp_map_backward(mesh, "gfd", face, bary, v, outs[0]["face"], outs[0]["bary"], outs[0]["dir"],
+                             outs[0]["status"], g)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[2]["grad_v"], r2["grad_v"])
+    assert torch.equal(outs[2]["grad_v"], -2.0 * eager[2]["grad_v"]) or \
+        (outs[2]["grad_v"] + 2.0 * eager[2]["grad_v"]).abs().max().item() < 1e-5
