@@ -710,8 +710,9 @@ def main():
     # ---- end to end through the public API with host buffers (pinned), copies timed.  The steps
     # run as a serving loop runs them: step k+1's inputs go up on a copy stream while step k
     # computes, and step k's results come down on another while step k+1 computes (two buffer
-    # slots).  One pair of events spans all timed steps, so every step's copies lie inside the
-    # timed region, and so does the L2 flush that precedes every step's compute.
+    # slots, each with its step captured as a CUDA graph reading the slot's device buffers).  One
+    # pair of events spans all timed steps, so every step's copies lie inside the timed region,
+    # and so does the L2 flush that precedes every step's compute.
     e2e = None
     if not args.no_e2e:
         hb = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
@@ -730,6 +731,47 @@ def main():
         for ev in outs_done:
             ev.record(stream)
 
+        def compute(di):
+            cs = torch.cuda.current_stream()
+            o = sg.exp_map(mesh, di["face"], di["bary"], di["v"], workspace=ws, opts=opts)
+            fdone = torch.cuda.Event()
+            fdone.record(cs)
+            ep_stream.wait_event(fdone)
+            with torch.cuda.stream(ep_stream):
+                sg.exp_map_backward(mesh, "ep", di["face"], di["bary"], di["v"], o["face"], o["bary"], o["dir"],
+                                    o["status"], di["g"], opts=bopts, workspace=ews)
+                edone = torch.cuda.Event()
+                edone.record(ep_stream)
+                if not torch.cuda.is_current_stream_capturing():
+                    for t in (o["face"], o["bary"], o["dir"], o["status"]):
+                        t.record_stream(ep_stream)
+            gV.zero_()
+            r = sg.exp_map_backward(mesh, "gfd", di["face"], di["bary"], di["v"], o["face"], o["bary"], o["dir"],
+                                    o["status"], di["g"], eps_v=EPS, eps_p=EPS, grad_V=gV, opts=bopts,
+                                    workspace=bws)
+            cs.wait_event(edone)
+            return o, r
+
+        # with graphs, one captured step per buffer slot (its inputs are the slot's device buffers)
+        graphs, static = None, None
+        if not args.no_graph:
+            for sl in range(2):
+                for name, t in hb.items():
+                    dev_in[sl][name].copy_(t)
+            cap = torch.cuda.Stream(device=dev)
+            cap.wait_stream(stream)
+            with torch.cuda.stream(cap):
+                compute(dev_in[0])
+            stream.wait_stream(cap)
+            torch.cuda.synchronize()
+            graphs, static = [], []
+            for sl in range(2):
+                gr = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gr, stream=cap):
+                    static.append(compute(dev_in[sl]))
+                graphs.append(gr)
+            torch.cuda.synchronize()
+
         def e2e_step(k):
             sl = k & 1
             di, ho = dev_in[sl], host_out[sl]
@@ -741,22 +783,12 @@ def main():
                 ready.record(up)
             flush.zero_()
             stream.wait_event(ready)
-            o = sg.exp_map(mesh, di["face"], di["bary"], di["v"], workspace=ws, opts=opts)
-            fdone = torch.cuda.Event()
-            fdone.record(stream)
-            ep_stream.wait_event(fdone)
-            with torch.cuda.stream(ep_stream):
-                sg.exp_map_backward(mesh, "ep", di["face"], di["bary"], di["v"], o["face"], o["bary"], o["dir"],
-                                    o["status"], di["g"], opts=bopts, workspace=ews)
-                edone = torch.cuda.Event()
-                edone.record(ep_stream)
-                for t in (o["face"], o["bary"], o["dir"], o["status"]):
-                    t.record_stream(ep_stream)
-            gV.zero_()
-            r = sg.exp_map_backward(mesh, "gfd", di["face"], di["bary"], di["v"], o["face"], o["bary"], o["dir"],
-                                    o["status"], di["g"], eps_v=EPS, eps_p=EPS, grad_V=gV, opts=bopts,
-                                    workspace=bws)
-            stream.wait_event(edone)
+            if graphs is not None:
+                stream.wait_event(outs_done[sl])  # the slot's last results are on the host
+                graphs[sl].replay()
+                o, r = static[sl]
+            else:
+                o, r = compute(di)
             free[sl].record(stream)
             done = torch.cuda.Event()
             done.record(stream)
@@ -765,7 +797,8 @@ def main():
             with torch.cuda.stream(down):
                 for name, t in (("pos", o["pos"]), ("grad_v", r["grad_v"]), ("grad_p", r["grad_p"])):
                     ho[name].copy_(t, non_blocking=True)
-                    t.record_stream(down)
+                    if graphs is None:
+                        t.record_stream(down)
                 outs_done[sl].record(down)
 
         for k in range(2):  # untimed: both slots warm
@@ -781,7 +814,8 @@ def main():
         torch.cuda.synchronize()
         e2e = {"value": args.steps * nq / (e0.elapsed_time(e1) * 1e-3), "unit": "geodesics/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "pipelined": "step k+1 uploads and step k-1 downloads overlap step k; L2 flush inside"}
+               "pipelined": "step k+1 uploads and step k-1 downloads overlap step k; L2 flush inside",
+               "launch": "eager" if graphs is None else "one captured CUDA graph per buffer slot"}
 
     # ---- kernels the library launches per step: the walk, EP, the GFD re-walk, literal walks,
     # assemble (with the chords) and its chord-walk pass, and the grad_V edge expansion and
