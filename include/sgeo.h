@@ -347,9 +347,11 @@ sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id
 
 /*
  * sg_exp_map_backward_workspace_size -- bytes of device scratch sg_exp_map_backward needs for
- * nq queries with `estimator` (SG_EST_*) and, if want_grad_V != 0, the vertex gradient: the
- * GFD column table (16 B per query) and literal-walk task list (12 B per query), a float4
- * accumulator per vertex for grad_V, and the re-walk's length order (5 B per query).  Pass it
+ * nq queries with `estimator` (SG_EST_*) and, if want_grad_V != 0, the vertex gradient: for
+ * GFD the column table (16 B per query), the literal-walk task list (12 B per query, reused for
+ * the queries whose chords are walked) and the literal walks' restart records (32 B per query);
+ * for grad_V a float4 accumulator per vertex and a float2 per interior edge; 12 B per query for
+ * an end-barycentric upstream gradient; and the re-walk's length order (5 B per query).  Pass it
  * as o->workspace; without it the library allocates stream-ordered scratch itself.
  */
 sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_t estimator, int64_t nq,
