@@ -20,7 +20,8 @@
 //                  re-walk accumulates grad_V (below).
 //   k_bwd_literal  evaluates the swept columns by the paper's literal walk
 //                  (Exp(p, v + eps e_perp), or Exp(p_u, v_u) after Exp(p, eps e_u) carrying v),
-//                  differences taken in face-local coordinates;
+//                  restarted on the entry edge of the face where the re-walk met the first
+//                  swept corner, differences taken in face-local coordinates;
 //   k_bwd_assemble evaluates every other column as the 3-D chord of a short walk from p'
 //                  along R delta, summed segment by segment (exact for unswept
 //                  perturbations, no cancellation against |p'|), and contracts the columns
@@ -36,9 +37,10 @@
 // gradient parallel-transported back (gbar_i = a d_i + s_i b perp(d_i)), so one forward
 // re-walk accumulates everything (no stored path).  2-D corner gradients map to 3-D by the
 // face frame F (in-plane); start and end faces add b_k F gbar0 and b'_k (g.n) n, plus a
-// tilt term when v has a normal component.  Contributions are accumulated per vertex in a
-// two-slot register cache (consecutive crossings share a vertex) and flushed with float4
-// atomics into a scratch accumulator that k_gradv_flush adds to the caller's grad_V.
+// tilt term when v has a normal component.  Each crossing adds two scalars to its interior
+// edge's accumulator (one 8-byte atomic; GradHook below), k_gradv_edges expands them into
+// vertex gradients once per edge, the start and end terms go into a float4 accumulator per
+// vertex, and k_gradv_flush adds it to the caller's grad_V.
 #include <cuda_runtime.h>
 
 #include <algorithm>
