@@ -101,13 +101,14 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def gather_ceilings(sg, ncross, ktimes):
+def gather_ceilings(ncross, ktimes):
     """The walks' record reads against the device's own 32-B gather ceilings, measured after the
     timed region by sg_probe_gather on an L2-resident 16 MiB table (the icosphere's half-edge and
     face records take 10.5 MB): the L2 streaming read rate, independent random record gathers,
     and chains of dependent gathers at each walk kernel's occupancy (one gather in flight per
     thread, as in a walk), each with the walks' two 16-B loads per record and with one 256-bit
     load.  Rates are of record bytes only (32 B per crossing)."""
+    import measure as sg
     tb = 16 << 20
     W = sg.PROBE_LD256
     out = {"table_MiB": tb >> 20, "stream_GBps": sg.probe_gather(sg.PROBE_STREAM, tb, 4, 256, 100),
@@ -855,7 +856,7 @@ def main():
                 "algorithmic_bytes_per_launch": int(kern[dom][0]), "launch_ms": kern[dom][1]}
     kernels = {k: {"ms": t, "algorithmic_GBps": b / (t * 1e-3) / 1e9, "frac_of_hbm": b / (t * 1e-3) / 1e9 / peak}
                for k, (b, t) in kern.items()}
-    l2_gather = None if args.no_probe else gather_ceilings(sg, ncross, ktimes)
+    l2_gather = None if args.no_probe else gather_ceilings(ncross, ktimes)
 
     line = {"metric": METRIC, "value": value, "unit": "geodesics/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -242,6 +242,11 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
  * array: the library clears what must start at zero on every call, but calls whose GPU work
  * overlaps in time (concurrent streams, several host threads) race on it and must be
  * serialised by the caller.
+ * Two more rules keep it allocation-free.  The current device must be the one the mesh was
+ * created on (else SG_ERR_INVALID_ARG: the array's address is per device).  Precision 48 and 64
+ * walk on FP64 geometry (and, for 48, double-float records) that the first sg_exp_map call with
+ * that precision allocates on the mesh; until such a call has been made, this entry point
+ * rejects those precisions with SG_ERR_UNSUPPORTED instead of allocating them.
  */
 sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
                              const float *bary, const float *v, const float *length, int32_t n_w,
@@ -356,32 +361,6 @@ sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id
  */
 sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_t estimator, int64_t nq,
                                              int32_t want_grad_V, size_t *bytes);
-
-/*
- * sg_probe_gather -- measures a memory ceiling of record walks on the current device (a
- * diagnostic for reading the walk kernels' rates against; not part of the exponential map).
- * The walk reads one 32-byte record per edge crossing and cannot issue the next read before
- * the last one returns (Alg. "Parallel Geodesic Tracing CUDA Kernel").  A table of 32-byte
- * records (the largest power-of-two count within table_bytes, 4 KiB .. 2 GiB) is filled on the
- * host, copied to the device, read once untimed (bringing it into L2 when it fits) and then
- * once timed with CUDA events, by a grid of blocks_per_sm x (SM count) blocks of `threads`:
- *   SG_PROBE_STREAM  coalesced 16-byte loads sweeping the whole table `loads` times
- *   SG_PROBE_RANDOM  `loads` (rounded up to 4) independent record gathers per thread at random
- *                    positions, four in flight
- *   SG_PROBE_CHAIN   `loads` dependent record gathers per thread: each record holds the index
- *                    of the next along one random cycle through the table
- * OR SG_PROBE_LD256 into the random and chain modes to read each record with one 256-bit
- * load instead of two 16-byte loads (the walk kernels' form); the stream mode ignores it.
- * Outputs: *out_seconds the timed launch, *out_bytes the bytes it read (32 per gather).
- * Synchronous (the legacy default stream); allocates and frees its own device memory.
- * Errors: SG_ERR_INVALID_ARG (mode, sizes out of range), SG_ERR_OOM, SG_ERR_CUDA.
- */
-#define SG_PROBE_STREAM 0
-#define SG_PROBE_RANDOM 1
-#define SG_PROBE_CHAIN 2
-#define SG_PROBE_LD256 4
-sg_status sg_probe_gather(int32_t mode, int64_t table_bytes, int32_t blocks_per_sm, int32_t threads,
-                          int32_t loads, double *out_seconds, double *out_bytes);
 
 /* Library version string. */
 const char *sg_version(void);

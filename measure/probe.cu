@@ -22,7 +22,18 @@
 
 #include <vector>
 
-#include "sgeo_internal.h"
+// Measurement-only library (libsgeo_probe.so), built beside the exponential-map library and
+// loaded by the benchmark; it is not part of the exponential map's C ABI.  Return codes: 0 ok,
+// 1 invalid argument, 4 CUDA error, 5 out of device memory.
+#define SG_PROBE_STREAM 0
+#define SG_PROBE_RANDOM 1
+#define SG_PROBE_CHAIN 2
+#define SG_PROBE_LD256 4
+typedef int sg_probe_status;
+#define SG_OK 0
+#define SG_ERR_INVALID_ARG 1
+#define SG_ERR_CUDA 4
+#define SG_ERR_OOM 5
 
 namespace {
 
@@ -98,7 +109,7 @@ uint64_t splitmix64(uint64_t &s) {
 
 }  // namespace
 
-extern "C" sg_status sg_probe_gather(int32_t mode, int64_t table_bytes, int32_t blocks_per_sm, int32_t threads,
+extern "C" sg_probe_status sg_probe_gather(int32_t mode, int64_t table_bytes, int32_t blocks_per_sm, int32_t threads,
                                      int32_t loads, double *out_seconds, double *out_bytes) {
     if (!out_seconds || !out_bytes) return SG_ERR_INVALID_ARG;
     const bool w256 = (mode & SG_PROBE_LD256) != 0;
@@ -133,7 +144,7 @@ extern "C" sg_status sg_probe_gather(int32_t mode, int64_t table_bytes, int32_t 
     int4 *t = nullptr;
     unsigned *sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    sg_status st = SG_OK;
+    sg_probe_status st = SG_OK;
     if (cudaMalloc((void **)&t, bytes) != cudaSuccess || cudaMalloc((void **)&sink, 64) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(t);

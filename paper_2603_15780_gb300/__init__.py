@@ -34,7 +34,7 @@ EST_EP, EST_GFD = 0, 1
 EXPORTED = ["sg_opts_default", "sg_status_string", "sg_mesh_create", "sg_mesh_create_batched",
             "sg_mesh_destroy", "sg_mesh_get_info", "sg_exp_map_workspace_size", "sg_exp_map",
             "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc", "sg_exp_map_backward_workspace_size",
-            "sg_mesh_update_vertices", "sg_exp_map_trace", "sg_transport_back", "sg_probe_gather"]
+            "sg_mesh_update_vertices", "sg_exp_map_trace", "sg_transport_back"]
 
 
 def status_names(st: int) -> list[str]:
@@ -100,8 +100,6 @@ def lib():
                                               C.POINTER(Opts), P]
             L.sg_transport_back.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, C.c_int32, P, P,
                                             C.POINTER(Opts), P]
-            L.sg_probe_gather.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
-                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
             for f in EXPORTED:
                 if f not in ("sg_opts_default",):
                     getattr(L, f).restype = getattr(L, f).restype or C.c_int
@@ -413,20 +411,6 @@ def transport_back(mesh: Mesh, face, bary, v, end, u, mesh_id=None, *, opts: Opt
                                  C.c_void_p(s.cuda_stream))
     _check(rc, "sg_transport_back")
     return out.reshape(shape)
-
-
-PROBE_STREAM, PROBE_RANDOM, PROBE_CHAIN, PROBE_LD256 = 0, 1, 2, 4
-
-
-def probe_gather(mode: int, table_bytes: int, blocks_per_sm: int, threads: int, loads: int) -> float:
-    """sg_probe_gather: GB/s of one timed launch reading a table of 32-byte records (mode
-    PROBE_STREAM, PROBE_RANDOM or PROBE_CHAIN, optionally | PROBE_LD256; see the header).
-    Synchronous."""
-    _torch()
-    sec, nb = C.c_double(), C.c_double()
-    _check(lib().sg_probe_gather(mode, table_bytes, blocks_per_sm, threads, loads, C.byref(sec), C.byref(nb)),
-           "sg_probe_gather")
-    return nb.value / sec.value / 1e9
 
 
 def _autograd_function():

@@ -972,6 +972,8 @@ extern "C" sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int3
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SG_ERR_CUDA; }
     if (dev < 0 || dev >= SG_NOALLOC_MAX_DEVICES) return SG_ERR_UNSUPPORTED;
+    // the scratch address is per device: it must be the device that holds the mesh records
+    if (dev != m->device) return SG_ERR_INVALID_ARG;
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -992,6 +994,9 @@ extern "C" sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int3
     sg_status st = sg_exp_map_workspace_size(m, nq, &r, &need);
     if (st != SG_OK) return st;
     if (need > SG_NOALLOC_SCRATCH_BYTES) return SG_ERR_OOM;
+    // The FP64 geometry and the double-float records are allocated by the first call on a mesh
+    // that asks for them; this entry point allocates nothing, so it requires them to exist.
+    if (r.precision >= 48 && (!m->d_rec64 || (r.precision == 48 && !m->d_half48))) return SG_ERR_UNSUPPORTED;
     r.workspace = scratch;
     r.workspace_bytes = SG_NOALLOC_SCRATCH_BYTES;
     return sg_exp_map(m, nq, mesh_id, face, bary, v, length, n_w, w, out_face, out_bary, out_pos, out_dir, out_w,

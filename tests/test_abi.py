@@ -46,9 +46,6 @@ def test_null_arguments_rejected_without_gpu_work():
     assert L.sg_exp_map_trace(None, 1, None, None, None, None, None, 8, *([None] * 10), C.byref(o), None) == 1
     assert L.sg_mesh_update_vertices(None, None, None) == 1
     assert L.sg_transport_back(None, 1, *([None] * 7), 1, None, None, C.byref(o), None) == 1
-    sec, nb = C.c_double(), C.c_double()
-    assert L.sg_probe_gather(7, 1 << 20, 1, 256, 64, C.byref(sec), C.byref(nb)) == 1
-    assert L.sg_probe_gather(2, 1 << 20, 1, 100, 64, C.byref(sec), C.byref(nb)) == 1
     n = C.c_size_t()
     assert L.sg_exp_map_workspace_size(None, 1, None, C.byref(n)) == 1
 

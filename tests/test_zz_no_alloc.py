@@ -2,9 +2,11 @@
 allocate device memory at call time (code whose device memory is owned by another
 framework's pool, or loops where a cudaMalloc/cudaFree would synchronise the device).
 
-It is called here through the C ABI and must reproduce sg_exp_map's results on two
-calls in a row (the second call finds the first call's leftovers in the shared scratch
-array), and reject a batch too large for its fixed scratch without launching anything.
+It is called here through the C ABI and must reproduce sg_exp_map's results on calls in a
+row on the persistent kernel (each call finds the previous call's leftovers in the shared
+scratch array: queue counter, sort histogram, permutation), refuse the double-float walk on
+a mesh whose double-float records do not exist yet (creating them would allocate), and
+reject a batch too large for its fixed scratch without launching anything.
 This file is collected last so a failure here cannot hide the other tests' results.
 """
 import ctypes as C
@@ -35,31 +37,74 @@ def _noalloc(sg, mesh, face, bary, v, w, nw, opts, torch):
     return rc, out
 
 
+def _check_same(out, ref, diag, what):
+    for k in ("face", "status", "ncross", "hash"):
+        assert torch_equal(out[k], ref[k]), f"{what}: {k} differs"
+    for k in ("pos", "bary", "dir", "w"):
+        if k in ref and ref[k] is not None and k in out:
+            err = (out[k][..., :ref[k].shape[-1]] - ref[k]).abs().max().item()
+            assert err <= 1e-5 * diag, f"{what}: {k} differs by {err}"
+
+
+def torch_equal(a, b):
+    import torch
+    return torch.equal(a, b)
+
+
 def test_noalloc_matches_exp_map_on_two_calls():
+    """Two calls in a row on the persistent kernel, whose work queue lives in the shared scratch
+    array: the second call, of another size and order, starts from the first call's leftovers
+    (counter, histogram, permutation).  Each call is checked against sg_exp_map with the same
+    options, bit for bit on the discrete outputs."""
+    import torch
+    import paper_2603_15780_gb300 as sg
+    X, F = meshgen.icosphere(3)
+    X32 = parity.as_f32(X)
+    mesh = sg.Mesh(X32, F)
+    rng = np.random.default_rng(77)
+    q = meshgen.sample_queries(X, F, 100000, rng, 0.0, 3.0, 1)
+    diag = meshgen.bbox_diag(X)
+    # (queries, options): a length-ordered batch of 100,000, then a start-face sorted batch of
+    # 70,001 in reverse order, then an unsorted one of 65,536 -- all above the size where the
+    # automatic choice would skip the queue
+    calls = [(np.arange(100000), dict(kernel=2, sort=2)),
+             (np.arange(100000)[::-1][:70001].copy(), dict(kernel=2, sort=1)),
+             (np.arange(65536) * 3 % 100000, dict(kernel=2, sort=0))]
+    for call, (idx, kw) in enumerate(calls):
+        face = torch.tensor(q.face[idx], device="cuda")
+        bary = torch.tensor(parity.as_f32(q.bary[idx]), device="cuda")
+        v = torch.tensor(parity.as_f32(q.v[idx]), device="cuda")
+        w = torch.tensor(parity.as_f32(q.w[idx, :1]), device="cuda")
+        ref = sg.exp_map(mesh, face, bary, v, w, want_hash=True, **kw)
+        rc, out = _noalloc(sg, mesh, face, bary, v, w, 1, sg.default_opts(**kw), torch)
+        torch.cuda.synchronize()
+        assert rc == 0, f"call {call}: status {rc}"
+        _check_same(out, ref, diag, f"call {call} {kw}")
+
+
+def test_noalloc_double_float_needs_the_prepared_mesh():
+    """Precision 48 walks on double-float records that the first sg_exp_map call with that
+    precision allocates on the mesh: before it, the allocation-free entry point refuses
+    (SG_ERR_UNSUPPORTED) instead of allocating; after it, it matches sg_exp_map."""
     import torch
     import paper_2603_15780_gb300 as sg
     wl = meshgen.workload(0)
     X, F = wl.single
-    X32 = parity.as_f32(X)
-    mesh = sg.Mesh(X32, F)
+    mesh = sg.Mesh(parity.as_f32(X), F)
     q = wl.queries
-    diag = meshgen.bbox_diag(X)
-    batches = [np.arange(len(q)), np.arange(len(q))[::-1][:3001].copy()]   # second call: other size/order
-    for call, idx in enumerate(batches):
-        face = torch.tensor(q.face[idx], device="cuda")
-        bary = torch.tensor(parity.as_f32(q.bary[idx]), device="cuda")
-        v = torch.tensor(parity.as_f32(q.v[idx]), device="cuda")
-        w = torch.tensor(parity.as_f32(q.w[idx]), device="cuda")
-        ref = sg.exp_map(mesh, face, bary, v, w, want_hash=True)
-        opts = sg.default_opts()
-        rc, out = _noalloc(sg, mesh, face, bary, v, w, 1, opts, torch)
-        torch.cuda.synchronize()
-        assert rc == 0, f"call {call}: status {rc}"
-        for k in ("face", "status", "ncross", "hash"):
-            assert torch.equal(out[k], ref[k]), f"call {call}: {k} differs"
-        for k in ("pos", "bary", "dir", "w"):
-            err = (out[k] - ref[k]).abs().max().item()
-            assert err <= 1e-5 * diag, f"call {call}: {k} differs by {err}"
+    face = torch.tensor(q.face, device="cuda")
+    bary = torch.tensor(parity.as_f32(q.bary), device="cuda")
+    v = torch.tensor(parity.as_f32(q.v), device="cuda")
+    w = torch.tensor(parity.as_f32(q.w[:, :1]), device="cuda")
+    opts = sg.default_opts(kernel=2, precision=48)
+    rc, _ = _noalloc(sg, mesh, face, bary, v, w, 1, opts, torch)
+    torch.cuda.synchronize()
+    assert rc == 6
+    ref = sg.exp_map(mesh, face, bary, v, w, want_hash=True, kernel=2, precision=48)
+    rc, out = _noalloc(sg, mesh, face, bary, v, w, 1, sg.default_opts(kernel=2, precision=48), torch)
+    torch.cuda.synchronize()
+    assert rc == 0
+    _check_same(out, ref, meshgen.bbox_diag(X), "precision 48")
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
