@@ -62,6 +62,11 @@ typedef enum sg_status {
 #define SG_ST_NO_GRADV 1024u     /* (backward) no vertex-position gradient for this query (vertex
                                     hit or boundary stop: the map is not differentiable there) */
 #define SG_ST_HOLE 2048u         /* hole avoidance (boundary_mode 1) traced along the boundary */
+#define SG_ST_MIXED 4096u        /* walked by the mixed-precision walk (precision 40, or chosen by the
+                                    automatic precision for a walk beyond the FP32 walk's range) */
+#define SG_ST_REWALK_DIVERGED 8192u /* (backward) the FP32 re-walk ended in another face than the
+                                    forward walk (possible only where the forward walk was the
+                                    mixed walk): the gradients follow the re-walk's path */
 
 /* kernels */
 #define SG_KERNEL_AUTO 0

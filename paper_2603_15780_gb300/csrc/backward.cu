@@ -410,6 +410,10 @@ struct RewalkJob {
                     if (split & (1u << k)) A->tasks[base++] = (int32_t)((q << 2) | (k + 1));
             }
         }
+        // a forward walk beyond the FP32 walk's range ran in the mixed walk; this FP32 re-walk
+        // may then pass a vertex on the other side: reported when it ends in another face
+        if (A->end_status && (__ldg(A->end_status + q) & SG_ST_MIXED) && w.f - w.foff != __ldg(A->end_face + q))
+            st |= SG_ST_REWALK_DIVERGED;
         if (A->out_status) A->out_status[q] = st;
     }
 };
@@ -868,7 +872,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     sg_opts_default(&r);
     if (o) r = *o;
     if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
-    if (r.precision >= 48) return SG_ERR_UNSUPPORTED;
+    if (r.precision >= 40) return SG_ERR_UNSUPPORTED;
     if (r.max_steps <= 0) r.max_steps = 1 << 20;
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
     if (r.tau_snap <= 0.f) r.tau_snap = 1e-6f;
@@ -976,7 +980,7 @@ extern "C" sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32
     sg_opts r;
     sg_opts_default(&r);
     if (o) r = *o;
-    if (r.precision >= 48) return SG_ERR_UNSUPPORTED;
+    if (r.precision >= 40) return SG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     BwdArgs A{};
     A.P.rec = m->d_rec; A.P.fv = m->d_fv; A.P.frm = m->d_frm; A.P.half = m->d_half; A.P.V = m->d_V; A.P.face_off = m->d_face_off;

@@ -44,7 +44,23 @@ struct FwdArgs {
     uint64_t *out_hash;
     const int32_t *__restrict__ perm;  // queue position -> query index (NULL: identity)
     int32_t *counter;                  // persistent work counter
+    // automatic precision: queries handed to the mixed walk (precision 40) are appended to
+    // esc_list (count in *esc_count) and left unwritten -- those whose length exceeds
+    // esc_lmax l_ref at the start, and those whose crossing count reaches esc_ncross
+    int32_t *esc_list, *esc_count;
+    float esc_lmax;
+    int32_t esc_ncross;
 };
+
+// Appends query q to the escalation list (warp-aggregated: one atomic per calling warp).
+__device__ __forceinline__ void escalate(const FwdArgs &a, int64_t q) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(a.esc_count, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    a.esc_list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)q;
+}
 
 template <int NW>
 __device__ void walker_finish(const FwdArgs &a, int64_t q, const Walker &w, const Carry<NW> &cw) {
@@ -79,28 +95,50 @@ __device__ void walker_finish(const FwdArgs &a, int64_t q, const Walker &w, cons
     if (a.out_hash) a.out_hash[q] = w.hash;
 }
 
-template <int NW, bool ESC = false>
+template <int NW, bool ESC = false, bool AUTO = false>
 __global__ void __launch_bounds__(256) k_walk_plain(FwdArgs a) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.nq) return;
     Walker w;
     Carry<NW> cw;
     if (walker_init<NW>(a.P, a.in, q, w, cw)) {
+        if (AUTO && w.Lh > a.esc_lmax * w.lref) {
+            escalate(a, q);
+            return;
+        }
         while (!walker_step<ESC>(w, a.P)) {
+        }
+        // the step cap of an AUTO walk is its crossing budget (see FwdJob)
+        if (AUTO && a.esc_ncross && (w.st & SG_ST_MAX_STEPS)) {
+            escalate(a, q);
+            return;
         }
     }
     walker_finish<NW>(a, q, w, cw);
 }
 
-template <int NW, bool ESC, bool HOLE = false>
+// AUTO: the automatic precision -- a query leaves this FP32 walk for the mixed walk when its
+// length exceeds esc_lmax l_ref at the start, or when its walk reaches the crossing budget.  The
+// budget is the walk's step cap (P.max_steps, set to it by the host; a crossing is a step, so
+// no walk kept here crosses more edges than that), which costs no test of its own per step; a
+// walk stopped by it is handed on (esc_ncross != 0) unless the caller's own cap is that low.
+template <int NW, bool ESC, bool HOLE = false, bool AUTO = false>
 struct FwdJob {
     const FwdArgs *a;
     Walker w;
     Carry<NW> cw;
     int64_t q;
+    bool esc;  // handed to the mixed walk: nothing to write here
     __device__ __forceinline__ bool init(int64_t t) {
         q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
-        return walker_init<NW>(a->P, a->in, q, w, cw);
+        esc = false;
+        const bool live = walker_init<NW>(a->P, a->in, q, w, cw);
+        if (AUTO && live && w.Lh > a->esc_lmax * w.lref) {
+            esc = true;
+            escalate(*a, q);
+            return false;
+        }
+        return live;
     }
     __device__ __forceinline__ bool step() {
         if (HOLE) {
@@ -113,14 +151,21 @@ struct FwdJob {
         }
         return walker_step<ESC, HOLE>(w, a->P);
     }
-    __device__ __forceinline__ void finish() { walker_finish<NW>(*a, q, w, cw); }
+    __device__ __forceinline__ void finish() {
+        if (AUTO && !esc && a->esc_ncross && (w.st & SG_ST_MAX_STEPS)) {
+            esc = true;
+            escalate(*a, q);
+        }
+        if (AUTO && esc) return;
+        walker_finish<NW>(*a, q, w, cw);
+    }
 };
 
-template <int NW, bool ESC>
+template <int NW, bool ESC, bool AUTO = false>
 __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
-    FwdJob<NW, ESC, false> job;
+    FwdJob<NW, ESC, false, AUTO> job;
     job.a = &a;
-    run_persistent<FwdJob<NW, ESC, false>, SG_WALK_REFILL>(a.counter, a.nq, job);
+    run_persistent<FwdJob<NW, ESC, false, AUTO>, SG_WALK_REFILL>(a.counter, a.nq, job);
 }
 
 // hole avoidance (boundary_mode 1): the boundary handling needs more registers than the
@@ -466,14 +511,21 @@ thread_local char g_err[256];
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-    size_t counter, counts, sums, keys, perm, total;
+    size_t counter, counts, sums, keys, perm, esc, total;
 };
 
-// sort: 0 none, 1 by (mesh, start face), 2 by walk length
-WsLayout ws_layout(int64_t nF, int64_t nq, int sort) {
+// The 64-byte counter block (zeroed by every call): [0] the walk's tickets, [1] the mixed walk's
+// tickets, [2] the escalation list's length.
+#define SG_CTR_MIXED 1
+#define SG_CTR_ESC 2
+
+// sort: 0 none, 1 by (mesh, start face), 2 by walk length; esc: room for the escalation list of
+// the automatic precision
+WsLayout ws_layout(int64_t nF, int64_t nq, int sort, bool esc = false) {
     WsLayout L{};
     size_t o = 0;
     L.counter = o; o = align_up(o + 64, 256);
+    if (esc) { L.esc = o; o = align_up(o + sizeof(int32_t) * std::max<int64_t>(nq, 1), 256); }
     if (sort == 1) {
         int64_t nk = nF + 1;
         int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
@@ -497,6 +549,15 @@ WsLayout ws_layout(int64_t nF, int64_t nq, int sort) {
 #define SG_SORT_MIN_BATCH 65536
 // below this many queries the automatic kernel choice walks one thread per query
 #define SG_SMALL_BATCH 65536
+// The automatic precision (sg_opts.precision = 0) keeps a query in the FP32 walk while its walk
+// stays within the range where the FP32 walk's face sequences were measured equal to the
+// double-precision ones: below 256 crossings, no difference in 3.9M walks over icospheres, a
+// torus and heightfields with and without slivers (differences appear from 256 crossings, about
+// 3e-5 of the walks there, and grow with the crossing count).  A query whose length exceeds 96
+// l_ref (about 210-255 crossings on these meshes) goes to the mixed walk at the start; one whose
+// walk reaches 256 crossings is restarted there.
+#define SG_AUTO_FP32_LREF 96.0f
+#define SG_AUTO_FP32_CROSSINGS 256
 
 int l2_bytes() {
     static int cached = -1;
@@ -515,7 +576,7 @@ sg_opts resolve(const sg_opts *o, int64_t nq, int64_t nF) {
     if (o) r = *o;
     if (r.max_steps <= 0) r.max_steps = 1 << 20;
     if (r.block <= 0) r.block = 256;
-    if (r.precision <= 0) r.precision = 32;
+    if (r.precision < 0) r.precision = 0;  // 0: automatic (FP32, long walks in the mixed walk)
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
     if (r.tau_snap <= 0.f) r.tau_snap = r.precision >= 48 ? 1e-12f : 1e-6f;
     if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
@@ -525,12 +586,12 @@ sg_opts resolve(const sg_opts *o, int64_t nq, int64_t nF) {
     return r;
 }
 
-template <int NW>
+template <int NW, bool AUTO = false>
 cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
     if (o.kernel == SG_KERNEL_PLAIN) {
         int64_t grid = (a.nq + o.block - 1) / o.block;
-        if (o.fp64_escalate) k_walk_plain<NW, true><<<(unsigned)grid, o.block, 0, s>>>(a);
-        else k_walk_plain<NW, false><<<(unsigned)grid, o.block, 0, s>>>(a);
+        if (o.fp64_escalate) k_walk_plain<NW, true, AUTO><<<(unsigned)grid, o.block, 0, s>>>(a);
+        else k_walk_plain<NW, false, AUTO><<<(unsigned)grid, o.block, 0, s>>>(a);
         return cudaGetLastError();
     }
     int dev = 0, sms = 0, per = o.blocks_per_sm;
@@ -555,9 +616,9 @@ cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
     }
     int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(need, 1));
     if (o.fp64_escalate)
-        k_walk_persistent<NW, true><<<(unsigned)grid, o.block, 0, s>>>(a);
+        k_walk_persistent<NW, true, AUTO><<<(unsigned)grid, o.block, 0, s>>>(a);
     else
-        k_walk_persistent<NW, false><<<(unsigned)grid, o.block, 0, s>>>(a);
+        k_walk_persistent<NW, false, AUTO><<<(unsigned)grid, o.block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -581,7 +642,7 @@ void sg_opts_default(sg_opts *o) {
     o->workspace_bytes = 0;
     o->prof_events = nullptr;
     o->boundary_mode = 0;
-    o->precision = 32;
+    o->precision = 0;
 }
 
 const char *sg_status_string(sg_status s) {
@@ -678,6 +739,15 @@ sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int
         sg_mesh_destroy(m);
         return SG_ERR_OOM;
     }
+    // The FP64 geometry and double-float half-edge records of the mixed, double-float and FP64
+    // walks (192 B per face, 8 B per vertex), built now so that no walk call has to allocate.
+    sg_status st64 = sg_geom64_prepare(m, 0, true);
+    if (st64 == SG_OK && cudaStreamSynchronize(0) != cudaSuccess) st64 = SG_ERR_CUDA;
+    if (st64 != SG_OK) {
+        cudaGetLastError();
+        sg_mesh_destroy(m);
+        return st64;
+    }
     *out = m;
     return SG_OK;
 }
@@ -737,7 +807,8 @@ sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts 
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
     sg_opts r = resolve(o, nq, m->nF);
     if (r.sort < 0 || r.sort > 2) return SG_ERR_INVALID_ARG;
-    *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT ? r.sort : 0).total;
+    *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT ? r.sort : 0,
+                       r.precision == 0 && r.boundary_mode == 0).total;
     return SG_OK;
 }
 
@@ -760,9 +831,9 @@ FwdArgs fwd_args(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int
 // of queries by (mesh, start face).  Uses the caller's workspace or stream-ordered scratch
 // (*own_ws = the pointer to free after the walk).
 sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const sg_opts &r,
-                        int sort, cudaStream_t s, FwdArgs &a, void **own_ws) {
+                        int sort, cudaStream_t s, FwdArgs &a, void **own_ws, bool esc = false) {
     *own_ws = nullptr;
-    WsLayout L = ws_layout(m->nF, nq, sort);
+    WsLayout L = ws_layout(m->nF, nq, sort, esc);
     void *ws = nullptr;
     if (r.workspace) {
         if (r.workspace_bytes < L.total) return SG_ERR_OOM;
@@ -774,6 +845,10 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
     char *base = (char *)ws;
     a.counter = (int32_t *)(base + L.counter);
     if (cudaMemsetAsync(a.counter, 0, 64, s) != cudaSuccess) return SG_ERR_CUDA;
+    if (esc) {
+        a.esc_list = (int32_t *)(base + L.esc);
+        a.esc_count = a.counter + SG_CTR_ESC;
+    }
     if (sort == 2) {
         int32_t *perm = (int32_t *)(base + L.perm);
         sg_length_order(m, a.in, nq, (uint8_t *)(base + L.keys), (int32_t *)(base + L.counts), perm, s);
@@ -830,14 +905,19 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode != 0 && r.boundary_mode != 1) return SG_ERR_INVALID_ARG;
+    if (r.precision != 0 && r.precision != 32 && r.precision != 40 && r.precision != 48 && r.precision != 64)
+        return SG_ERR_INVALID_ARG;
+    // The automatic precision walks in FP32 and hands long walks to the mixed walk; hole avoidance
+    // has no mixed walk, so there it is the FP32 walk.
+    const bool autoprec = r.precision == 0 && r.boundary_mode == 0;
+    if (r.precision == 0) r.precision = 32;
     // A small batch fills the persistent grid once, so no lane would take a second query: the
     // automatic choice walks it one thread per query with the persistent kernel's arithmetic
     // (FP64 classification kept), without the queue and its counter reset.
     if (auto_kernel && nq < SG_SMALL_BATCH && r.precision == 32 && r.boundary_mode == 0 && r.sort == 0)
         r.kernel = SG_KERNEL_PLAIN;
     if (r.boundary_mode && r.kernel == SG_KERNEL_PLAIN) return SG_ERR_UNSUPPORTED;
-    if (r.precision != 32 && r.precision != 48 && r.precision != 64) return SG_ERR_INVALID_ARG;
-    if (r.precision >= 48 && (r.boundary_mode || r.kernel == SG_KERNEL_PLAIN)) return SG_ERR_UNSUPPORTED;
+    if (r.precision >= 40 && (r.boundary_mode || r.kernel == SG_KERNEL_PLAIN)) return SG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a = fwd_args(m, nq, mesh_id, face, bary, v, length, w, r);
     a.P.want_hash = out_hash != nullptr;
@@ -846,39 +926,56 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
 
     const bool persistent = r.kernel == SG_KERNEL_PERSISTENT;
     void *own_ws = nullptr;
-    if (persistent) {
-        sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.sort, s, a, &own_ws);
+    if (persistent || autoprec) {
+        sg_status st = prepare_queue(m, nq, mesh_id, face, r, persistent ? r.sort : 0, s, a, &own_ws, autoprec);
         if (st != SG_OK) {
             if (own_ws) cudaFreeAsync(own_ws, s);
             return st;
         }
     }
-    if (r.precision >= 48) {
-        // the FP64 geometry (and the double-float records) are a lazily built cache of the mesh
-        // (hence the const_cast)
-        sg_status st = sg_geom64_prepare(const_cast<sg_mesh *>(m), s, r.precision == 48);
+    if (r.precision >= 40 || autoprec) {
+        // the FP64 geometry and the double-float records (built with the mesh; re-derived here
+        // after a vertex update)
+        sg_status st = sg_geom64_prepare(const_cast<sg_mesh *>(m), s, r.precision <= 48);
         if (st != SG_OK) {
             if (own_ws) cudaFreeAsync(own_ws, s);
             return st;
         }
+    }
+    cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
+    if (r.precision >= 40) {
         SgFwdIO io{a.in, nq, out_face, out_bary, out_pos, out_dir, out_w, out_status, out_ncross, out_hash, a.perm,
-                   a.counter};
-        cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
+                   a.counter, nullptr};
         if (pev) cudaEventRecord(pev[0], s);
         cudaError_t e = sg_launch_walk64(m, io, n_w, r, s);
         if (pev) cudaEventRecord(pev[1], s);
         if (own_ws) cudaFreeAsync(own_ws, s);
         return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
     }
-    cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
+    if (autoprec) {
+        a.esc_lmax = SG_AUTO_FP32_LREF;
+        // the FP32 walk's step cap becomes the crossing budget; the caller's cap, if lower, stays
+        // final (esc_ncross = 0: nothing to hand on)
+        a.esc_ncross = r.max_steps > SG_AUTO_FP32_CROSSINGS ? SG_AUTO_FP32_CROSSINGS : 0;
+        a.P.max_steps = std::min(r.max_steps, SG_AUTO_FP32_CROSSINGS);
+    }
     if (pev) cudaEventRecord(pev[0], s);
     cudaError_t e;
     switch (n_w) {
-        case 0: e = launch_walk<0>(a, r, s); break;
-        case 1: e = launch_walk<1>(a, r, s); break;
-        case 2: e = launch_walk<2>(a, r, s); break;
-        case 3: e = launch_walk<3>(a, r, s); break;
-        default: e = launch_walk<4>(a, r, s); break;
+        case 0: e = autoprec ? launch_walk<0, true>(a, r, s) : launch_walk<0>(a, r, s); break;
+        case 1: e = autoprec ? launch_walk<1, true>(a, r, s) : launch_walk<1>(a, r, s); break;
+        case 2: e = autoprec ? launch_walk<2, true>(a, r, s) : launch_walk<2>(a, r, s); break;
+        case 3: e = autoprec ? launch_walk<3, true>(a, r, s) : launch_walk<3>(a, r, s); break;
+        default: e = autoprec ? launch_walk<4, true>(a, r, s) : launch_walk<4>(a, r, s); break;
+    }
+    if (e == cudaSuccess && autoprec) {
+        // the escalated queries, in the order the FP32 walk listed them, by the mixed walk; its
+        // grid reads the list's length from device memory (no host synchronisation)
+        sg_opts r40 = r;
+        r40.precision = 40;
+        SgFwdIO io{a.in, nq, out_face, out_bary, out_pos, out_dir, out_w, out_status, out_ncross, out_hash,
+                   a.esc_list, a.counter + SG_CTR_MIXED, a.esc_count};
+        e = sg_launch_walk64(m, io, n_w, r40, s);
     }
     if (pev) cudaEventRecord(pev[1], s);
     if (own_ws) cudaFreeAsync(own_ws, s);
@@ -901,7 +998,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
         return SG_ERR_INVALID_ARG;
     if (path_cap > 0 && !out_path_face) return SG_ERR_INVALID_ARG;
     sg_opts r = resolve(o, nq, m->nF);
-    if (r.boundary_mode || r.precision >= 48) return SG_ERR_UNSUPPORTED;
+    if (r.boundary_mode || r.precision >= 40) return SG_ERR_UNSUPPORTED;
     if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -996,7 +1093,7 @@ extern "C" sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int3
     if (need > SG_NOALLOC_SCRATCH_BYTES) return SG_ERR_OOM;
     // The FP64 geometry and the double-float records are allocated by the first call on a mesh
     // that asks for them; this entry point allocates nothing, so it requires them to exist.
-    if (r.precision >= 48 && (!m->d_rec64 || (r.precision == 48 && !m->d_half48))) return SG_ERR_UNSUPPORTED;
+    if (r.precision >= 40 && (!m->d_rec64 || (r.precision <= 48 && !m->d_half48))) return SG_ERR_UNSUPPORTED;
     r.workspace = scratch;
     r.workspace_bytes = SG_NOALLOC_SCRATCH_BYTES;
     return sg_exp_map(m, nq, mesh_id, face, bary, v, length, n_w, w, out_face, out_bary, out_pos, out_dir, out_w,

@@ -494,6 +494,138 @@ __device__ __forceinline__ bool step48(W64 &w, const P64 &P) {
     return done;
 }
 
+// ------------------------------------------------------------------ mixed-precision walk
+// The error of the FP32 walk that grows with the path is the direction's: each crossing rotates
+// the walking direction into the next edge frame with an FP32 edge vector and FP32 products, a
+// rounding of about one unit in the last place of the angle, and the rotations' errors add up
+// along the path while the position error they cause grows with the distance walked.  The error
+// of the position itself does not grow that way: every crossing recomputes the exit point from
+// the corners and the direction, so its rounding (about 1e-7 of the face size) enters once per
+// crossing and adds up like a random walk.  The mixed walk (precision 40) therefore keeps the
+// FP32 walk's arithmetic for the orientation tests, the exit point and the length, and carries
+// only the direction in double-float: its rotation into the next frame uses the double-float
+// edge vector of the double-float half-edge record (the record of the double-float walk, one
+// 32-byte sector) and double-float products.  The start (double-float) and the rare events
+// (FP64 face-frame code) are those of the double-float walk.
+//
+// Walker registers in the mixed half-edge mode: as in the double-float mode (px = the fraction s
+// along the entry edge, (dx, dy) the direction, L the remaining length, all packed pairs), with
+// only the high word of s and the pair L = Lh + Ll updated by FP32 steps.
+
+// a b + c d in double-float: the two exact products summed by one two-sum, all cross terms and
+// rounding errors gathered into the low part
+__device__ __forceinline__ DF df_dot2(DF a, DF b, DF c, DF d) {
+    const DF p = two_prod(a.hi, b.hi), q = two_prod(c.hi, d.hi);
+    DF s = two_sum(p.hi, q.hi);
+    float lo = s.lo + (p.lo + q.lo);
+    lo = fmaf(a.hi, b.lo, lo);
+    lo = fmaf(a.lo, b.hi, lo);
+    lo = fmaf(c.hi, d.lo, lo);
+    lo = fmaf(c.lo, d.hi, lo);
+    return fast_two_sum(s.hi, lo);
+}
+
+template <int NW>
+__device__ bool half40(W64 &w, const P64 &P) {
+    const DF L0 = dunpack(w.R.l01), cx = dunpack(w.R.x2x), cy = dunpack(w.R.x2y);
+    const DF dx = dunpack(w.dx), dy = dunpack(w.dy), Lr = dunpack(w.L);
+    const float sp = dunpack(w.px).hi;
+    const float l = L0.hi, x = sp * l, ddx = dx.hi, ddy = dy.hi;
+    float sA = ddy * x, sB = -ddy * (l - x), sC = fmaf(ddx, cy.hi, -ddy * (cx.hi - x));
+    if (fabsf(sC) < w.nearf) {
+        // the classification in FP64 from the double-float record and direction
+        w.st |= SG_ST_FP64;
+        const double X = (double)sp * df_to(L0), DX = df_to(dx), DY = df_to(dy);
+        sA = f32_keep_sign(DY * X);
+        sB = f32_keep_sign(-DY * (df_to(L0) - X));
+        sC = f32_keep_sign(DX * df_to(cy) - DY * (df_to(cx) - X));
+    }
+    const bool hit = fabsf(sC) <= w.snapf;
+    if (!hit && fabsf(sC) < w.nearf) w.st |= SG_ST_NEAR_VERTEX;
+    const bool right = sC > 0.f;
+    const float x0 = right ? l : cx.hi, y0 = right ? 0.f : cy.hi;
+    const float x1 = right ? cx.hi : 0.f, y1 = right ? cy.hi : 0.f;
+    float qx, qy, s;
+    if (hit) {
+        qx = cx.hi; qy = cy.hi;
+        s = right ? 1.f : 0.f;
+    } else {
+        const float s0 = right ? sB : sC, s1 = right ? sC : sA;
+        const float den = s0 - s1;
+        s = den != 0.f ? __fdividef(s0, den) : 0.5f;
+        s = fminf(fmaxf(s, 0.f), 1.f);
+        qx = fmaf(s, x1 - x0, x0);
+        qy = fmaf(s, y1 - y0, y0);
+    }
+    const float t = fmaxf(fmaf(qx - x, ddx, qy * ddy), 0.f);
+    const float Lf = Lr.hi + Lr.lo;
+    const int k = w.f - 3 * (w.f / 3);
+    if (t >= Lf) {
+        // final truncated in-face segment; the end point stays in the edge frame (SG48_END)
+        const float xe = fmaf(Lf, ddx, x), ye = Lf * ddy;
+        const float bcx = cx.hi - l;
+        const float cB = fabsf(bcx * ye - cy.hi * (xe - l)) * rsqrtf(fmaf(bcx, bcx, cy.hi * cy.hi));
+        const float cA = fabsf(cx.hi * ye - cy.hi * xe) * rsqrtf(fmaf(cx.hi, cx.hi, cy.hi * cy.hi));
+        if (fminf(fminf(fabsf(ye), cB), cA) <= w.nearf) w.st |= SG_ST_NEAR_EDGE;
+        w.px = dpack(DF{xe, 0.f});
+        w.py = dpack(DF{ye, 0.f});
+        w.L = 0.0;
+        w.mode = SG48_END;
+        return true;
+    }
+    // compensated L -= t (t < Lh + Ll: Dekker's fast two-sum gives the exact rounding error)
+    const float Lh = Lr.hi - t;
+    const DF Ln{Lh, Lr.lo + (-t - (Lh - Lr.hi))};
+    if (hit) {  // the apex is corner k+2 of the face: the straightest rule in FP64
+        leave48(w, P, cx, cy, dx, dy);
+        w.L = df_to(Ln);
+        return !vertex64<NW>(w, prv(k), P);
+    }
+    const int link = right ? w.R.n0 : w.R.n1;
+    if (link < 0) {  // boundary edge: the walk stops (Sec. 4)
+        leave48(w, P, DF{qx, 0.f}, DF{qy, 0.f}, dx, dy);
+        w.L = df_to(Ln);
+        w.st |= SG_ST_BOUNDARY;
+        return true;
+    }
+    const int hn = link >> 1, fl = link & 1;
+    // the exit edge vector in double-float: B -> C = (cx - l, cy), C -> A = -(cx, cy)
+    const DF ex = right ? df_sub(cx, L0) : df_neg(cx), ey = right ? cy : df_neg(cy);
+    const DF da = df_dot2(dx, ex, dy, ey);            // |e| (d . e_hat)
+    const DF dc = df_dot2(dx, ey, df_neg(dy), ex);    // |e| (d . n_out)
+    // one FP32 scale for both components keeps the direction's angle to double-float precision;
+    // its norm is 1 to FP32 precision, which only scales the next step's orientation tests
+    const float re = rsqrtf(fmaf(da.hi, da.hi, dc.hi * dc.hi));
+    w.px = dpack(DF{fl ? s : 1.f - s, 0.f});
+    w.dx = dpack(df_mul_f(fl ? da : df_neg(da), re));
+    w.dy = dpack(df_mul_f(dc, re));
+    w.L = dpack(Ln);
+    load48(w.R, P, hn);
+    w.f = hn;
+    if (fl) w.st ^= SG_PARITY_BIT;
+    w.ncross++;
+    hash64(w, hn / 3, P.want_hash);
+    return false;
+}
+
+template <int NW>
+__device__ __forceinline__ bool step40(W64 &w, const P64 &P) {
+    if (w.mode == SG48_HALF) {
+        if (w.steps >= P.max_steps) {
+            const DF L0 = dunpack(w.R.l01);
+            leave48(w, P, DF{dunpack(w.px).hi * L0.hi, 0.f}, DF{0.f, 0.f}, dunpack(w.dx), dunpack(w.dy));
+            w.L = 0.0;
+            w.st |= SG_ST_MAX_STEPS;
+            return true;
+        }
+        w.steps++;
+        return half40<NW>(w, P);
+    }
+    const bool done = step64<NW>(w, P);
+    if (!done && w.mode < 3) enter48(w, P);
+    return done;
+}
+
 struct Fwd64Args {
     P64 P;
     QueryIn in;
@@ -505,10 +637,13 @@ struct Fwd64Args {
     uint64_t *out_hash;
     const int32_t *__restrict__ perm;
     int32_t *counter;
+    const int32_t *n_dev;
 };
 
-template <int NW, bool DFW = false>
+// PREC 64: the FP64 walk; 48: the double-float walk; 40: the mixed walk
+template <int NW, int PREC = 64>
 struct Job64 {
+    static constexpr bool DFW = PREC != 64;
     const Fwd64Args *a;
     W64 w;
     double cc[NW > 0 ? NW : 1], cs[NW > 0 ? NW : 1];
@@ -656,7 +791,9 @@ struct Job64 {
         w.mode = SG48_HALF;
         return 1;
     }
-    __device__ __forceinline__ bool step() { return DFW ? step48<NW>(w, a->P) : step64<NW>(w, a->P); }
+    __device__ __forceinline__ bool step() {
+        return PREC == 40 ? step40<NW>(w, a->P) : (PREC == 48 ? step48<NW>(w, a->P) : step64<NW>(w, a->P));
+    }
     // The end of a double-float walk that stopped inside a face in the half-edge mode: the
     // outputs (float32) from the double-float end point, with FP32 rotations and frames.
     __device__ __forceinline__ void finish48() {
@@ -696,7 +833,8 @@ struct Job64 {
                 o[2] = u1 * fa.z + u2 * fb.y;
             }
         }
-        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u);
+        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u) |
+                          (PREC == 40 ? SG_ST_MIXED : 0u);
         if (A.out_ncross) A.out_ncross[q] = w.ncross;
         if (A.out_hash) A.out_hash[q] = w.hash;
     }
@@ -733,7 +871,8 @@ struct Job64 {
                 o[2] = (float)(u1 * fr[2] + u2 * fr[5]);
             }
         }
-        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u);
+        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u) |
+                          (PREC == 40 ? SG_ST_MIXED : 0u);
         if (A.out_ncross) A.out_ncross[q] = w.ncross;
         if (A.out_hash) A.out_hash[q] = w.hash;
     }
@@ -753,9 +892,20 @@ __global__ void __launch_bounds__(128) k_walk64(Fwd64Args a) {
 #endif
 template <int NW>
 __global__ void __launch_bounds__(128, SG_WALK48_MINB) k_walk48(Fwd64Args a) {
-    Job64<NW, true> job;
+    Job64<NW, 48> job;
     job.a = &a;
-    run_persistent(a.counter, a.nq, job);
+    run_persistent(a.counter, a.nq, job, a.n_dev);
+}
+
+// resident blocks per SM the mixed walk is compiled for
+#ifndef SG_WALK40_MINB
+#define SG_WALK40_MINB 5
+#endif
+template <int NW>
+__global__ void __launch_bounds__(128, SG_WALK40_MINB) k_walk40(Fwd64Args a) {
+    Job64<NW, 40> job;
+    job.a = &a;
+    run_persistent(a.counter, a.nq, job, a.n_dev);
 }
 
 // Double-float half-edge records from the FP64 face shapes, in the layout of the FP32 half-edge
@@ -883,7 +1033,7 @@ cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const
     a.in = io.in; a.nq = io.nq;
     a.out_face = io.out_face; a.out_bary = io.out_bary; a.out_pos = io.out_pos; a.out_dir = io.out_dir;
     a.out_w = io.out_w; a.out_status = io.out_status; a.out_ncross = io.out_ncross; a.out_hash = io.out_hash;
-    a.perm = io.perm; a.counter = io.counter;
+    a.perm = io.perm; a.counter = io.counter; a.n_dev = io.n_dev;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -896,7 +1046,15 @@ cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const
         const int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>((io.nq + 127) / 128, 1));
         kern<<<(unsigned)grid, 128, 0, s>>>(a);
     };
-    if (r.precision == 48) {
+    if (r.precision == 40) {
+        switch (n_w) {
+            case 0: go(k_walk40<0>); break;
+            case 1: go(k_walk40<1>); break;
+            case 2: go(k_walk40<2>); break;
+            case 3: go(k_walk40<3>); break;
+            default: go(k_walk40<4>); break;
+        }
+    } else if (r.precision == 48) {
         switch (n_w) {
             case 0: go(k_walk48<0>); break;
             case 1: go(k_walk48<1>); break;

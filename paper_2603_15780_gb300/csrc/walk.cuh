@@ -758,6 +758,7 @@ struct SgFwdIO {
     uint64_t *out_hash;
     const int32_t *perm;
     int32_t *counter;
+    const int32_t *n_dev;  // task count in device memory (the escalation list's), or NULL: nq
 };
 sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s, bool half48);
 // Length order of a batch (exp_map.cu): perm[0 .. nq) = the queries longest walk first, in
@@ -907,7 +908,10 @@ __device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
 #endif
 
 template <class Job, int REFILL = SG_REFILL_LANES>
-__device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job) {
+__device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job, const int32_t *n_dev = nullptr) {
+    // n_dev: the task count as written by an earlier kernel on the stream (an upper bound n)
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    if (n <= 0) return;  // an empty list: no ticket to take
     bool live = false, pending = false, exhausted = false;
     const unsigned FULL = 0xffffffffu;
     while (true) {

@@ -30,7 +30,7 @@ def test_defaults_and_status_strings():
     import paper_2603_15780_gb300 as sg
     o = sg.default_opts()
     assert o.max_steps == 1 << 20 and o.block == 256 and o.fp64_escalate == 1
-    assert abs(o.tau_near - 1e-4) < 1e-9 and o.tau_snap == 0.0 and o.precision == 32  # snap: 1e-6 (FP32) / 1e-12 (FP64)
+    assert abs(o.tau_near - 1e-4) < 1e-9 and o.tau_snap == 0.0 and o.precision == 0  # snap: 1e-6 (FP32, mixed) / 1e-12 (FP64); precision: automatic
     assert sg.lib().sg_status_string(2) == b"non-manifold mesh"
     assert sg.lib().sg_version().startswith(b"sgeo")
 

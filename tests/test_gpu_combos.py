@@ -51,7 +51,7 @@ def test_hole_avoidance_in_a_batch_of_closed_and_holey_meshes():
     assert ((gpu["status"][2000:] & oracle.HOLE) != 0).mean() > 0.2
 
 
-@pytest.mark.parametrize("prec", [64, 48], ids=["fp64", "double-float"])
+@pytest.mark.parametrize("prec", [64, 48, 40], ids=["fp64", "double-float", "mixed"])
 def test_fp64_walk_on_a_klein_bottle(prec):
     X, F = meshgen.klein_bottle(64, 32)
     X32 = parity.as_f32(X)

@@ -33,10 +33,11 @@ def _bad_batch():
 
 
 VARIANTS = [dict(), dict(kernel=1), dict(sort=0), dict(sort=2), dict(boundary_mode=1), dict(precision=64),
-            dict(precision=48)]
+            dict(precision=48), dict(precision=40), dict(precision=32)]
 
 
-@pytest.mark.parametrize("kw", VARIANTS, ids=["persistent", "plain", "unsorted", "length-order", "hole", "fp64", "double-float"])
+@pytest.mark.parametrize("kw", VARIANTS, ids=["persistent", "plain", "unsorted", "length-order", "hole", "fp64", "double-float",
+                                             "mixed", "fp32"])
 def test_bad_queries_are_invalid_and_the_rest_walk(kw):
     X, F, q, bad = _bad_batch()
     X32 = parity.as_f32(X)

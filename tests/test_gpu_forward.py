@@ -159,11 +159,12 @@ def test_torus_subset_two_carried_vectors():
 
 
 def test_heightfield_slivers_and_boundary():
-    """Workload-4 mesh (1449^2 heightfield, 10% sliver vertices, ~1.4k crossings per walk):
-    boundary stops and FP64-escalated classification of an FP32 walk.  Over this many
-    crossings the FP32 state error reaches the near-vertex band, so a walk can pass a vertex
-    on the other side than the FP64 oracle; the test bounds how often that happens and the
-    end-point error distribution (the statistics are printed)."""
+    """Workload-4 mesh (1449^2 heightfield, 10% sliver vertices, ~1.8k crossings per walk) at the
+    full parity bar with the default options: face sequences bit-exact on every query neither side
+    flags, end points within 1e-5 of the bbox diagonal.  The FP32 walk's accumulated direction
+    error passes vertices on the wrong side beyond ~256 crossings, so the automatic precision walks
+    those queries in the mixed walk (SG_ST_MIXED); the escalated and flagged fractions are printed
+    and bounded, and the boundary stops must agree."""
     wl = meshgen.workload(4, scale=20000 / 16777216)
     X, F = wl.single
     X32 = parity.as_f32(X)
@@ -171,23 +172,39 @@ def test_heightfield_slivers_and_boundary():
     gpu = parity.run_gpu(mesh, wl.queries, 0)
     ref, _ = parity.run_oracle(X32, F, wl.queries, 0)
     diag = meshgen.bbox_diag(X)
-    st = gpu["status"] | ref["status"]
-    flagged = (st & parity.FLAGS) != 0
-    same = (gpu["hash"] == ref["hash"]) & (gpu["face"] == ref["face"])
-    dpos = np.linalg.norm(gpu["pos"] - ref["pos"], axis=1)
-    within = dpos <= 1e-5 * diag
+    r = parity.compare(gpu, ref, diag, 0, max_flagged=0.25, what="heightfield, automatic precision")
+    mixed = (gpu["status"] & 4096) != 0
     nc = ref["ncross"]
-    stats = {"flagged": flagged.mean(), "same_faces_unflagged": same[~flagged].mean(),
-             "pos_within_1e-5_diag": within.mean(), "median_pos_err_over_diag": np.median(dpos) / diag,
-             "p99_pos_err_over_diag": np.quantile(dpos, 0.99) / diag, "mean_ncross": nc.mean(),
-             "boundary": ((ref["status"] & oracle.BOUNDARY) != 0).mean(),
-             "fp64_escalated": ((gpu["status"] & 32) != 0).mean()}
-    print("heightfield", {k: float(v) for k, v in stats.items()})
+    stats = dict(r, escalated=float(mixed.mean()), mean_ncross=float(nc.mean()),
+                 boundary=float(((ref["status"] & oracle.BOUNDARY) != 0).mean()),
+                 fp32_max_ncross=int(gpu["ncross"][~mixed].max()))
+    print("heightfield", stats)
     assert ((ref["status"] & oracle.BOUNDARY) != 0).mean() > 0.3
-    assert (((gpu["status"] ^ ref["status"]) & oracle.BOUNDARY) != 0).mean() < 0.01
-    short = (nc < 100) & ~flagged
-    assert same[short].mean() > 0.99
-    assert np.median(dpos) <= 1e-5 * diag
+    # every walk the FP32 walk kept stayed below its crossing budget, and the long ones escalated
+    assert gpu["ncross"][~mixed].max() < 256
+    assert mixed[gpu["ncross"] >= 256].all()
+    assert 0.5 < mixed.mean() < 1.0
+
+
+def test_heightfield_fp32_walk_diverges_beyond_its_range():
+    """The same sample with the plain FP32 walk (precision 32): below 256 crossings its face
+    sequences are bit-exact on unflagged queries; beyond, they differ on a few percent -- the
+    measurement that sets the automatic precision's crossing budget."""
+    wl = meshgen.workload(4, scale=20000 / 16777216)
+    X, F = wl.single
+    X32 = parity.as_f32(X)
+    mesh = sg().Mesh(X32, F)
+    gpu = parity.run_gpu(mesh, wl.queries, 0, precision=32)
+    ref, _ = parity.run_oracle(X32, F, wl.queries, 0)
+    flagged = ((gpu["status"] | ref["status"]) & parity.FLAGS) != 0
+    same = (gpu["hash"] == ref["hash"]) & (gpu["face"] == ref["face"])
+    nc = ref["ncross"]
+    short = (nc < 256) & ~flagged
+    long_ = (nc >= 1000) & ~flagged
+    print("fp32 heightfield: unflagged mismatches below 256 crossings", int((~same[short]).sum()), "of", int(short.sum()),
+          "; from 1000 crossings", int((~same[long_]).sum()), "of", int(long_.sum()))
+    assert same[short].all()
+    assert (~same[long_]).mean() > 0.02
 
 
 def test_multi_mesh_batch():
@@ -196,13 +213,19 @@ def test_multi_mesh_batch():
     mesh = sg().Mesh([(parity.as_f32(X), F) for X, F in wl.meshes])
     q = wl.queries
     gpu = parity.run_gpu(mesh, q, 0, mesh_id=q.mesh_id)
+    # A walk is flagged when it passes within tau_near l_ref = 1e-4 l_ref of a vertex, which
+    # happens with probability about 1.5e-4 per crossing on these meshes: each mesh's flagged
+    # fraction is bounded by 2e-4 times its mean crossing count (plus 1% for small samples).
     for m in (0, 1, 2, 17, 40, 63):
         sel = np.nonzero(q.mesh_id == m)[0]
         X, F = wl.meshes[m]
         X32 = parity.as_f32(X)
         ref, _ = parity.run_oracle(X32, F, q.take(sel), 0)
         sub = {k: v[sel] for k, v in gpu.items()}
-        parity.compare(sub, ref, meshgen.bbox_diag(X), 0, what=f"mesh {m}", max_flagged=0.2)
+        bound = 2e-4 * float(ref["ncross"].mean()) + 0.01
+        r = parity.compare(sub, ref, meshgen.bbox_diag(X), 0, what=f"mesh {m}", max_flagged=bound)
+        print(f"mesh {m}: {len(sel)} queries, mean crossings {ref['ncross'].mean():.0f}, flagged {r['flagged']:.4f} "
+              f"(bound {bound:.4f}), mixed walk {((sub['status'] & 4096) != 0).mean():.3f}")
 
 
 def test_edge_cases():

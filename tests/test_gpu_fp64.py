@@ -24,6 +24,8 @@ def sg():
 
 
 PRECISIONS = pytest.mark.parametrize("prec", [64, 48], ids=["fp64", "double-float"])
+# with the mixed walk (FP32 positions and orientation tests, double-float direction)
+ALL_WIDE = pytest.mark.parametrize("prec", [64, 48, 40], ids=["fp64", "double-float", "mixed"])
 
 
 @PRECISIONS
@@ -35,7 +37,7 @@ def test_fp64_walk_on_the_sliver_heightfield(prec):
     q = wl.queries
     tau = 1e-8
     g64 = parity.run_gpu(mesh, q, 0, precision=prec, tau_near=tau)
-    g32 = parity.run_gpu(mesh, q, 0, tau_near=tau)
+    g32 = parity.run_gpu(mesh, q, 0, tau_near=tau, precision=32)
     ref, _ = parity.run_oracle(X32, F, q, 0, tau_near=tau)
     diag = meshgen.bbox_diag(X)
     flag64 = ((g64["status"] | ref["status"]) & parity.FLAGS) != 0
@@ -53,7 +55,7 @@ def test_fp64_walk_on_the_sliver_heightfield(prec):
     assert (~same32[~flag32]).sum() > 100
 
 
-@PRECISIONS
+@ALL_WIDE
 def test_fp64_walk_workload0_parity_with_carried_vectors(prec):
     wl = meshgen.workload(0)
     X, F = wl.single
@@ -106,7 +108,7 @@ def test_double_float_walk_on_a_multi_mesh_batch():
                        what=f"double-float mesh {m}", pos_tol=1e-6, dir_tol=1e-5)
 
 
-@PRECISIONS
+@ALL_WIDE
 def test_fp64_geometry_follows_vertex_updates(prec):
     rng = np.random.default_rng(91)
     XA, F = meshgen.icosphere(4, 0.004, rng)
@@ -123,7 +125,7 @@ def test_fp64_geometry_follows_vertex_updates(prec):
         assert np.abs(moved[k] - fresh[k]).max() <= 1e-6, k
 
 
-@PRECISIONS
+@ALL_WIDE
 def test_fp64_rejected_where_unsupported(prec):
     wl = meshgen.workload(0, scale=0.05)
     X, F = wl.single

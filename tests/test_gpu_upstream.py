@@ -157,8 +157,9 @@ def test_grad_V_of_end_barycentrics_matches_central_differences():
         r = bwd(mesh, q, out, "ep", g_bary=gbm, want_grad_V=True)
         lhs = float(np.sum(r["grad_V"] * dX))
         rhs = float(np.sum(fd[keep]))
-        scale = float(np.sum(np.abs(fd[keep])))
-        assert abs(lhs - rhs) <= 2e-3 * scale, (lhs, rhs, scale)
+        scale = float(np.linalg.norm(fd[keep]))
+        print("grad_V through g_bary: err / |fd| =", abs(lhs - rhs) / scale)
+        assert abs(lhs - rhs) <= 1e-3 * scale, (lhs, rhs, scale)
 
 
 def _oracle_chain(om, X, F, face, bary, A, K):
@@ -217,4 +218,5 @@ def test_k_step_exp_positions_and_field_gradient():
     loss.backward()
     lhs = At.grad.cpu().numpy().astype(np.float64)
     rhs = fd[:, :, keep].sum(-1)
+    print("K-step field gradient: max |gpu - fd| / max |fd| =", np.abs(lhs - rhs).max() / np.abs(rhs).max())
     assert np.abs(lhs - rhs).max() <= 2e-2 * np.abs(rhs).max(), (lhs, rhs)

@@ -4,9 +4,9 @@ framework's pool, or loops where a cudaMalloc/cudaFree would synchronise the dev
 
 It is called here through the C ABI and must reproduce sg_exp_map's results on calls in a
 row on the persistent kernel (each call finds the previous call's leftovers in the shared
-scratch array: queue counter, sort histogram, permutation), refuse the double-float walk on
-a mesh whose double-float records do not exist yet (creating them would allocate), and
-reject a batch too large for its fixed scratch without launching anything.
+scratch array: queue counter, sort histogram, permutation), run the double-float walk and
+the automatic precision (whose escalation list lives in the same array) on the double-float
+records built with the mesh, and reject a batch too large for its fixed scratch without launching anything.
 This file is collected last so a failure here cannot hide the other tests' results.
 """
 import ctypes as C
@@ -82,29 +82,30 @@ def test_noalloc_matches_exp_map_on_two_calls():
         _check_same(out, ref, diag, f"call {call} {kw}")
 
 
-def test_noalloc_double_float_needs_the_prepared_mesh():
-    """Precision 48 walks on double-float records that the first sg_exp_map call with that
-    precision allocates on the mesh: before it, the allocation-free entry point refuses
-    (SG_ERR_UNSUPPORTED) instead of allocating; after it, it matches sg_exp_map."""
+def test_noalloc_wider_precisions():
+    """The double-float walk (precision 48) and the automatic precision walk on double-float
+    records that sg_mesh_create builds with the mesh, so the allocation-free entry point runs
+    them without allocating; each call matches sg_exp_map.  The automatic precision's batch
+    includes walks beyond the FP32 walk's crossing budget, which go through the escalation list
+    in the shared array."""
     import torch
     import paper_2603_15780_gb300 as sg
-    wl = meshgen.workload(0)
-    X, F = wl.single
+    X, F = meshgen.icosphere(4)
     mesh = sg.Mesh(parity.as_f32(X), F)
-    q = wl.queries
+    rng = np.random.default_rng(78)
+    q = meshgen.sample_queries(X, F, 70000, rng, 0.0, 12.0, 1)
     face = torch.tensor(q.face, device="cuda")
     bary = torch.tensor(parity.as_f32(q.bary), device="cuda")
     v = torch.tensor(parity.as_f32(q.v), device="cuda")
     w = torch.tensor(parity.as_f32(q.w[:, :1]), device="cuda")
-    opts = sg.default_opts(kernel=2, precision=48)
-    rc, _ = _noalloc(sg, mesh, face, bary, v, w, 1, opts, torch)
-    torch.cuda.synchronize()
-    assert rc == 6
-    ref = sg.exp_map(mesh, face, bary, v, w, want_hash=True, kernel=2, precision=48)
-    rc, out = _noalloc(sg, mesh, face, bary, v, w, 1, sg.default_opts(kernel=2, precision=48), torch)
-    torch.cuda.synchronize()
-    assert rc == 0
-    _check_same(out, ref, meshgen.bbox_diag(X), "precision 48")
+    for kw in (dict(kernel=2, precision=48), dict(precision=0), dict(precision=0, sort=1)):
+        ref = sg.exp_map(mesh, face, bary, v, w, want_hash=True, **kw)
+        rc, out = _noalloc(sg, mesh, face, bary, v, w, 1, sg.default_opts(**kw), torch)
+        torch.cuda.synchronize()
+        assert rc == 0, f"{kw}: status {rc}"
+        if kw["precision"] == 0:
+            assert ((out["status"] & 4096) != 0).any(), "no walk escalated"
+        _check_same(out, ref, meshgen.bbox_diag(X), str(kw))
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
@@ -121,8 +122,9 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     rc, _ = _noalloc(sg, mesh, face, bary, v, None, 0, opts, torch)
     torch.cuda.synchronize()
     assert rc == 5                # SG_ERR_OOM: nothing launched
-    # without the sort the scratch is a single counter: the same batch is accepted
-    opts0 = sg.default_opts(sort=0)
+    # without the sort (and without the automatic precision's escalation list) the scratch is a
+    # single counter: the same batch is accepted
+    opts0 = sg.default_opts(sort=0, precision=32)
     rc, out = _noalloc(sg, mesh, face, bary, v, None, 0, opts0, torch)
     torch.cuda.synchronize()
     assert rc == 0
