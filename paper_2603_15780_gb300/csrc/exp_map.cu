@@ -50,6 +50,9 @@ struct FwdArgs {
     int32_t *esc_list, *esc_count;
     float esc_lmax;
     int32_t esc_ncross;
+    // when a query order routed the long queries to the mixed walk: the head of perm it takes
+    // (*route_n queries; the persistent FP32 walk's ticket counter starts there)
+    const int32_t *route_n;
 };
 
 // Appends query q to the escalation list (warp-aggregated: one atomic per calling warp).
@@ -117,28 +120,20 @@ __global__ void __launch_bounds__(256) k_walk_plain(FwdArgs a) {
     walker_finish<NW>(a, q, w, cw);
 }
 
-// AUTO: the automatic precision -- a query leaves this FP32 walk for the mixed walk when its
-// length exceeds esc_lmax l_ref at the start, or when its walk reaches the crossing budget.  The
-// budget is the walk's step cap (P.max_steps, set to it by the host; a crossing is a step, so
-// no walk kept here crosses more edges than that), which costs no test of its own per step; a
-// walk stopped by it is handed on (esc_ncross != 0) unless the caller's own cap is that low.
+// AUTO: the automatic precision -- the query order gave the long queries to the mixed walk, and
+// a query leaves this FP32 walk for the mixed walk when its walk reaches the crossing budget.  The
+// budget is the walk's step cap (P.max_steps, set to it by the host; a crossing is a step, so no
+// walk kept here crosses more edges than that), which costs no test of its own per step; a walk
+// stopped by it is handed on (esc_ncross != 0) unless the caller's own cap is that low.
 template <int NW, bool ESC, bool HOLE = false, bool AUTO = false>
 struct FwdJob {
     const FwdArgs *a;
     Walker w;
     Carry<NW> cw;
     int64_t q;
-    bool esc;  // handed to the mixed walk: nothing to write here
     __device__ __forceinline__ bool init(int64_t t) {
         q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
-        esc = false;
-        const bool live = walker_init<NW>(a->P, a->in, q, w, cw);
-        if (AUTO && live && w.Lh > a->esc_lmax * w.lref) {
-            esc = true;
-            escalate(*a, q);
-            return false;
-        }
-        return live;
+        return walker_init<NW>(a->P, a->in, q, w, cw);
     }
     __device__ __forceinline__ bool step() {
         if (HOLE) {
@@ -152,11 +147,12 @@ struct FwdJob {
         return walker_step<ESC, HOLE>(w, a->P);
     }
     __device__ __forceinline__ void finish() {
-        if (AUTO && !esc && a->esc_ncross && (w.st & SG_ST_MAX_STEPS)) {
-            esc = true;
-            escalate(*a, q);
+        if (AUTO && a->esc_ncross && (w.st & SG_ST_MAX_STEPS)) {
+            // (one atomic per such query: these are the walks that outran their predicted
+            // length, and an aggregated append here costs the walk registers)
+            a->esc_list[atomicAdd(a->esc_count, 1)] = (int32_t)q;
+            return;
         }
-        if (AUTO && esc) return;
         walker_finish<NW>(*a, q, w, cw);
     }
 };
@@ -334,33 +330,45 @@ __global__ void __launch_bounds__(256, 4) k_trace_persistent(FwdArgs a, TraceOut
 }
 
 // ------------------------------------------------------------------ start-face counting sort
-__global__ void k_sort_keys_hist(int64_t nq, const int32_t *__restrict__ mesh_id, const int32_t *__restrict__ face,
-                                 const int32_t *__restrict__ face_off, int32_t n_mesh, int32_t nF,
-                                 int32_t *__restrict__ counts) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
-        int m = mesh_id ? mesh_id[i] : 0;
-        int key = nF;  // invalid queries go last
-        if (m >= 0 && m < n_mesh) {
-            int lo = face_off[m], hi = face_off[m + 1];
-            int f = face[i];
-            if (f >= 0 && f < hi - lo) key = lo + f;
-        }
-        atomicAdd(counts + key, 1);
-    }
+// The length a query walks, as the query orders see it: the given length, else |v| (the ambient
+// norm, an upper bound of the projected length).
+__device__ __forceinline__ float query_length(const QueryIn &in, int64_t i) {
+    if (in.length) return __ldg(in.length + i);
+    const float x = __ldg(in.v + 3 * i), y = __ldg(in.v + 3 * i + 1), z = __ldg(in.v + 3 * i + 2);
+    return sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
 }
 
-__global__ void k_sort_scatter(int64_t nq, const int32_t *__restrict__ mesh_id, const int32_t *__restrict__ face,
-                               const int32_t *__restrict__ face_off, int32_t n_mesh, int32_t nF,
+// Key of query i: its global start face; nF for an invalid query.  With the automatic precision
+// (esc_lmax > 0) the queries longer than esc_lmax l_ref, which the mixed walk takes, keep their
+// start face as key and form the permutation's head; the others get nF + their start face, and an
+// invalid query 2 nF.
+__device__ __forceinline__ int face_key(const QueryIn &in, const int32_t *__restrict__ face_off,
+                                        const float *__restrict__ lref, int32_t nF, float esc_lmax, int64_t i) {
+    const int inval = esc_lmax > 0.f ? 2 * nF : nF;
+    const int m = in.mesh_id ? __ldg(in.mesh_id + i) : 0;
+    if (m < 0 || m >= in.n_mesh) return inval;
+    const int lo = __ldg(face_off + m), hi = __ldg(face_off + m + 1);
+    const int f = __ldg(in.face + i);
+    if (f < 0 || f >= hi - lo) return inval;
+    int key = lo + f;
+    if (esc_lmax > 0.f && !(query_length(in, i) > esc_lmax * __ldg(lref + m))) key += nF;
+    return key;
+}
+
+__global__ void k_sort_keys_hist(int64_t nq, QueryIn in, const int32_t *__restrict__ face_off,
+                                 const float *__restrict__ lref, int32_t nF, float esc_lmax,
+                                 int32_t *__restrict__ counts) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(counts + face_key(in, face_off, lref, nF, esc_lmax, i), 1);
+}
+
+// after the scatter offsets[k] is the end of bucket k (with the automatic precision offsets[nF - 1]
+// is the number of routed queries at the head)
+__global__ void k_sort_scatter(int64_t nq, QueryIn in, const int32_t *__restrict__ face_off,
+                               const float *__restrict__ lref, int32_t nF, float esc_lmax,
                                int32_t *__restrict__ offsets, int32_t *__restrict__ perm) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
-        int m = mesh_id ? mesh_id[i] : 0;
-        int key = nF;
-        if (m >= 0 && m < n_mesh) {
-            int lo = face_off[m], hi = face_off[m + 1];
-            int f = face[i];
-            if (f >= 0 && f < hi - lo) key = lo + f;
-        }
-        int pos = atomicAdd(offsets + key, 1);
+        const int pos = atomicAdd(offsets + face_key(in, face_off, lref, nF, esc_lmax, i), 1);
         perm[pos] = (int32_t)i;
     }
 }
@@ -369,30 +377,30 @@ __global__ void k_sort_scatter(int64_t nq, const int32_t *__restrict__ mesh_id, 
 // Walks of similar length end together, so a warp whose lanes hold them waits less with idle
 // lanes before it refills.  Key: an eighth of an octave of L / l_ref per bucket, longest walks
 // first (the short ones then fill the tail of the queue); invalid queries last.  L is the given
-// length, else |v| (its ambient norm: a key, not the walked length).
-__device__ __forceinline__ int length_key(const QueryIn &in, const float *__restrict__ lref, int64_t i) {
+// length, else |v| (its ambient norm: a key, not the walked length).  With the automatic precision
+// (esc_lmax > 0) bucket 0 holds the queries longer than esc_lmax l_ref, which the mixed walk
+// takes: the permutation's head; the length buckets then start at 1.
+__device__ __forceinline__ int length_key(const QueryIn &in, const float *__restrict__ lref, int64_t i,
+                                          float esc_lmax) {
     const int m = in.mesh_id ? __ldg(in.mesh_id + i) : 0;
     if (m < 0 || m >= in.n_mesh) return SG_LBUCKETS - 1;
-    float L;
-    if (in.length) {
-        L = __ldg(in.length + i);
-    } else {
-        const float x = __ldg(in.v + 3 * i), y = __ldg(in.v + 3 * i + 1), z = __ldg(in.v + 3 * i + 2);
-        L = sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
-    }
+    const float L = query_length(in, i);
     const float lr = __ldg(lref + m);
     if (!(L > 0.f) || !(L <= 3.0e38f) || !(lr > 0.f)) return SG_LBUCKETS - 1;
+    if (esc_lmax > 0.f && L > esc_lmax * lr) return 0;
     const float t = fminf(fmaxf(fmaf(8.f, __log2f(L / lr), 128.f), 0.f), (float)(SG_LBUCKETS - 2));
-    return SG_LBUCKETS - 2 - (int)t;
+    const int k = SG_LBUCKETS - 2 - (int)t;
+    return esc_lmax > 0.f ? max(k, 1) : k;
 }
 
 __global__ void __launch_bounds__(256) k_lorder_hist(int64_t nq, QueryIn in, const float *__restrict__ lref,
-                                                     uint8_t *__restrict__ keys, int32_t *__restrict__ counts) {
+                                                     float esc_lmax, uint8_t *__restrict__ keys,
+                                                     int32_t *__restrict__ counts) {
     __shared__ int32_t h[SG_LBUCKETS];
     for (int b = threadIdx.x; b < SG_LBUCKETS; b += blockDim.x) h[b] = 0;
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
-        const int k = length_key(in, lref, i);
+        const int k = length_key(in, lref, i, esc_lmax);
         keys[i] = (uint8_t)k;
         atomicAdd(&h[k], 1);
     }
@@ -527,7 +535,7 @@ WsLayout ws_layout(int64_t nF, int64_t nq, int sort, bool esc = false) {
     L.counter = o; o = align_up(o + 64, 256);
     if (esc) { L.esc = o; o = align_up(o + sizeof(int32_t) * std::max<int64_t>(nq, 1), 256); }
     if (sort == 1) {
-        int64_t nk = nF + 1;
+        int64_t nk = esc ? 2 * nF + 1 : nF + 1;
         int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
         L.counts = o; o = align_up(o + sizeof(int32_t) * nk, 256);
         L.sums = o; o = align_up(o + sizeof(int32_t) * ntiles, 256);
@@ -849,41 +857,50 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
         a.esc_list = (int32_t *)(base + L.esc);
         a.esc_count = a.counter + SG_CTR_ESC;
     }
+    // with the automatic precision the orders route the long queries to the mixed walk (the
+    // length order's head, the start-face order's tail)
+    const float lmax = esc ? SG_AUTO_FP32_LREF : 0.f;
     if (sort == 2) {
         int32_t *perm = (int32_t *)(base + L.perm);
-        sg_length_order(m, a.in, nq, (uint8_t *)(base + L.keys), (int32_t *)(base + L.counts), perm, s);
+        int32_t *counts = (int32_t *)(base + L.counts);
+        sg_length_order(m, a.in, nq, (uint8_t *)(base + L.keys), counts, perm, s, lmax);
         a.perm = perm;
+        if (esc) a.route_n = counts;  // bucket 0: counts[0] queries
     } else if (sort == 1) {
         int32_t *counts = (int32_t *)(base + L.counts);
         int32_t *sums = (int32_t *)(base + L.sums);
         int32_t *perm = (int32_t *)(base + L.perm);
-        int64_t nk = m->nF + 1;
+        int64_t nk = esc ? 2 * m->nF + 1 : m->nF + 1;
         int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
         cudaMemsetAsync(counts, 0, sizeof(int32_t) * nk, s);
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         int g = (int)std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 8);
-        k_sort_keys_hist<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts);
+        k_sort_keys_hist<<<g, 256, 0, s>>>(nq, a.in, m->d_face_off, m->d_lref, (int32_t)m->nF, lmax, counts);
         k_scan_tiles<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(counts, nk, sums);
         k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums, ntiles);
         k_scan_add<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(counts, nk, sums);
-        k_sort_scatter<<<g, 256, 0, s>>>(nq, mesh_id, face, m->d_face_off, m->n_mesh, (int32_t)m->nF, counts, perm);
+        k_sort_scatter<<<g, 256, 0, s>>>(nq, a.in, m->d_face_off, m->d_lref, (int32_t)m->nF, lmax, counts, perm);
         a.perm = perm;
+        if (esc) a.route_n = counts + m->nF - 1;  // the head: up to the end of bucket nF - 1
     }
+    // the FP32 walk starts its tickets after the routed head
+    if (a.route_n && cudaMemcpyAsync(a.counter, a.route_n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return SG_ERR_CUDA;
     return SG_OK;
 }
 
 }  // namespace
 
 void sg_length_order(const sg_mesh *m, const QueryIn &in, int64_t nq, uint8_t *keys, int32_t *counts, int32_t *perm,
-                     cudaStream_t s) {
+                     cudaStream_t s, float esc_lmax) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * SG_LBUCKETS, s);
     const int64_t g1 = std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 4);
-    k_lorder_hist<<<(unsigned)std::max<int64_t>(g1, 1), 256, 0, s>>>(nq, in, m->d_lref, keys, counts);
+    k_lorder_hist<<<(unsigned)std::max<int64_t>(g1, 1), 256, 0, s>>>(nq, in, m->d_lref, esc_lmax, keys, counts);
     const int64_t g2 = std::min<int64_t>((nq + 256 * SG_LCHUNK - 1) / (256 * SG_LCHUNK), (int64_t)sms * 4);
     k_lorder_scatter<<<(unsigned)std::max<int64_t>(g2, 1), 256, 0, s>>>(nq, keys, counts, perm);
 }
@@ -945,7 +962,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
     if (r.precision >= 40) {
         SgFwdIO io{a.in, nq, out_face, out_bary, out_pos, out_dir, out_w, out_status, out_ncross, out_hash, a.perm,
-                   a.counter, nullptr};
+                   a.counter, nullptr, nullptr, nullptr, nullptr};
         if (pev) cudaEventRecord(pev[0], s);
         cudaError_t e = sg_launch_walk64(m, io, n_w, r, s);
         if (pev) cudaEventRecord(pev[1], s);
@@ -969,12 +986,14 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
         default: e = autoprec ? launch_walk<4, true>(a, r, s) : launch_walk<4>(a, r, s); break;
     }
     if (e == cudaSuccess && autoprec) {
-        // the escalated queries, in the order the FP32 walk listed them, by the mixed walk; its
-        // grid reads the list's length from device memory (no host synchronisation)
+        // the mixed walk takes the queries the order routed to it (in that order), then those the
+        // FP32 walk handed on at its crossing budget; its grid reads the lists' lengths from
+        // device memory (no host synchronisation)
         sg_opts r40 = r;
         r40.precision = 40;
         SgFwdIO io{a.in, nq, out_face, out_bary, out_pos, out_dir, out_w, out_status, out_ncross, out_hash,
-                   a.esc_list, a.counter + SG_CTR_MIXED, a.esc_count};
+                   a.route_n ? a.perm : nullptr, a.counter + SG_CTR_MIXED, nullptr, a.route_n, a.esc_list,
+                   a.esc_count};
         e = sg_launch_walk64(m, io, n_w, r40, s);
     }
     if (pev) cudaEventRecord(pev[1], s);

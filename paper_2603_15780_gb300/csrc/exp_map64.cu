@@ -637,8 +637,17 @@ struct Fwd64Args {
     uint64_t *out_hash;
     const int32_t *__restrict__ perm;
     int32_t *counter;
-    const int32_t *n_dev;
+    // task lists under the automatic precision (SgFwdIO): perm[off1 + t] for t < n1, then perm2
+    const int32_t *off1_dev, *n1_dev, *perm2, *n2_dev;
 };
+
+// number of tasks of the first list (the rest come from perm2)
+__device__ __forceinline__ int64_t task_n1(const Fwd64Args &a) {
+    if (a.n1_dev) return __ldg(a.n1_dev);
+    if (a.off1_dev) return a.nq - __ldg(a.off1_dev);
+    return a.perm2 ? 0 : a.nq;
+}
+__device__ __forceinline__ int64_t task_n(const Fwd64Args &a) { return task_n1(a) + (a.n2_dev ? __ldg(a.n2_dev) : 0); }
 
 // PREC 64: the FP64 walk; 48: the double-float walk; 40: the mixed walk
 template <int NW, int PREC = 64>
@@ -650,7 +659,13 @@ struct Job64 {
     int64_t q;
 
     __device__ __forceinline__ bool init(int64_t t) {
-        q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
+        if (a->perm2) {  // the automatic precision's lists
+            const int64_t n1 = task_n1(*a);
+            if (t < n1) q = __ldg(a->perm + (a->off1_dev ? __ldg(a->off1_dev) : 0) + t);
+            else q = __ldg(a->perm2 + (t - n1));
+        } else {
+            q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
+        }
         const P64 &P = a->P;
         const QueryIn &in = a->in;
         const int m = in.mesh_id ? __ldg(in.mesh_id + q) : 0;
@@ -894,7 +909,7 @@ template <int NW>
 __global__ void __launch_bounds__(128, SG_WALK48_MINB) k_walk48(Fwd64Args a) {
     Job64<NW, 48> job;
     job.a = &a;
-    run_persistent(a.counter, a.nq, job, a.n_dev);
+    run_persistent(a.counter, a.nq, job);
 }
 
 // resident blocks per SM the mixed walk is compiled for
@@ -905,7 +920,7 @@ template <int NW>
 __global__ void __launch_bounds__(128, SG_WALK40_MINB) k_walk40(Fwd64Args a) {
     Job64<NW, 40> job;
     job.a = &a;
-    run_persistent(a.counter, a.nq, job, a.n_dev);
+    run_persistent(a.counter, a.perm2 ? task_n(a) : a.nq, job);
 }
 
 // Double-float half-edge records from the FP64 face shapes, in the layout of the FP32 half-edge
@@ -1033,7 +1048,8 @@ cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const
     a.in = io.in; a.nq = io.nq;
     a.out_face = io.out_face; a.out_bary = io.out_bary; a.out_pos = io.out_pos; a.out_dir = io.out_dir;
     a.out_w = io.out_w; a.out_status = io.out_status; a.out_ncross = io.out_ncross; a.out_hash = io.out_hash;
-    a.perm = io.perm; a.counter = io.counter; a.n_dev = io.n_dev;
+    a.perm = io.perm; a.counter = io.counter;
+    a.off1_dev = io.off1_dev; a.n1_dev = io.n1_dev; a.perm2 = io.perm2; a.n2_dev = io.n2_dev;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -758,14 +758,20 @@ struct SgFwdIO {
     uint64_t *out_hash;
     const int32_t *perm;
     int32_t *counter;
-    const int32_t *n_dev;  // task count in device memory (the escalation list's), or NULL: nq
+    // Task lists of the mixed walk under the automatic precision (device counts, written by
+    // earlier kernels on the stream): tasks [0, n1) are perm[off1 + t], with n1 = *n1_dev, or
+    // nq - *off1_dev when n1_dev is NULL; tasks [n1, n1 + *n2_dev) are perm2[t - n1].  All NULL:
+    // tasks [0, nq) are perm[t] (or t).
+    const int32_t *off1_dev, *n1_dev, *perm2, *n2_dev;
 };
 sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s, bool half48);
 // Length order of a batch (exp_map.cu): perm[0 .. nq) = the queries longest walk first, in
 // buckets of an eighth of an octave of L / l_ref.  Scratch: keys (nq bytes), counts (512 int32).
 #define SG_LBUCKETS 256
+// With esc_lmax > 0, bucket 0 (the order's head, counts[0] queries) holds the queries longer than
+// esc_lmax l_ref.
 void sg_length_order(const sg_mesh *m, const QueryIn &in, int64_t nq, uint8_t *keys, int32_t *counts, int32_t *perm,
-                     cudaStream_t s);
+                     cudaStream_t s, float esc_lmax = 0.f);
 cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const sg_opts &r, cudaStream_t s);
 
 struct Frame3 {
@@ -908,10 +914,8 @@ __device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
 #endif
 
 template <class Job, int REFILL = SG_REFILL_LANES>
-__device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job, const int32_t *n_dev = nullptr) {
-    // n_dev: the task count as written by an earlier kernel on the stream (an upper bound n)
-    if (n_dev) n = min(n, (int64_t)*n_dev);
-    if (n <= 0) return;  // an empty list: no ticket to take
+__device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job) {
+    if (n <= 0) return;  // an empty list (a count read from device memory): no ticket to take
     bool live = false, pending = false, exhausted = false;
     const unsigned FULL = 0xffffffffu;
     while (true) {
