@@ -34,9 +34,10 @@ CLOCKS_DIR = os.environ.get("SG_BENCH_CLOCKS_DIR", "/tmp")
 RECORD_BYTES = 32
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
-    kernel's sources changed since that capture (profiles/ncu_traffic.json)."""
+def ncu_traffic(kernel: str, key: str = "dram_bytes_per_launch"):
+    """DRAM bytes (or, with key="lts_requests_per_launch", L2 requests) per launch of `kernel` from
+    the committed ncu capture, or None when the kernel's sources changed since that capture
+    (profiles/ncu_traffic.json)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
@@ -47,7 +48,7 @@ def ncu_traffic(kernel: str):
     files = {"k_bwd_rewalk": ["walk.cuh", "backward.cu"], "k_walk_persistent": ["walk.cuh", "exp_map.cu"]}[kernel]
     csrc = os.path.join(ROOT, "paper_2603_15780_gb300", "csrc")
     sha = hashlib.sha1(b"".join(open(os.path.join(csrc, f), "rb").read() for f in files)).hexdigest()
-    return rec["dram_bytes_per_launch"] if sha == rec["source_sha1"] else None
+    return rec.get(key) if sha == rec["source_sha1"] else None
 
 
 def peaks():
@@ -881,6 +882,17 @@ def main():
         roofline = dict(hbm_norm, bound="hbm", kernel=dom)
     roofline.update({"traffic": ncu_traffic(dom), "algorithmic_bytes_per_launch": int(kern[dom][0]),
                      "launch_ms": kern[dom][1], "crossings_per_launch": int(ncross), "queries_per_launch": nq})
+    # The same kernel counted in L2 requests (ncu's lts__t_requests of the committed capture, null
+    # once the kernel changed): record reads, edge reductions and query I/O, each a request, against
+    # the request rate of the gather probe (one request per 32-B gather).
+    nreq = ncu_traffic(dom, "lts_requests_per_launch")
+    if nreq is not None and l2_gather is not None:
+        peak_req = l2_gather["random_GBps"]["1x32B"] * 1e9 / 32
+        ach_req = nreq / (kern[dom][1] * 1e-3)
+        roofline["l2_requests"] = {"per_launch": int(nreq), "achieved_per_s": ach_req, "peak_per_s": peak_req,
+                                   "frac": ach_req / peak_req,
+                                   "source": "ncu lts__t_requests.sum of the committed capture; peak: the gather "
+                                             "probe's 32-B gathers per second"}
     if dom == "k_bwd_rewalk":
         roofline["atomic_bytes_per_launch"] = int(rewalk_atomic_bytes)
     kernels = {k: {"ms": t, "algorithmic_GBps": b / (t * 1e-3) / 1e9, "frac_of_hbm": b / (t * 1e-3) / 1e9 / peak_hbm}
