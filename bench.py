@@ -277,7 +277,8 @@ def run_multimesh(args):
                  "p99_pos_err_over_diag": float(np.quantile(np.concatenate(v), 0.99)),
                  "near_vertex_flagged": float(np.mean(flagged[k]))} for k, v in acc.items()}
     cfg = {f[0]: getattr(best, f[0]) for f in best._fields_
-           if f[0] in ("kernel", "block", "blocks_per_sm", "sort", "fp64_escalate")}
+           if f[0] in ("kernel", "block", "blocks_per_sm", "sort", "fp64_escalate", "queries_per_thread",
+                       "precision")}
     line = {"metric": "geodesics/s, 64 uneven meshes in one launch", "value": nq / (t_graph * 1e-3),
             "unit": "geodesics/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_graph, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -427,7 +428,9 @@ def run_features(args):
                  against the stopping walk;
       update     sg_mesh_update_vertices on the icosphere s6 (81,920 faces);
       k_step     exp_map_steps with K = 5 and a linear field on 1M queries, forward and
-                 forward + GFD backward through all steps."""
+                 forward + GFD backward through all steps;
+      field_steps  the fused K-step of a vertex-sampled field (sg_exp_map_steps, K = 5) against
+                 K launches with the field evaluated by torch between them."""
     import torch
     import meshgen
     import paper_2603_15780_gb300 as sg
@@ -501,6 +504,39 @@ def run_features(args):
         (xK * gK).sum().backward()
     t_kb = timed(kstep_bwd)
     res["k_step"] = {"K": 5, "fwd_ms": t_k, "fwd_bwd_gfd_ms": t_kb, "geodesics_per_s_fwd": 5 * nq / (t_k * 1e-3)}
+    # K-step of a vertex-sampled field (u = the vertex values of x -> A x, interpolated in each
+    # face): one fused launch (sg_exp_map_steps) against K sg_exp_map launches with the field
+    # evaluated by torch between them, forward and forward + GFD backward through all steps
+    Fd = torch.tensor(F, dtype=torch.int64, device=dev)
+    U = (T(X32) @ A.T).contiguous()
+    fs = sg.exp_map_field_steps(mesh, face, bary, U, 5)
+    t_fs = timed(lambda: sg.exp_map_field_steps(mesh, face, bary, U, 5))
+    Ug = U.clone().requires_grad_(True)
+    bg = bary.clone().requires_grad_(True)
+
+    def fused_bwd():
+        xK = sg.ExpMapFieldSteps.apply(mesh, face, bg, Ug, 5)[0]
+        (xK * gK).sum().backward()
+    t_fsb = timed(fused_bwd)
+
+    def loop(Uu, b0, grad=False):
+        f, b = face, b0
+        for _ in range(5):
+            v = 0.2 * (b.clamp(min=0.0)[:, :, None] * Uu[Fd[f.long()]]).sum(1)
+            x, f, b, _, _ = sg.ExpMap.apply(mesh, f, b, v, "gfd")
+        return x
+
+    def loop_fwd():
+        with torch.no_grad():
+            loop(U, bary)
+
+    def loop_bwd():
+        (loop(Ug, bg) * gK).sum().backward()
+    t_lf = timed(loop_fwd)
+    t_lb = timed(loop_bwd)
+    res["field_steps"] = {"K": 5, "fused_fwd_ms": t_fs, "fused_fwd_bwd_gfd_ms": t_fsb, "loop_fwd_ms": t_lf,
+                          "loop_fwd_bwd_gfd_ms": t_lb, "speedup_fwd": t_lf / t_fs, "speedup_fwd_bwd": t_lb / t_fsb,
+                          "mixed_or_flagged": float(((fs["status"].cpu().numpy() & 12) != 0).mean())}
     # hole avoidance on the sphere with 8% of its faces removed
     rngh = np.random.default_rng(6)
     Xh, Fh = meshgen.remove_faces(X, F, 0.08, rngh)

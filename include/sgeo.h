@@ -106,22 +106,34 @@ typedef struct sg_opts {
                                it (SG_ST_HOLE).  Mode 1 runs on the persistent kernel with FP64
                                classification; the plain kernel and sg_exp_map_trace reject it
                                (SG_ERR_UNSUPPORTED). */
-    int32_t precision;      /* 32 (default): FP32 walk with FP64 classification near vertices;
-                               64: every quantity of the walk in FP64 (state, face shapes,
-                               frames, vertex angles), for inputs whose FP32 error exceeds the
-                               classification margins; persistent kernel, forward only (the
-                               trace, the backward, boundary_mode 1 and the plain kernel reject
-                               it with SG_ERR_UNSUPPORTED).  The first FP64 call on a mesh
-                               allocates and derives its FP64 geometry (synchronous cudaMalloc,
-                               88 B per face and 8 B per vertex, kept by the mesh);
-                               48: the double-float walk, the same accuracy class as 64 on the
-                               FP32 pipes: every crossing in double-float arithmetic (each value
-                               an unevaluated sum of two FP32 numbers, about 48 significant
-                               bits; one 32-byte record per crossing, the start and the end as
-                               well), the rare events (vertex hits, boundary stops, starts on an
-                               edge or vertex) in FP64; the same restrictions as 64,
-                               and its first call on a mesh also allocates 96 B per face of
-                               double-float records. */
+    int32_t precision;      /* 0 (default): automatic -- each query walks in FP32 (with FP64
+                               classification near vertices) while its walk stays within the range
+                               where the FP32 walk's face sequences were measured equal to the
+                               double-precision ones (at most 256 crossings), else in the mixed walk
+                               (40): queries longer than 96 l_ref are routed to it by the query order,
+                               and a walk that reaches 256 crossings is restarted there (SG_ST_MIXED
+                               marks both).  sg_exp_map_trace, the backward and hole avoidance
+                               (boundary_mode 1) walk in FP32 under this setting;
+                               32: the FP32 walk for every query;
+                               40: the mixed walk: the FP32 walk's orientation tests, exit points and
+                               length, with the walking direction and the records' edge vectors in
+                               double-float (pairs of FP32 numbers), so that the direction's error no
+                               longer grows with the path;
+                               48: the double-float walk: every crossing in double-float arithmetic
+                               (about 48 significant bits), the rare events (vertex hits, boundary
+                               stops, starts on an edge or vertex) in FP64;
+                               64: every quantity of the walk in FP64 (state, face shapes, frames,
+                               vertex angles).
+                               40, 48 and 64 run on the persistent kernel, forward only (the trace,
+                               the backward, boundary_mode 1 and the plain kernel reject them with
+                               SG_ERR_UNSUPPORTED).  Their FP64 geometry and double-float records
+                               (192 B per face, 8 B per vertex) are built with the mesh. */
+    int32_t queries_per_thread; /* <= 0: the default launch.  Plain kernel: each thread walks this
+                               many queries in turn (grid-stride; grid = ceil(nq / (block * qpt))).
+                               Persistent kernel: the grid is sized so that each thread takes about
+                               this many queries from the queue on average (blocks per SM =
+                               ceil(nq / (qpt * SMs * block)), at most the occupancy limit and the
+                               blocks_per_sm given); the autotuner sweeps it. */
 } sg_opts;
 
 /* Fills `o` with the defaults described above. */
@@ -329,6 +341,62 @@ sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, 
                               const float *g_dir, int32_t n_w, const float *g_w,
                               float *grad_v, float *grad_p, float *grad_bary, float *grad_V,
                               float *grad_w, uint32_t *out_status, const sg_opts *o, void *stream);
+
+/*
+ * sg_exp_map_steps -- the K-step exponential map of a vector field sampled at the mesh vertices,
+ * x_{k+1} = Exp_{x_k}(h u(x_k)) for k = 0..K-1, in one launch (Sec. 5, Eq. "fmobj": the flow is
+ * integrated by K exponential-map steps with the field re-evaluated at every intermediate point).
+ * The field is given by its values at the vertices and evaluated at a point by barycentric
+ * interpolation, u(x) = sum_j b_j U[F[f, j]]; each step projects h u(x_k) onto the face it starts
+ * in and walks it with the FP32 walk of sg_exp_map (FP64 classification near vertices).
+ *   K          number of steps, 1..64;  h  the step's scale (for example 1 / K)
+ *   U          device float32 [n_vertices][3] ambient field vectors (global vertex ids of a batch)
+ *   mesh_id, face, bary  the start points, as in sg_exp_map
+ * Outputs (device, caller-allocated): out_face, out_bary, out_pos, out_dir of the last step;
+ * out_status the OR of the steps' status bits (SG_ST_FLIPPED excluded).  Per-step records, all
+ * given or all NULL (step_hash may be NULL), needed by sg_exp_map_steps_backward:
+ *   step_face  int32 [K + 1][nq]: each step's start face (local), then the end face
+ *   step_bary  float32 [K + 1][nq][3]: each step's start barycentrics, then the end's
+ *   step_v     float32 [K][nq][3]: the ambient vector h u(x_k) each step was given
+ *   step_dir   float32 [K][nq][3]: each step's end direction
+ *   step_status uint32 [K][nq]: each step's status (SG_ST_FLIPPED relative to its own start)
+ *   step_hash  uint64 [K][nq]: each step's face-sequence hash (as sg_exp_map's out_hash)
+ * A zero vector makes its step the identity.  opts: kernel, sort and block are ignored (the
+ * persistent kernel, queries in input order); precision 0 and 32 walk in FP32, others and
+ * boundary_mode 1 are rejected with SG_ERR_UNSUPPORTED.  Scratch: 64 bytes (o->workspace, or
+ * stream-ordered memory).  Asynchronous on `stream`.
+ * Errors: SG_ERR_INVALID_ARG (K out of range, a required array NULL, records given in part),
+ * SG_ERR_UNSUPPORTED, SG_ERR_OOM, SG_ERR_CUDA.
+ */
+sg_status sg_exp_map_steps(const sg_mesh *m, int32_t K, float h, const float *U, int64_t nq, const int32_t *mesh_id,
+                           const int32_t *face, const float *bary, int32_t *out_face, float *out_bary, float *out_pos,
+                           float *out_dir, uint32_t *out_status, int32_t *step_face, float *step_bary, float *step_v,
+                           float *step_dir, uint32_t *step_status, uint64_t *step_hash, const sg_opts *o,
+                           void *stream);
+
+/*
+ * sg_exp_map_steps_backward -- vector-Jacobian product of sg_exp_map_steps (the chain rule through
+ * the K steps, Sec. 4 "Gradient computation"): from the last step back to the first, the
+ * estimator's VJP of the step (sg_exp_map_backward, EP or GFD, which recomputes the step's walk)
+ * with the upstream gradients of its end point (g_pos, last step only) and end barycentrics, then
+ * the field's term: with v_k = h sum_j b_kj U_j, grad U_j += h b_kj grad_v_k and the gradient of
+ * the step's start barycentrics gains h <U_j, grad_v_k>; their sum is the upstream gradient of the
+ * previous step's end barycentrics.
+ *   step_*     the forward's per-step records;  U, h, K, mesh_id as given to the forward
+ *   g_pos      device float32 [nq][3] dL/dx_K;  g_bary  [nq][3] dL/db_K or NULL
+ * Outputs (device): grad_U float32 [n_vertices][3] ACCUMULATED (+=) or NULL; grad_bary float32
+ * [nq][3] dL/db_0 (meaningful up to the simplex gauge); grad_V [n_vertices][3] accumulated or NULL.
+ * Scratch: sg_exp_map_steps_backward_workspace_size (o->workspace, or stream-ordered memory).
+ * Asynchronous on `stream`.  Errors: as sg_exp_map_backward.
+ */
+sg_status sg_exp_map_steps_backward(const sg_mesh *m, int32_t estimator, float eps_v, float eps_p, int32_t K,
+                                    float h, const float *U, int64_t nq, const int32_t *mesh_id,
+                                    const int32_t *step_face, const float *step_bary, const float *step_v,
+                                    const float *step_dir, const uint32_t *step_status, const float *g_pos,
+                                    const float *g_bary, float *grad_U, float *grad_bary, float *grad_V,
+                                    const sg_opts *o, void *stream);
+sg_status sg_exp_map_steps_backward_workspace_size(const sg_mesh *m, int32_t estimator, int32_t K, int64_t nq,
+                                                   int32_t want_grad_V, size_t *bytes);
 
 /*
  * sg_transport_back -- the adjoint of the parallel transport along each query's geodesic,

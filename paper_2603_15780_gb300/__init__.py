@@ -20,28 +20,33 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Mesh", "exp_map", "exp_map_backward", "transport_back", "ExpMap", "Opts", "lib", "status_names",
+__all__ = ["Mesh", "exp_map", "exp_map_backward", "transport_back", "ExpMap", "ExpMapFieldSteps", "exp_map_field_steps",
+           "exp_map_field_steps_backward", "Opts", "lib", "status_names",
            "ST_BOUNDARY", "ST_MAX_STEPS", "ST_NEAR_VERTEX", "ST_NEAR_EDGE", "ST_VERTEX_HIT", "ST_FP64",
-           "ST_START_ON_EDGE", "ST_INVALID", "ST_GFD_SPLIT", "ST_FLIPPED", "ST_NO_GRADV",
+           "ST_START_ON_EDGE", "ST_INVALID", "ST_GFD_SPLIT", "ST_FLIPPED", "ST_NO_GRADV", "ST_HOLE", "ST_MIXED",
+           "ST_REWALK_DIVERGED",
            "KERNEL_AUTO", "KERNEL_PLAIN", "KERNEL_PERSISTENT", "EST_EP", "EST_GFD", "SgError"]
 
 ST_BOUNDARY, ST_MAX_STEPS, ST_NEAR_VERTEX, ST_NEAR_EDGE = 1, 2, 4, 8
 ST_VERTEX_HIT, ST_FP64, ST_START_ON_EDGE, ST_INVALID = 16, 32, 64, 128
 ST_GFD_SPLIT, ST_FLIPPED, ST_NO_GRADV = 256, 512, 1024
+ST_HOLE, ST_MIXED, ST_REWALK_DIVERGED = 2048, 4096, 8192
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT = 0, 1, 2
 EST_EP, EST_GFD = 0, 1
 
 EXPORTED = ["sg_opts_default", "sg_status_string", "sg_mesh_create", "sg_mesh_create_batched",
             "sg_mesh_destroy", "sg_mesh_get_info", "sg_exp_map_workspace_size", "sg_exp_map",
             "sg_exp_map_backward", "sg_version", "sg_exp_map_noalloc", "sg_exp_map_backward_workspace_size",
-            "sg_mesh_update_vertices", "sg_exp_map_trace", "sg_transport_back"]
+            "sg_mesh_update_vertices", "sg_exp_map_trace", "sg_transport_back", "sg_exp_map_steps",
+            "sg_exp_map_steps_backward", "sg_exp_map_steps_backward_workspace_size"]
 
 
 def status_names(st: int) -> list[str]:
     names = {ST_BOUNDARY: "BOUNDARY", ST_MAX_STEPS: "MAX_STEPS", ST_NEAR_VERTEX: "NEAR_VERTEX",
              ST_NEAR_EDGE: "NEAR_EDGE", ST_VERTEX_HIT: "VERTEX_HIT", ST_FP64: "FP64",
              ST_START_ON_EDGE: "START_ON_EDGE", ST_INVALID: "INVALID", ST_GFD_SPLIT: "GFD_SPLIT",
-             ST_FLIPPED: "FLIPPED", ST_NO_GRADV: "NO_GRADV"}
+             ST_FLIPPED: "FLIPPED", ST_NO_GRADV: "NO_GRADV", ST_HOLE: "HOLE", ST_MIXED: "MIXED",
+             ST_REWALK_DIVERGED: "REWALK_DIVERGED"}
     return [n for b, n in names.items() if st & b]
 
 
@@ -55,7 +60,7 @@ class Opts(C.Structure):
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("fp64_escalate", C.c_int32),
                 ("tau_near", C.c_float), ("tau_snap", C.c_float), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("prof_events", C.c_void_p), ("boundary_mode", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("queries_per_thread", C.c_int32)]
 
 
 class MeshInfo(C.Structure):
@@ -100,6 +105,13 @@ def lib():
                                               C.POINTER(Opts), P]
             L.sg_transport_back.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, C.c_int32, P, P,
                                             C.POINTER(Opts), P]
+            L.sg_exp_map_steps.argtypes = [P, C.c_int32, C.c_float, P, C.c_int64, P, P, P, P, P, P, P, P,
+                                           P, P, P, P, P, P, C.POINTER(Opts), P]
+            L.sg_exp_map_steps_backward.argtypes = [P, C.c_int32, C.c_float, C.c_float, C.c_int32, C.c_float, P,
+                                                    C.c_int64, P, P, P, P, P, P, P, P, P, P, P,
+                                                    C.POINTER(Opts), P]
+            L.sg_exp_map_steps_backward_workspace_size.argtypes = [P, C.c_int32, C.c_int32, C.c_int64, C.c_int32,
+                                                                   C.POINTER(C.c_size_t)]
             for f in EXPORTED:
                 if f not in ("sg_opts_default",):
                     getattr(L, f).restype = getattr(L, f).restype or C.c_int
@@ -267,9 +279,10 @@ def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, mesh_id=None, *, wan
             out["ncross"] = torch.empty(nq, dtype=torch.int32, device=dev)
         if want_hash:
             out["hash"] = torch.empty(nq, dtype=torch.int64, device=dev)
-    if workspace is None and o.kernel != KERNEL_PLAIN:
+    if workspace is None:
+        # the persistent kernel's queue and sorts, and the automatic precision's escalation list
         nb = workspace_size(mesh, nq, o)
-        workspace = torch.empty(nb, dtype=torch.uint8, device=face.device)
+        workspace = torch.empty(max(nb, 1), dtype=torch.uint8, device=face.device)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel()
@@ -413,6 +426,82 @@ def transport_back(mesh: Mesh, face, bary, v, end, u, mesh_id=None, *, opts: Opt
     return out.reshape(shape)
 
 
+def exp_map_field_steps(mesh: Mesh, face, bary, U, K: int, h: float | None = None, mesh_id=None, *,
+                        want_steps=True, want_hash=False, opts: Opts | None = None, stream=None):
+    """sg_exp_map_steps: K exponential-map steps x_{k+1} = Exp_{x_k}(h u(x_k)) of the vector field
+    whose values at the vertices are U [n_vertices, 3] (barycentric interpolation inside a face), in
+    one launch; h defaults to 1 / K.  Returns dict(face, bary, pos, dir, status) of the last step,
+    with want_steps the per-step records step_face [K+1, nq], step_bary [K+1, nq, 3], step_v [K, nq, 3],
+    step_dir [K, nq, 3], step_status [K, nq] (and step_hash [K, nq] with want_hash)."""
+    torch = _torch()
+    face = _dev(face, torch.int32)
+    nq = face.numel()
+    bary = _dev(bary, torch.float32, (nq, 3))
+    U = _dev(U, torch.float32, (-1, 3))
+    mesh_id = _dev(mesh_id, torch.int32, (nq,))
+    h = (1.0 / K if K > 0 else 0.0) if h is None else float(h)   # K < 1 is rejected by the library
+    dev = face.device
+    out = {"face": torch.empty(nq, dtype=torch.int32, device=dev), "bary": torch.empty(nq, 3, device=dev),
+           "pos": torch.empty(nq, 3, device=dev), "dir": torch.empty(nq, 3, device=dev),
+           "status": torch.empty(nq, dtype=torch.int32, device=dev)}
+    if want_steps and K > 0:
+        out.update({"step_face": torch.empty(K + 1, nq, dtype=torch.int32, device=dev),
+                    "step_bary": torch.empty(K + 1, nq, 3, device=dev), "step_v": torch.empty(K, nq, 3, device=dev),
+                    "step_dir": torch.empty(K, nq, 3, device=dev),
+                    "step_status": torch.empty(K, nq, dtype=torch.int32, device=dev)})
+        if want_hash:
+            out["step_hash"] = torch.empty(K, nq, dtype=torch.int64, device=dev)
+    o = opts if opts is not None else default_opts()
+    ws = torch.empty(64, dtype=torch.uint8, device=dev)
+    o.workspace = ws.data_ptr()
+    o.workspace_bytes = 64
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().sg_exp_map_steps(mesh.handle, K, h, _ptr(U), nq, _ptr(mesh_id), _ptr(face), _ptr(bary),
+                                _ptr(out["face"]), _ptr(out["bary"]), _ptr(out["pos"]), _ptr(out["dir"]),
+                                _ptr(out["status"]), _ptr(out.get("step_face")), _ptr(out.get("step_bary")),
+                                _ptr(out.get("step_v")), _ptr(out.get("step_dir")), _ptr(out.get("step_status")),
+                                _ptr(out.get("step_hash")), C.byref(o), C.c_void_p(s.cuda_stream))
+    _check(rc, "sg_exp_map_steps")
+    out["_workspace"] = ws
+    return out
+
+
+def exp_map_field_steps_backward(mesh: Mesh, estimator, fwd: dict, U, K: int, h: float, g_pos, g_bary=None,
+                                 mesh_id=None, *, eps_v=1e-4, eps_p=1e-4, grad_U=None, want_grad_V=False,
+                                 grad_V=None, opts: Opts | None = None, stream=None):
+    """sg_exp_map_steps_backward on the per-step records of exp_map_field_steps.  Returns
+    dict(grad_bary [nq, 3] of the start barycentrics, grad_U [n_vertices, 3] (accumulated into
+    `grad_U` when given), grad_V (if requested))."""
+    torch = _torch()
+    est = {"ep": EST_EP, "gfd": EST_GFD}.get(estimator, estimator)
+    nq = fwd["face"].numel()
+    dev = fwd["face"].device
+    U = _dev(U, torch.float32, (-1, 3))
+    g_pos = _dev(g_pos, torch.float32, (nq, 3))
+    g_bary = _dev(g_bary, torch.float32, (nq, 3))
+    mesh_id = _dev(mesh_id, torch.int32, (nq,))
+    res = {"grad_bary": torch.empty(nq, 3, device=dev),
+           "grad_U": grad_U if grad_U is not None else torch.zeros(U.shape[0], 3, device=dev)}
+    if want_grad_V or grad_V is not None:
+        res["grad_V"] = grad_V if grad_V is not None else torch.zeros(mesh.n_vertices, 3, device=dev)
+    n = C.c_size_t()
+    _check(lib().sg_exp_map_steps_backward_workspace_size(mesh.handle, est, K, nq, int("grad_V" in res), C.byref(n)),
+           "sg_exp_map_steps_backward_workspace_size")
+    ws = torch.empty(max(n.value, 1), dtype=torch.uint8, device=dev)
+    o = opts if opts is not None else default_opts()
+    o.workspace = ws.data_ptr()
+    o.workspace_bytes = ws.numel()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().sg_exp_map_steps_backward(mesh.handle, est, eps_v, eps_p, K, h, _ptr(U), nq, _ptr(mesh_id),
+                                         _ptr(fwd["step_face"]), _ptr(fwd["step_bary"]), _ptr(fwd["step_v"]),
+                                         _ptr(fwd["step_dir"]), _ptr(fwd["step_status"]), _ptr(g_pos), _ptr(g_bary),
+                                         _ptr(res["grad_U"]), _ptr(res["grad_bary"]), _ptr(res.get("grad_V")),
+                                         C.byref(o), C.c_void_p(s.cuda_stream))
+    _check(rc, "sg_exp_map_steps_backward")
+    res["_workspace"] = ws
+    return res
+
+
 def _autograd_function():
     import torch
 
@@ -481,13 +570,52 @@ def exp_map_steps(mesh: Mesh, face, bary, field, K: int, estimator="gfd", V=None
     return (x, face, bary, st, steps) if return_steps else (x, face, bary, st)
 
 
+def _steps_autograd_function():
+    import torch
+
+    class ExpMapFieldSteps(torch.autograd.Function):
+        """(pos, face, bary, dir, status) after K steps x_{k+1} = Exp_{x_k}(h u(x_k)) of the field
+        with vertex values U, in one launch (sg_exp_map_steps).  Differentiable in the start
+        barycentrics `bary` and in `U`; the backward chains the K steps' estimator VJPs
+        (sg_exp_map_steps_backward: "ep" or "gfd", step `eps`)."""
+
+        @staticmethod
+        def forward(ctx, mesh, face, bary, U, K, h=None, estimator="gfd", mesh_id=None, eps=1e-4):
+            h = 1.0 / K if h is None else float(h)
+            out = exp_map_field_steps(mesh, face, bary.detach(), U.detach(), K, h, mesh_id=mesh_id)
+            ctx.mesh, ctx.K, ctx.h, ctx.estimator, ctx.eps = mesh, K, h, estimator, eps
+            ctx.rec = {k: out[k] for k in ("face", "step_face", "step_bary", "step_v", "step_dir", "step_status")}
+            ctx.save_for_backward(U.detach(), mesh_id if mesh_id is not None else torch.empty(0))
+            ctx.mark_non_differentiable(out["face"], out["status"])
+            ctx.set_materialize_grads(False)
+            return out["pos"], out["face"], out["bary"], out["dir"], out["status"]
+
+        @staticmethod
+        def backward(ctx, g_pos, _gf, g_bary, _gd, _gs):
+            U, mid = ctx.saved_tensors
+            nq = ctx.rec["face"].numel()
+            if g_pos is None:
+                g_pos = torch.zeros(nq, 3, device=U.device)
+            r = exp_map_field_steps_backward(ctx.mesh, ctx.estimator, ctx.rec, U, ctx.K, ctx.h, g_pos.contiguous(),
+                                             None if g_bary is None else g_bary.contiguous(),
+                                             mesh_id=mid if mid.numel() else None, eps_v=ctx.eps, eps_p=ctx.eps)
+            return None, None, r["grad_bary"], r["grad_U"], None, None, None, None, None
+
+    return ExpMapFieldSteps
+
+
 class _Lazy:
-    _cls = None
+    def __init__(self, make):
+        self._make = make
+        self._cls = None
 
     def __getattr__(self, name):
-        if _Lazy._cls is None:
-            _Lazy._cls = _autograd_function()
-        return getattr(_Lazy._cls, name)
+        if name.startswith("_"):
+            raise AttributeError(name)
+        if self._cls is None:
+            self._cls = self._make()
+        return getattr(self._cls, name)
 
 
-ExpMap = _Lazy()
+ExpMap = _Lazy(_autograd_function)
+ExpMapFieldSteps = _Lazy(_steps_autograd_function)

@@ -2,10 +2,12 @@
 
 `tune(mesh, face, bary, v, ...)` times candidate launch configurations of the forward
 walk on the caller's own batch (CUDA events on the current stream, median of `reps`) and
-returns the fastest `Opts`: kernel shape (plain one-thread-per-query or persistent),
-threads per block, persistent residency (blocks per SM, which sets how many queries each
-thread takes from the queue) and the start-face sort.  Results are cached per
-(mesh, batch size bucket, carried vectors).
+returns the fastest `Opts`: kernel shape (plain or persistent), threads per block, queries
+per thread and the query order.  Queries per thread is the plain kernel's grid-stride count
+(1 = the paper's one thread per query) and, for the persistent kernel, the average number of
+queries each thread takes from the queue (it sets the grid: blocks per SM = nq / (qpt x SMs x
+block), capped by the occupancy limit; 0 = as many resident blocks as fit).  Results are
+cached per (mesh, batch size bucket, carried vectors).
 
 `GraphedExpMap` captures one sg_exp_map call (static input/output/workspace buffers) into a
 torch.cuda.CUDAGraph so a fixed-shape batch -- e.g. many meshes of uneven size in one
@@ -16,20 +18,21 @@ from __future__ import annotations
 import itertools
 import math
 
-from . import (KERNEL_PERSISTENT, KERNEL_PLAIN, Mesh, SgError, default_opts, exp_map, workspace_size)
+from . import KERNEL_PERSISTENT, KERNEL_PLAIN, Mesh, SgError, default_opts, exp_map, workspace_size
 
 _cache: dict = {}
 
 
 def candidates(fp64_escalate: int = 1):
-    """The search space: plain kernel at 3 block sizes; persistent kernel at 3 block sizes x
-    residency {auto, 2, 1 blocks/SM} x sort {on, off}."""
+    """The search space: the plain kernel at 3 block sizes x {1, 2, 4} queries per thread; the
+    persistent kernel at 2 block sizes x {all resident, 32, 8} queries per thread x query order
+    {the library's automatic choice, start face, input order}."""
     out = []
-    for block in (64, 128, 256):
-        out.append(dict(kernel=KERNEL_PLAIN, block=block, sort=0, fp64_escalate=0, blocks_per_sm=0))
-    for block, per, sort in itertools.product((64, 128, 256), (0, 2, 1), (1, 0)):
+    for block, qpt in itertools.product((64, 128, 256), (1, 2, 4)):
+        out.append(dict(kernel=KERNEL_PLAIN, block=block, sort=0, fp64_escalate=0, queries_per_thread=qpt))
+    for block, qpt, sort in itertools.product((128, 256), (0, 32, 8), (-1, 1, 0)):
         out.append(dict(kernel=KERNEL_PERSISTENT, block=block, sort=sort, fp64_escalate=fp64_escalate,
-                        blocks_per_sm=per))
+                        queries_per_thread=qpt))
     return out
 
 
@@ -61,9 +64,7 @@ def tune(mesh: Mesh, face, bary, v, w=None, mesh_id=None, *, reps: int = 5, fp64
     table = []
     for cfg in (space or candidates(fp64_escalate)):
         o = default_opts(**cfg)
-        ws = None
-        if o.kernel != KERNEL_PLAIN:
-            ws = torch.empty(workspace_size(mesh, nq, o), dtype=torch.uint8, device=face.device)
+        ws = torch.empty(max(workspace_size(mesh, nq, o), 1), dtype=torch.uint8, device=face.device)
         try:
             fn = lambda: exp_map(mesh, face, bary, v, w, mesh_id=mesh_id, opts=o, workspace=ws, out=out)
             fn()

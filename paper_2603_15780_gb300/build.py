@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsgeo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["exp_map.cu", "exp_map64.cu", "backward.cu", "mesh_update.cu", "mesh_build.cpp"]
+SOURCES = ["exp_map.cu", "exp_map64.cu", "exp_map_steps.cu", "backward.cu", "mesh_update.cu", "mesh_build.cpp"]
 # The host mesh builder and the device vertex update evaluate the same FP64 expressions; both are
 # compiled without multiply-add contraction so that they round identically.
 PER_FILE = {"mesh_build.cpp": ["-Xcompiler", "-ffp-contract=off"], "mesh_update.cu": ["--fmad=false"]}

@@ -98,26 +98,28 @@ __device__ void walker_finish(const FwdArgs &a, int64_t q, const Walker &w, cons
     if (a.out_hash) a.out_hash[q] = w.hash;
 }
 
+// One thread per query (Alg. "Parallel Geodesic Tracing CUDA Kernel"), or several queries in turn
+// (grid-stride) when the grid is smaller than the batch (sg_opts.queries_per_thread).
 template <int NW, bool ESC = false, bool AUTO = false>
 __global__ void __launch_bounds__(256) k_walk_plain(FwdArgs a) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= a.nq) return;
-    Walker w;
-    Carry<NW> cw;
-    if (walker_init<NW>(a.P, a.in, q, w, cw)) {
-        if (AUTO && w.Lh > a.esc_lmax * w.lref) {
-            escalate(a, q);
-            return;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.nq; q += (int64_t)gridDim.x * blockDim.x) {
+        Walker w;
+        Carry<NW> cw;
+        if (walker_init<NW>(a.P, a.in, q, w, cw)) {
+            if (AUTO && w.Lh > a.esc_lmax * w.lref) {
+                escalate(a, q);
+                continue;
+            }
+            while (!walker_step<ESC>(w, a.P)) {
+            }
+            // the step cap of an AUTO walk is its crossing budget (see FwdJob)
+            if (AUTO && a.esc_ncross && (w.st & SG_ST_MAX_STEPS)) {
+                escalate(a, q);
+                continue;
+            }
         }
-        while (!walker_step<ESC>(w, a.P)) {
-        }
-        // the step cap of an AUTO walk is its crossing budget (see FwdJob)
-        if (AUTO && a.esc_ncross && (w.st & SG_ST_MAX_STEPS)) {
-            escalate(a, q);
-            return;
-        }
+        walker_finish<NW>(a, q, w, cw);
     }
-    walker_finish<NW>(a, q, w, cw);
 }
 
 // AUTO: the automatic precision -- the query order gave the long queries to the mixed walk, and
@@ -597,7 +599,8 @@ sg_opts resolve(const sg_opts *o, int64_t nq, int64_t nF) {
 template <int NW, bool AUTO = false>
 cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
     if (o.kernel == SG_KERNEL_PLAIN) {
-        int64_t grid = (a.nq + o.block - 1) / o.block;
+        const int64_t per_thread = std::max(o.queries_per_thread, 1);
+        int64_t grid = std::max<int64_t>((a.nq + o.block * per_thread - 1) / (o.block * per_thread), 1);
         if (o.fp64_escalate) k_walk_plain<NW, true, AUTO><<<(unsigned)grid, o.block, 0, s>>>(a);
         else k_walk_plain<NW, false, AUTO><<<(unsigned)grid, o.block, 0, s>>>(a);
         return cudaGetLastError();
@@ -622,6 +625,9 @@ cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
         k_walk_hole<NW><<<(unsigned)grid, o.block, 0, s>>>(a);
         return cudaGetLastError();
     }
+    if (o.queries_per_thread > 0)  // about that many queries per thread: fewer resident blocks
+        per = (int)std::min<int64_t>(per, std::max<int64_t>(
+                  (a.nq + (int64_t)o.queries_per_thread * sms * o.block - 1) / ((int64_t)o.queries_per_thread * sms * o.block), 1));
     int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>(need, 1));
     if (o.fp64_escalate)
         k_walk_persistent<NW, true, AUTO><<<(unsigned)grid, o.block, 0, s>>>(a);

@@ -55,6 +55,34 @@ def test_autotuner_picks_a_valid_configuration():
     assert np.array_equal(out["face"].cpu().numpy()[ok], ref["face"].cpu().numpy()[ok])
 
 
+@pytest.mark.parametrize("pick", ["tuned", "plain-4-per-thread", "persistent-32-per-thread"])
+def test_tuned_and_swept_launches_match_the_oracle(pick):
+    """The launch the autotuner picks on the multi-mesh batch, and the two ends of its
+    queries-per-thread axis, at the full parity bar against the oracle mesh by mesh (face
+    sequences bit-exact on unflagged queries, end points within 1e-5 of each mesh's diagonal)."""
+    import oracle
+    sg, mesh, q, face, bary, v, mid = _batch()
+    from paper_2603_15780_gb300 import autotune
+    if pick == "tuned":
+        opts, _ = autotune.tune(mesh, face, bary, v, mesh_id=mid, reps=2)
+    elif pick == "plain-4-per-thread":
+        opts = sg.default_opts(kernel=sg.KERNEL_PLAIN, sort=0, fp64_escalate=0, queries_per_thread=4)
+    else:
+        opts = sg.default_opts(kernel=sg.KERNEL_PERSISTENT, queries_per_thread=32)
+    gpu = parity.run_gpu(mesh, q, 0, mesh_id=q.mesh_id, opts=opts)
+    wl = meshgen.workload(3, scale=0.001)
+    for m in range(0, 64, 9):
+        sel = np.nonzero(q.mesh_id == m)[0]
+        X, F = wl.meshes[m]
+        ref, _ = parity.run_oracle(parity.as_f32(X), F, q.take(sel), 0)
+        sub = {k: val[sel] for k, val in gpu.items()}
+        # flagged with probability ~1.5e-4 per crossing: bound 2e-4 per crossing plus three
+        # binomial standard deviations of the mesh's sample (a few dozen queries on the small ones)
+        p = 2e-4 * float(ref["ncross"].mean()) + 0.005
+        parity.compare(sub, ref, meshgen.bbox_diag(X), 0, what=f"{pick} mesh {m}",
+                       max_flagged=p + 3 * np.sqrt(p / len(sel)))
+
+
 def test_graph_of_forward_and_both_backwards():
     """The forward, EP on a second stream and GFD with the vertex gradient, captured as one CUDA
     graph (memsets, the length orders, the task list and every counter inside) and replayed:
