@@ -48,6 +48,7 @@
 
 #include "sgeo_internal.h"
 #include "walk.cuh"
+#include "walk64.cuh"
 
 #define SG_BWD_MAX_W 4
 // lanes of a warp that must be idle before the re-walk refills them together (swept under the
@@ -93,10 +94,15 @@ struct BwdArgs {
                         // evaluated the par slot holds the re-walk's swept-column mask (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) columns recomputed by literal walks (scratch)
     int32_t *ntask;     // counters (scratch): [0] tasks, [1] re-walk and [2] literal-walk tickets,
-                        // [3] queries the assemble pass deferred (their ids reuse `tasks`)
+                        // [3] queries the assemble pass deferred (their ids reuse `tasks`),
+                        // [4] mixed-walk tasks and [5] their tickets
     int4 *rst;          // [nq][2] where the literal walks of a split query restart (scratch):
                         // {half-edge | parity << 30 (-1: from the start), s, dx, dy}, {Lh, Ll, -, -}
     const int32_t *perm;  // re-walk queue position -> query (length order), or NULL
+    // the literal walks of the queries whose forward walk was the mixed walk (SG_ST_MIXED): their
+    // task list [3 nq] (count ntask[4], tickets ntask[5]) and the mesh's wide-precision geometry
+    int32_t *tasks40;
+    P64 P4;
 };
 
 struct F3 {
@@ -395,25 +401,29 @@ struct RewalkJob {
             atomic_add3(A->gacc, fve.y, b1 * gn);
             atomic_add3(A->gacc, fve.z, b2 * gn);
         }
+        // A forward walk beyond the FP32 walk's range ran in the mixed walk; this FP32 re-walk
+        // may then pass a vertex on the other side: reported when it ends in another face.
+        const bool mixed = A->end_status && (__ldg(A->end_status + q) & SG_ST_MIXED);
+        const bool diverged = mixed && w.f - w.foff != __ldg(A->end_face + q);
+        if (diverged) st |= SG_ST_REWALK_DIVERGED;
         if (GFD) {
             // A walk that stopped at the boundary or at MAX_STEPS, or slid along the boundary
             // (hole avoidance), takes literal walks for all perturbed columns; the par column
-            // is the chord from p' in every case (Round 2 of the paper's batching).
+            // is the chord from p' in every case (Round 2 of the paper's batching).  So does a
+            // re-walk that left the forward's path.  The literal walks of a query the forward
+            // walked in the mixed walk are the mixed walk too (k_bwd_literal40, from the start).
             unsigned split = H.S.split & 7u;
-            if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS)) split = 7u;
+            if (w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS) || diverged) split = 7u;
             A->cols[4 * (int64_t)q] = __uint_as_float(split);  // read by k_bwd_assemble
-            if (split && !(H.S.split & SG_SPLIT_RESTART)) A->rst[2 * (int64_t)q] = make_int4(-1, 0, 0, 0);
+            if (split && !mixed && !(H.S.split & SG_SPLIT_RESTART)) A->rst[2 * (int64_t)q] = make_int4(-1, 0, 0, 0);
             if (split) {
                 st |= SG_ST_GFD_SPLIT;
-                int base = atomicAdd(A->ntask, __popc(split));
+                int32_t *list = mixed ? A->tasks40 : A->tasks;
+                int base = atomicAdd(A->ntask + (mixed ? 4 : 0), __popc(split));
                 for (int k = 0; k < 3; ++k)
-                    if (split & (1u << k)) A->tasks[base++] = (int32_t)((q << 2) | (k + 1));
+                    if (split & (1u << k)) list[base++] = (int32_t)((q << 2) | (k + 1));
             }
         }
-        // a forward walk beyond the FP32 walk's range ran in the mixed walk; this FP32 re-walk
-        // may then pass a vertex on the other side: reported when it ends in another face
-        if (A->end_status && (__ldg(A->end_status + q) & SG_ST_MIXED) && w.f - w.foff != __ldg(A->end_face + q))
-            st |= SG_ST_REWALK_DIVERGED;
         if (A->out_status) A->out_status[q] = st;
     }
 };
@@ -603,6 +613,104 @@ __global__ void __launch_bounds__(128, SG_LITERAL_MINB) k_bwd_literal(BwdArgs A)
     LiteralJob<HOLE> job;
     job.A = &A;
     run_persistent<LiteralJob<HOLE>, SG_LITERAL_REFILL>(A.ntask + 2, (int64_t)*A.ntask, job);
+}
+
+// The literal walks of the swept columns of a query whose forward walk was the mixed walk (a walk
+// beyond the FP32 walk's range): the same two perturbed walks as LiteralJob, from the start, on
+// the mixed walk (walk64.cuh).  The start and the perturbation are FP64 (the perturbed vector
+// v + eps e_perp or the shift eps e_u, e_v is formed exactly, not rounded to FP32), and the
+// column's difference p'' - p' is taken in FP64 face-local coordinates: an FP32 end point would
+// carry an error of the order of 1e-7 of the mesh size into a difference divided by eps.
+struct Literal40Job {
+    const BwdArgs *A;
+    W64 w;
+    int64_t q;
+    int k, phase;
+    double L, d0x, d0y, ux, uy;
+
+    // a walk that ended in the half-edge mode: into its face's frame (FP64)
+    __device__ __forceinline__ void to_face() {
+        if (w.mode == SG48_END) leave48(w, A->P4, dunpack(w.px), dunpack(w.py), dunpack(w.dx), dunpack(w.dy));
+    }
+    __device__ __forceinline__ bool init(int64_t t) {
+        const P64 &P = A->P4;
+        const QueryIn &in = A->in;
+        const int32_t task = A->tasks40[t];
+        q = task >> 2;
+        k = task & 3;
+        const int m = in.mesh_id ? __ldg(in.mesh_id + q) : 0;
+        w.foff = __ldg(P.face_off + m);
+        w.f = w.foff + __ldg(in.face + q);
+        w.lref = (double)__ldg(P.lref + m);
+        w.nearf = (float)(P.tau_near * w.lref);
+        w.snapf = (float)(P.tau_snap * w.lref);
+        w.R = load64(P, w.f);
+        double b0 = __ldg(in.bary + 3 * q), b1 = __ldg(in.bary + 3 * q + 1), b2 = __ldg(in.bary + 3 * q + 2);
+        const double sb = b0 + b1 + b2;
+        b1 = fmax(b1, 0.0) / sb; b2 = fmax(b2, 0.0) / sb;
+        w.px = b1 * w.R.l01 + b2 * w.R.x2x;
+        w.py = b2 * w.R.x2y;
+        const double *fr = P.frm64 + 6 * w.f;
+        const double vx = __ldg(in.v + 3 * q), vy = __ldg(in.v + 3 * q + 1), vz = __ldg(in.v + 3 * q + 2);
+        const double v1 = vx * fr[0] + vy * fr[1] + vz * fr[2], v2 = vx * fr[3] + vy * fr[4] + vz * fr[5];
+        L = sqrt(v1 * v1 + v2 * v2);
+        d0x = v1 / L; d0y = v2 / L;
+        w.st = 0; w.steps = 0; w.ncross = 0; w.hash = SG_FNV_OFFSET; w.mode = 6;
+        if (k == 1) {  // v + eps e_perp, e_perp = perp(d0)
+            const double ev = A->eps_v;
+            const double px = L * d0x - ev * d0y, py = L * d0y + ev * d0x, Lp = sqrt(px * px + py * py);
+            w.dx = px / Lp; w.dy = py / Lp; w.L = Lp;
+            phase = 1;
+        } else {        // p -> p_u = Exp(p, eps e_u) (e_u = corner 0 -> 1, e_v = corner 0 -> 2)
+            ux = k == 2 ? 1.0 : w.R.x2x * w.R.il2;
+            uy = k == 2 ? 0.0 : w.R.x2y * w.R.il2;
+            w.dx = ux; w.dy = uy; w.L = A->eps_p;
+            phase = 0;
+        }
+        return true;
+    }
+    __device__ __forceinline__ bool step() {
+        if (!step40<0>(w, A->P4)) return false;
+        if (phase == 1) return true;
+        // end of p -> p_u: continue with v transported along the short walk (its angle to the
+        // walking direction kept)
+        to_face();
+        const double vc = d0x * ux + d0y * uy, vs = ux * d0y - uy * d0x;
+        const double s_t = (w.st & SG_PARITY_BIT) ? -1.0 : 1.0;
+        const double nx = vc * w.dx - s_t * vs * w.dy, ny = vc * w.dy + s_t * vs * w.dx;
+        w.dx = nx; w.dy = ny; w.L = L; w.mode = 6; w.steps = 0;
+        phase = 1;
+        return false;
+    }
+    __device__ __forceinline__ void finish() {
+        to_face();
+        const P64 &P = A->P4;
+        const EndAdj E = end_adjoint(*A, q, w.foff);
+        // p'' - p' = (x0_a - x0_b) + (px e1_a + py e2_a) - (b1 (x1_b - x0_b) + b2 (x2_b - x0_b))
+        const int4 ta = __ldg(P.fv + w.f), tb = __ldg(P.fv + E.gfe);
+        const float4 a0 = __ldg(P.V + ta.x), c0 = __ldg(P.V + tb.x), c1 = __ldg(P.V + tb.y), c2 = __ldg(P.V + tb.z);
+        const double *fr = P.frm64 + 6 * w.f;
+        const double b1 = __ldg(A->end_bary + 3 * q + 1), b2 = __ldg(A->end_bary + 3 * q + 2);
+        double d[3];
+        const double ax[3] = {a0.x, a0.y, a0.z}, x0[3] = {c0.x, c0.y, c0.z}, x1[3] = {c1.x, c1.y, c1.z},
+                     x2[3] = {c2.x, c2.y, c2.z};
+        for (int i = 0; i < 3; ++i)
+            d[i] = (ax[i] - x0[i]) + (w.px * fr[i] + w.py * fr[3 + i]) - (b1 * (x1[i] - x0[i]) + b2 * (x2[i] - x0[i]));
+        const double dn = d[0] * E.nm.x + d[1] * E.nm.y + d[2] * E.nm.z;
+        const double c = ((d[0] - dn * E.nm.x) * E.g.x + (d[1] - dn * E.nm.y) * E.g.y + (d[2] - dn * E.nm.z) * E.g.z);
+        A->cols[4 * q + k] = (float)(c / (k == 1 ? A->eps_v : A->eps_p));
+        if (A->out_status) atomicOr(A->out_status + q, w.st & (SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_NEAR_VERTEX));
+    }
+};
+
+// resident blocks per SM of the mixed literal walks (the mixed forward walk's residency)
+#ifndef SG_LITERAL40_MINB
+#define SG_LITERAL40_MINB 5
+#endif
+__global__ void __launch_bounds__(128, SG_LITERAL40_MINB) k_bwd_literal40(BwdArgs A) {
+    Literal40Job job;
+    job.A = &A;
+    run_persistent<Literal40Job, SG_LITERAL_REFILL>(A.ntask + 5, (int64_t)A.ntask[4], job);
 }
 
 // Columns the re-walk found unswept are chords from p' (the par column always is); the swept
@@ -813,7 +921,7 @@ unsigned persistent_grid(K kernel, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
 }
 struct BwdLayout {
-    size_t gacc, eacc, cols, tasks, rst, ntask, gpos, lcounts, lkeys, perm, total;
+    size_t gacc, eacc, cols, tasks, tasks40, rst, ntask, gpos, lcounts, lkeys, perm, total;
 };
 // The re-walk takes its queries longest first (the forward's length order, rebuilt here) for
 // batches of at least this many queries, unless opts.sort is 0.
@@ -837,6 +945,7 @@ BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool
     if (estimator == SG_EST_GFD) {
         L.cols = o; o = align_up(o + sizeof(float) * 4 * (size_t)std::max<int64_t>(nq, 1), 256);
         L.tasks = o; o = align_up(o + sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(nq, 1), 256);
+        L.tasks40 = o; o = align_up(o + sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(nq, 1), 256);
         L.rst = o; o = align_up(o + sizeof(int4) * 2 * (size_t)std::max<int64_t>(nq, 1), 256);
     }
     L.total = o;
@@ -910,7 +1019,19 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     if (estimator == SG_EST_GFD) {
         A.cols = (float *)(base + Lw.cols);
         A.tasks = (int32_t *)(base + Lw.tasks);
+        A.tasks40 = (int32_t *)(base + Lw.tasks40);
         A.rst = (int4 *)(base + Lw.rst);
+        // the wide-precision geometry of the mixed literal walks (built with the mesh; re-derived
+        // here after a vertex update)
+        sg_status st64 = sg_geom64_prepare(const_cast<sg_mesh *>(m), s, true);
+        if (st64 != SG_OK) {
+            if (own) cudaFreeAsync(ws, s);
+            return st64;
+        }
+        P64 &Q = A.P4;
+        Q.rec = m->d_rec; Q.half48 = m->d_half48; Q.half = m->d_half; Q.frm = m->d_frm; Q.rec64 = m->d_rec64;
+        Q.frm64 = m->d_frm64; Q.th64 = m->d_th64; Q.fv = m->d_fv; Q.V = m->d_V; Q.face_off = m->d_face_off;
+        Q.lref = m->d_lref; Q.max_steps = r.max_steps; Q.want_hash = 0; Q.tau_near = r.tau_near; Q.tau_snap = r.tau_snap;
     }
     cudaMemsetAsync(A.ntask, 0, 64, s);
     if (lorder) {
@@ -948,6 +1069,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
             k_bwd_assemble_walk<true><<<gw, 128, 0, s>>>(A);
         } else {
             k_bwd_literal<false><<<persistent_grid(k_bwd_literal<false>, 3 * nq), 128, 0, s>>>(A);
+            k_bwd_literal40<<<persistent_grid(k_bwd_literal40, 3 * nq), 128, 0, s>>>(A);
             k_bwd_assemble<false><<<g128, 128, 0, s>>>(A);
             k_bwd_assemble_walk<false><<<gw, 128, 0, s>>>(A);
         }

@@ -268,3 +268,40 @@ def test_autograd_function_routes_gradients():
     assert v.grad is not None and torch.isfinite(v.grad).all()
     assert bary.grad is not None and V.grad is not None
     assert V.grad.abs().sum() > 0
+
+
+@pytest.mark.parametrize("estimator", ["ep", "gfd"])
+def test_backward_on_the_sliver_heightfield(estimator):
+    """Both estimators on a sample of the 4.2M-face sliver heightfield (~1.7k crossings per walk,
+    most walks in the mixed walk under the automatic precision) against the oracle's estimator, per
+    query at 1e-3 relative (of the query's gradient (grad_v, grad_p)), on queries neither side flags.  The literal GFD walks of a query walked
+    by the mixed walk are mixed-precision walks with the perturbation and the column's difference
+    in FP64 (FP32 literal walks carry their ~2e-7 end-point error into a difference divided by
+    eps = 1e-4).  Queries whose FP32 re-walk left the forward's path are reported (their GFD columns
+    are all literal walks, so they are compared as well)."""
+    wl = meshgen.workload(4, scale=3000 / 16777216)
+    X, F = wl.single
+    X32 = parity.as_f32(X)
+    mesh = sg().Mesh(X32, F)
+    q = wl.queries
+    b, v, g = f64(q)
+    om = oracle.Mesh(X32.astype(np.float64), F)
+    r = forward_backward(mesh, q, estimator)
+    ref = (oracle.ep_backward if estimator == "ep" else oracle.gfd_backward)(om, q.face, b, v, g)
+    flag = ((r["fwd_status"] | r["status"] | ref["flags"]) & parity.FLAGS) != 0
+    # error of the query's whole gradient (grad_v, grad_p): on a walk that stops at the boundary
+    # the par column vanishes and the perp column is small (the perturbed ray meets the boundary
+    # edge a short way off), so grad_v alone can be a near-zero vector beside the position columns
+    gg = np.concatenate([r["grad_v"], r["grad_p"]], 1)
+    gr = np.concatenate([ref["grad_v"], ref["grad_p"]], 1)
+    e = rel(gg, gr)
+    ev = rel(r["grad_v"], ref["grad_v"])
+    mixed = (r["fwd_status"] & sg().ST_MIXED) != 0
+    div = (r["status"] & sg().ST_REWALK_DIVERGED) != 0
+    ok = ~flag
+    print(f"heightfield {estimator}: flagged {flag.mean():.3f}, mixed {mixed.mean():.3f}, re-walk diverged "
+          f"{div.mean():.3f}, gradient rel median {np.median(e[ok]):.2e} p99 {np.quantile(e[ok], 0.99):.2e} "
+          f"max {e[ok].max():.2e}; grad_v alone: median {np.median(ev[ok]):.2e} max {ev[ok].max():.2e}")
+    assert ok.mean() > 0.4
+    assert mixed.mean() > 0.9
+    assert (e[ok] <= 1e-3).all(), np.nonzero(ok & (e > 1e-3))[0][:10]
