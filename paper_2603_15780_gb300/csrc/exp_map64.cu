@@ -315,15 +315,21 @@ __global__ void __launch_bounds__(128, SG_WALK48_MINB) k_walk48(Fwd64Args a) {
     run_persistent(a.counter, a.nq, job);
 }
 
-// resident blocks per SM the mixed walk is compiled for
+// resident blocks per SM the mixed walk is compiled for, and the idle lanes its warps refill at
+// (1M queries, mixed walk: 5 blocks 1.146 ms on the 81,920-face sphere and 36.0 ms on the
+// heightfield, 4 blocks 1.276 / 39.6, 6 blocks 1.295 / 37.0; refill at 12 lanes 1.055 / 37.2,
+// at 4 lanes 1.368 / 35.2)
 #ifndef SG_WALK40_MINB
 #define SG_WALK40_MINB 5
+#endif
+#ifndef SG_WALK40_REFILL
+#define SG_WALK40_REFILL 12
 #endif
 template <int NW>
 __global__ void __launch_bounds__(128, SG_WALK40_MINB) k_walk40(Fwd64Args a) {
     Job64<NW, 40> job;
     job.a = &a;
-    run_persistent(a.counter, a.perm2 ? task_n(a) : a.nq, job);
+    run_persistent<Job64<NW, 40>, SG_WALK40_REFILL>(a.counter, a.perm2 ? task_n(a) : a.nq, job);
 }
 
 // Double-float half-edge records from the FP64 face shapes, in the layout of the FP32 half-edge
