@@ -422,8 +422,8 @@ def run_features(args):
     entry (CUDA events, L2 flushed between steps, median of the timed steps):
       trace      sg_exp_map_trace on the icosphere-s6 workload (1M queries, 64 path entries)
                  against sg_exp_map on the same queries;
-      fp64       the full-precision walks (FP64, double-float) on the same workload against the
-                 FP32 walk;
+      fp64       the full-precision walks (FP64, double-float, mixed) on the same workload against
+                 the FP32 walk;
       hole       hole avoidance on the icosphere s6 with 8% of its faces removed (1M queries)
                  against the stopping walk;
       update     sg_mesh_update_vertices on the icosphere s6 (81,920 faces);
@@ -480,6 +480,12 @@ def run_features(args):
     t48 = timed(lambda: sg.exp_map(mesh, face, bary, v, opts=o48, workspace=ws48, out=out48))
     res["double_float"] = {"ms": t48, "geodesics_per_s": nq / (t48 * 1e-3), "vs_fp32": t48 / t_fwd,
                            "vs_fp64": t64 / t48}
+    o40 = sg.default_opts(precision=40)
+    out40 = sg.exp_map(mesh, face, bary, v, opts=o40)
+    ws40 = out40.pop("_workspace")
+    t40 = timed(lambda: sg.exp_map(mesh, face, bary, v, opts=o40, workspace=ws40, out=out40))
+    res["mixed"] = {"ms": t40, "geodesics_per_s": nq / (t40 * 1e-3), "vs_fp32": t40 / t_fwd,
+                    "vs_double_float": t48 / t40}
     # update: positions with fresh radial noise
     rng = np.random.default_rng(5)
     Vn = T(X32 * (1.0 + 0.003 * rng.standard_normal((len(X32), 1))).astype(np.float32))

@@ -260,10 +260,10 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
  * overlaps in time (concurrent streams, several host threads) race on it and must be
  * serialised by the caller.
  * Two more rules keep it allocation-free.  The current device must be the one the mesh was
- * created on (else SG_ERR_INVALID_ARG: the array's address is per device).  Precision 48 and 64
- * walk on FP64 geometry (and, for 48, double-float records) that the first sg_exp_map call with
- * that precision allocates on the mesh; until such a call has been made, this entry point
- * rejects those precisions with SG_ERR_UNSUPPORTED instead of allocating them.
+ * created on (else SG_ERR_INVALID_ARG: the array's address is per device).  The FP64 geometry
+ * and double-float records that the automatic, mixed, double-float and FP64 precisions walk on
+ * are allocated by sg_mesh_create; after a vertex update they are re-derived in place, on
+ * `stream`, by the next call.
  */
 sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
                              const float *bary, const float *v, const float *length, int32_t n_w,
@@ -330,7 +330,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
  *                               tangent planes for a fixed face sequence; exact)
  *   out_status uint32 [nq]      SG_ST_* of the extra walks (GFD) or of the re-walk
  * Asynchronous on `stream`.  Errors: SG_ERR_INVALID_ARG (bad estimator, eps <= 0 for GFD, a
- * required array NULL, nq above 536,869,887), SG_ERR_UNSUPPORTED (precision 48 or 64), SG_ERR_OOM
+ * required array NULL, nq above 536,869,887), SG_ERR_UNSUPPORTED (precision 40, 48 or 64), SG_ERR_OOM
  * (no workspace given and none could be allocated), SG_ERR_CUDA.
  */
 sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, float eps_v, float eps_p,
@@ -416,7 +416,7 @@ sg_status sg_exp_map_steps_backward_workspace_size(const sg_mesh *m, int32_t est
  *             tangent to the start face.  Zero for invalid queries; for a zero vector v the
  *             path is empty and out_u is u projected onto the start face.
  * Asynchronous on `stream`; no scratch.  Errors: SG_ERR_INVALID_ARG (NULL array, n_u out of
- * range), SG_ERR_UNSUPPORTED (opts->precision 48 or 64), SG_ERR_CUDA.
+ * range), SG_ERR_UNSUPPORTED (opts->precision 40, 48 or 64), SG_ERR_CUDA.
  */
 sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face,
                             const float *bary, const float *v, const int32_t *end_face,

@@ -53,6 +53,9 @@ struct FwdArgs {
     // when a query order routed the long queries to the mixed walk: the head of perm it takes
     // (*route_n queries; the persistent FP32 walk's ticket counter starts there)
     const int32_t *route_n;
+    // the mixed walk under the automatic precision: its tasks are the routed head of perm, then
+    // the escalation list (lengths from device memory)
+    int mix_lists;
 };
 
 // Appends query q to the escalation list (warp-aggregated: one atomic per calling warp).
@@ -164,6 +167,46 @@ __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
     FwdJob<NW, ESC, false, AUTO> job;
     job.a = &a;
     run_persistent<FwdJob<NW, ESC, false, AUTO>, SG_WALK_REFILL>(a.counter, a.nq, job);
+}
+
+// The mixed walk (precision 40; walk.cuh, MIX): the FP32 walker with the direction in
+// double-float, a double-float start and the double-float half-edge records.  With mix_lists its
+// tasks are the automatic precision's: perm[0, *route_n), then esc_list[0, *esc_count).
+template <int NW, bool ESC>
+struct MixJob {
+    const FwdArgs *a;
+    Walker w;
+    Carry<NW> cw;
+    int64_t q, n1;
+    __device__ __forceinline__ bool init(int64_t t) {
+        if (a->mix_lists) q = t < n1 ? (int64_t)__ldg(a->perm + t) : (int64_t)__ldg(a->esc_list + (t - n1));
+        else q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
+        w.dxl = 0.f; w.dyl = 0.f;
+        const bool live = walker_init<NW>(a->P, a->in, q, w, cw);
+        if (live) walker_start_mix(a->P, a->in, q, w);
+        return live;
+    }
+    __device__ __forceinline__ bool step() { return walker_step<ESC, false, true>(w, a->P); }
+    __device__ __forceinline__ void finish() {
+        w.st |= SG_ST_MIXED;
+        walker_finish<NW>(*a, q, w, cw);
+    }
+};
+
+#ifndef SG_MIX_MINB
+#define SG_MIX_MINB 4
+#endif
+template <int NW, bool ESC>
+__global__ void __launch_bounds__(256, SG_MIX_MINB) k_walk_mixed(FwdArgs a) {
+    MixJob<NW, ESC> job;
+    job.a = &a;
+    int64_t n = a.nq;
+    job.n1 = 0;
+    if (a.mix_lists) {
+        job.n1 = a.route_n ? __ldg(a.route_n) : 0;
+        n = job.n1 + __ldg(a.esc_count);
+    }
+    run_persistent<MixJob<NW, ESC>, SG_WALK_REFILL>(a.counter, n, job);
 }
 
 // hole avoidance (boundary_mode 1): the boundary handling needs more registers than the
@@ -636,6 +679,32 @@ cudaError_t launch_walk(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int NW>
+cudaError_t launch_mixed(const FwdArgs &a, const sg_opts &o, cudaStream_t s) {
+    int dev = 0, sms = 0, per = o.blocks_per_sm;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per <= 0) {
+        if (o.fp64_escalate) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk_mixed<NW, true>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_walk_mixed<NW, false>, 256, 0);
+        per = std::max(per, 1);
+    }
+    const int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>((a.nq + 255) / 256, 1));
+    if (o.fp64_escalate) k_walk_mixed<NW, true><<<(unsigned)grid, 256, 0, s>>>(a);
+    else k_walk_mixed<NW, false><<<(unsigned)grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_nw(const FwdArgs &a, int n_w, const sg_opts &o, cudaStream_t s) {
+    switch (n_w) {
+        case 0: return launch_mixed<0>(a, o, s);
+        case 1: return launch_mixed<1>(a, o, s);
+        case 2: return launch_mixed<2>(a, o, s);
+        case 3: return launch_mixed<3>(a, o, s);
+        default: return launch_mixed<4>(a, o, s);
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI
@@ -836,6 +905,7 @@ FwdArgs fwd_args(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int
     FwdArgs a{};
     a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.frm = m->d_frm; a.P.half = m->d_half; a.P.V = m->d_V; a.P.face_off = m->d_face_off; a.P.lref = m->d_lref;
     a.P.max_steps = r.max_steps; a.P.tau_near = r.tau_near; a.P.tau_snap = r.tau_snap;
+    a.P.half48 = m->d_half48; a.P.frm64 = m->d_frm64;
     a.nq = nq; a.in.n_mesh = m->n_mesh; a.nF_total = (int32_t)m->nF;
     a.in.mesh_id = mesh_id; a.in.face = face; a.in.bary = bary; a.in.v = v; a.in.length = length; a.in.w = w;
     return a;
@@ -966,9 +1036,16 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
         }
     }
     cudaEvent_t *pev = (cudaEvent_t *)r.prof_events;
+    if (r.precision == 40) {  // the mixed walk over every query, in the chosen order
+        if (pev) cudaEventRecord(pev[0], s);
+        cudaError_t e = launch_mixed_nw(a, n_w, r, s);
+        if (pev) cudaEventRecord(pev[1], s);
+        if (own_ws) cudaFreeAsync(own_ws, s);
+        return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+    }
     if (r.precision >= 40) {
         SgFwdIO io{a.in, nq, out_face, out_bary, out_pos, out_dir, out_w, out_status, out_ncross, out_hash, a.perm,
-                   a.counter, nullptr, nullptr, nullptr, nullptr};
+                   a.counter};
         if (pev) cudaEventRecord(pev[0], s);
         cudaError_t e = sg_launch_walk64(m, io, n_w, r, s);
         if (pev) cudaEventRecord(pev[1], s);
@@ -995,12 +1072,11 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
         // the mixed walk takes the queries the order routed to it (in that order), then those the
         // FP32 walk handed on at its crossing budget; its grid reads the lists' lengths from
         // device memory (no host synchronisation)
-        sg_opts r40 = r;
-        r40.precision = 40;
-        SgFwdIO io{a.in, nq, out_face, out_bary, out_pos, out_dir, out_w, out_status, out_ncross, out_hash,
-                   a.route_n ? a.perm : nullptr, a.counter + SG_CTR_MIXED, nullptr, a.route_n, a.esc_list,
-                   a.esc_count};
-        e = sg_launch_walk64(m, io, n_w, r40, s);
+        FwdArgs am = a;
+        am.counter = a.counter + SG_CTR_MIXED;
+        am.mix_lists = 1;
+        am.P.max_steps = r.max_steps;  // the caller's cap (the FP32 walk's was its crossing budget)
+        e = launch_mixed_nw(am, n_w, r, s);
     }
     if (pev) cudaEventRecord(pev[1], s);
     if (own_ws) cudaFreeAsync(own_ws, s);
@@ -1116,9 +1192,10 @@ extern "C" sg_status sg_exp_map_noalloc(const sg_mesh *m, int64_t nq, const int3
     sg_status st = sg_exp_map_workspace_size(m, nq, &r, &need);
     if (st != SG_OK) return st;
     if (need > SG_NOALLOC_SCRATCH_BYTES) return SG_ERR_OOM;
-    // The FP64 geometry and the double-float records are allocated by the first call on a mesh
-    // that asks for them; this entry point allocates nothing, so it requires them to exist.
-    if (r.precision >= 40 && (!m->d_rec64 || (r.precision <= 48 && !m->d_half48))) return SG_ERR_UNSUPPORTED;
+    // The FP64 geometry and the double-float records are allocated with the mesh (a vertex update
+    // only marks them for re-derivation, which launches kernels and allocates nothing).
+    if ((r.precision == 0 || r.precision >= 40) && (!m->d_rec64 || (r.precision <= 48 && !m->d_half48)))
+        return SG_ERR_UNSUPPORTED;
     r.workspace = scratch;
     r.workspace_bytes = SG_NOALLOC_SCRATCH_BYTES;
     return sg_exp_map(m, nq, mesh_id, face, bary, v, length, n_w, w, out_face, out_bary, out_pos, out_dir, out_w,

@@ -40,19 +40,10 @@ struct Fwd64Args {
     uint64_t *out_hash;
     const int32_t *__restrict__ perm;
     int32_t *counter;
-    // task lists under the automatic precision (SgFwdIO): perm[off1 + t] for t < n1, then perm2
-    const int32_t *off1_dev, *n1_dev, *perm2, *n2_dev;
 };
 
-// number of tasks of the first list (the rest come from perm2)
-__device__ __forceinline__ int64_t task_n1(const Fwd64Args &a) {
-    if (a.n1_dev) return __ldg(a.n1_dev);
-    if (a.off1_dev) return a.nq - __ldg(a.off1_dev);
-    return a.perm2 ? 0 : a.nq;
-}
-__device__ __forceinline__ int64_t task_n(const Fwd64Args &a) { return task_n1(a) + (a.n2_dev ? __ldg(a.n2_dev) : 0); }
 
-// PREC 64: the FP64 walk; 48: the double-float walk; 40: the mixed walk
+// PREC 64: the FP64 walk; 48: the double-float walk
 template <int NW, int PREC = 64>
 struct Job64 {
     static constexpr bool DFW = PREC != 64;
@@ -62,13 +53,7 @@ struct Job64 {
     int64_t q;
 
     __device__ __forceinline__ bool init(int64_t t) {
-        if (a->perm2) {  // the automatic precision's lists
-            const int64_t n1 = task_n1(*a);
-            if (t < n1) q = __ldg(a->perm + (a->off1_dev ? __ldg(a->off1_dev) : 0) + t);
-            else q = __ldg(a->perm2 + (t - n1));
-        } else {
-            q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
-        }
+        q = a->perm ? (int64_t)__ldg(a->perm + t) : t;
         const P64 &P = a->P;
         const QueryIn &in = a->in;
         const int m = in.mesh_id ? __ldg(in.mesh_id + q) : 0;
@@ -210,7 +195,7 @@ struct Job64 {
         return 1;
     }
     __device__ __forceinline__ bool step() {
-        return PREC == 40 ? step40<NW>(w, a->P) : (PREC == 48 ? step48<NW>(w, a->P) : step64<NW>(w, a->P));
+        return PREC == 48 ? step48<NW>(w, a->P) : step64<NW>(w, a->P);
     }
     // The end of a double-float walk that stopped inside a face in the half-edge mode: the
     // outputs (float32) from the double-float end point, with FP32 rotations and frames.
@@ -251,8 +236,7 @@ struct Job64 {
                 o[2] = u1 * fa.z + u2 * fb.y;
             }
         }
-        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u) |
-                          (PREC == 40 ? SG_ST_MIXED : 0u);
+        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u);
         if (A.out_ncross) A.out_ncross[q] = w.ncross;
         if (A.out_hash) A.out_hash[q] = w.hash;
     }
@@ -289,8 +273,7 @@ struct Job64 {
                 o[2] = (float)(u1 * fr[2] + u2 * fr[5]);
             }
         }
-        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u) |
-                          (PREC == 40 ? SG_ST_MIXED : 0u);
+        A.out_status[q] = (w.st & ~SG_PARITY_BIT) | ((w.st & SG_PARITY_BIT) ? SG_ST_FLIPPED : 0u);
         if (A.out_ncross) A.out_ncross[q] = w.ncross;
         if (A.out_hash) A.out_hash[q] = w.hash;
     }
@@ -313,23 +296,6 @@ __global__ void __launch_bounds__(128, SG_WALK48_MINB) k_walk48(Fwd64Args a) {
     Job64<NW, 48> job;
     job.a = &a;
     run_persistent(a.counter, a.nq, job);
-}
-
-// resident blocks per SM the mixed walk is compiled for, and the idle lanes its warps refill at
-// (1M queries, mixed walk: 5 blocks 1.146 ms on the 81,920-face sphere and 36.0 ms on the
-// heightfield, 4 blocks 1.276 / 39.6, 6 blocks 1.295 / 37.0; refill at 12 lanes 1.055 / 37.2,
-// at 4 lanes 1.368 / 35.2)
-#ifndef SG_WALK40_MINB
-#define SG_WALK40_MINB 5
-#endif
-#ifndef SG_WALK40_REFILL
-#define SG_WALK40_REFILL 12
-#endif
-template <int NW>
-__global__ void __launch_bounds__(128, SG_WALK40_MINB) k_walk40(Fwd64Args a) {
-    Job64<NW, 40> job;
-    job.a = &a;
-    run_persistent<Job64<NW, 40>, SG_WALK40_REFILL>(a.counter, a.perm2 ? task_n(a) : a.nq, job);
 }
 
 // Double-float half-edge records from the FP64 face shapes, in the layout of the FP32 half-edge
@@ -458,7 +424,6 @@ cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const
     a.out_face = io.out_face; a.out_bary = io.out_bary; a.out_pos = io.out_pos; a.out_dir = io.out_dir;
     a.out_w = io.out_w; a.out_status = io.out_status; a.out_ncross = io.out_ncross; a.out_hash = io.out_hash;
     a.perm = io.perm; a.counter = io.counter;
-    a.off1_dev = io.off1_dev; a.n1_dev = io.n1_dev; a.perm2 = io.perm2; a.n2_dev = io.n2_dev;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -471,15 +436,7 @@ cudaError_t sg_launch_walk64(const sg_mesh *m, const SgFwdIO &io, int n_w, const
         const int64_t grid = std::min<int64_t>((int64_t)sms * per, std::max<int64_t>((io.nq + 127) / 128, 1));
         kern<<<(unsigned)grid, 128, 0, s>>>(a);
     };
-    if (r.precision == 40) {
-        switch (n_w) {
-            case 0: go(k_walk40<0>); break;
-            case 1: go(k_walk40<1>); break;
-            case 2: go(k_walk40<2>); break;
-            case 3: go(k_walk40<3>); break;
-            default: go(k_walk40<4>); break;
-        }
-    } else if (r.precision == 48) {
+    if (r.precision == 48) {
         switch (n_w) {
             case 0: go(k_walk48<0>); break;
             case 1: go(k_walk48<1>); break;

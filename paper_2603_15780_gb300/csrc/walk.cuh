@@ -89,6 +89,9 @@ struct WalkParams {
     int max_steps;
     float tau_near, tau_snap;
     int want_hash;
+    // the mixed walk's double-float half-edge records and FP64 face axes (NULL elsewhere)
+    const int4 *__restrict__ half48;
+    const double *__restrict__ frm64;
 };
 
 // Walker state (all registers).  mode 7: on the entry edge of half-edge h (the hot case; R
@@ -110,6 +113,7 @@ struct Walker {
     float lref;
     uint64_t hash;
     FaceRec R;
+    float dxl, dyl;      // mixed walk: low parts of the direction (double-float d = dx + dxl, ...)
 };
 
 __device__ __forceinline__ float sigma32(float dx, float dy, float cx, float cy, float px, float py) {
@@ -139,6 +143,97 @@ __device__ __forceinline__ void renorm(float &x, float &y) {
     float r = rsqrtf(n2);
     r = r * fmaf(-0.5f * n2 * r, r, 1.5f);  // one Newton step
     x *= r; y *= r;
+}
+
+// ------------------------------------------------------------------ double-float arithmetic
+// Error-free transformations: Knuth's two-sum (TAOCP vol. 2, sec. 4.2.2), Dekker's fast two-sum
+// (Dekker 1971, |a| >= |b|) and the exact product by one fused multiply-add.  Built on them, the
+// double-float sum, product and quotient keep about 2^-46 relative error.  Each function below
+// has a float32 numpy twin of the same name, operation for operation, in
+// tests/test_double_float_arith.py, which checks these error bounds on the CPU; a change here
+// goes there too.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = a * b;
+    return DF{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+// the sum with both parts summed exactly: accurate under cancellation (c - x near a vertex)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    const DF t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+// the sum of two terms of equal sign (no cancellation): one two-sum of the high parts suffices
+__device__ __forceinline__ DF df_add_same_sign(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    DF p = two_prod(a.hi, b.hi);
+    p.lo = fmaf(a.hi, b.lo, p.lo);
+    p.lo = fmaf(a.lo, b.hi, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    DF p = two_prod(a.hi, b);
+    p.lo = fmaf(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+// quotient by long division: two FP32 quotient digits (the second from the remainder, formed
+// in double-float) with one correctly rounded reciprocal of the divisor's high part
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float rb = __frcp_rn(b.hi);
+    const float q1 = a.hi * rb;
+    const DF r = df_sub(a, df_mul_f(b, q1));
+    return fast_two_sum(q1, r.hi * rb);
+}
+// 1/sqrt(n): the FP32 estimate refined by one Newton step r + r (1 - n r^2) / 2, which squares
+// its relative error
+__device__ __forceinline__ DF df_rsqrt(DF n) {
+    const float r = rsqrtf(n.hi);
+    const DF e = df_sub(DF{1.f, 0.f}, df_mul(n, two_prod(r, r)));
+    return fast_two_sum(r, 0.5f * r * e.hi);
+}
+__device__ __forceinline__ DF df_from(double x) {
+    const float hi = (float)x;
+    return DF{hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ bool df_ge(DF a, DF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+// a double-float pair in one double register pair (the low word holds hi), so the half-edge mode
+// reuses the FP64 state's registers
+__device__ __forceinline__ double dpack(DF a) { return __hiloint2double(__float_as_int(a.lo), __float_as_int(a.hi)); }
+__device__ __forceinline__ DF dunpack(double d) {
+    return DF{__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d))};
+}
+
+// a b + c d in double-float: the two exact products summed by one two-sum, all cross terms and
+// rounding errors gathered into the low part
+__device__ __forceinline__ DF df_dot2(DF a, DF b, DF c, DF d) {
+    const DF p = two_prod(a.hi, b.hi), q = two_prod(c.hi, d.hi);
+    DF s = two_sum(p.hi, q.hi);
+    float lo = s.lo + (p.lo + q.lo);
+    lo = fmaf(a.hi, b.lo, lo);
+    lo = fmaf(a.lo, b.hi, lo);
+    lo = fmaf(c.hi, d.lo, lo);
+    lo = fmaf(c.lo, d.hi, lo);
+    return fast_two_sum(s.hi, lo);
 }
 
 // ------------------------------------------------------------------ hole avoidance
@@ -474,11 +569,17 @@ struct NoHook {
 
 // Leave the half-edge frame: position (xe, ye) and direction into the face frame of w.f,
 // R becomes the face record (needed at the end of a walk and before a vertex transport).
+template <bool MIX = false>
 __device__ __forceinline__ void half_to_face(Walker &w, const WalkParams &P, float xe, float ye) {
-    const float ca = hca(w.R), sa = hsa(w.R);
+    float ca = MIX ? 1.f : hca(w.R), sa = MIX ? 0.f : hsa(w.R);
     w.f = w.h / 3;  // not kept up to date on the hot path
     const int k = w.h - 3 * w.f;
     const FaceRec F = load_rec(P.rec, w.f);
+    if (MIX) {  // the double-float record holds no rotation: edge k's direction in the face frame
+        if (k == 1) { ca = (F.x2x - F.l01) * F.il1; sa = F.x2y * F.il1; }
+        else if (k == 2) { ca = -F.x2x * F.il2; sa = -F.x2y * F.il2; }
+        w.dxl = 0.f; w.dyl = 0.f;
+    }
     w.px = corner_x(F, k) + ca * xe - sa * ye;
     w.py = corner_y(F, k) + sa * xe + ca * ye;
     const float dx = ca * w.dx - sa * w.dy, dy = sa * w.dx + ca * w.dy;
@@ -493,22 +594,34 @@ __device__ __forceinline__ void half_to_face(Walker &w, const WalkParams &P, flo
 // (sigma_C > 0), else C -> A.  The twin half-edge's frame has the crossed edge as its x axis
 // (reversed unless the adjacency is flipped) and the new face on +y, so the new direction is
 // (-+ d.e, d.n_out) / |e|, renormalised; no corner lookups are needed.
-template <bool ESC, bool HOLE, class Hook>
+// MIX: the mixed walk -- the same step on the double-float half-edge record (l, cx, cy as hi + lo
+// pairs and the two links, one 32-byte sector), the orientation tests, exit point and length in
+// FP32 from the high parts, and the direction carried in double-float: its rotation into the next
+// edge frame uses the double-float exit edge vector and double-float dot products, so the
+// direction's error does not grow with the path (the FP32 walk's does).
+template <bool ESC, bool HOLE, bool MIX, class Hook>
 __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &hook) {
     const FaceRec &R = w.R;
     const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
-    const float L0 = hl(R), cx = hcx(R), cy = hcy(R);
+    const float L0 = MIX ? __int_as_float(R.n0) : hl(R);
+    const float cx = MIX ? __int_as_float(R.n2) : hcx(R);
+    const float cy = MIX ? R.x2x : hcy(R);
     const float x = w.px * L0;
     float sA = w.dy * x;
     float sB = -w.dy * (L0 - x);
     float sC = fmaf(w.dx, cy, -w.dy * (cx - x));
     if (ESC && fabsf(sC) < near) {
-        // FP64 re-evaluation of the classification (exact products of the FP32 state)
+        // FP64 re-evaluation of the classification (exact products of the walker's state)
         w.st |= SG_ST_FP64;
-        const double X = (double)w.px * (double)L0;
-        sA = f32_keep_sign((double)w.dy * X);
-        sB = f32_keep_sign(-(double)w.dy * ((double)L0 - X));
-        sC = f32_keep_sign((double)w.dx * (double)cy - (double)w.dy * ((double)cx - X));
+        const double Ld = MIX ? (double)L0 + (double)__int_as_float(R.n1) : (double)L0;
+        const double cxd = MIX ? (double)cx + (double)R.l01 : (double)cx;
+        const double cyd = MIX ? (double)cy + (double)R.x2y : (double)cy;
+        const double dxd = MIX ? (double)w.dx + (double)w.dxl : (double)w.dx;
+        const double dyd = MIX ? (double)w.dy + (double)w.dyl : (double)w.dy;
+        const double X = (double)w.px * Ld;
+        sA = f32_keep_sign(dyd * X);
+        sB = f32_keep_sign(-dyd * (Ld - X));
+        sC = f32_keep_sign(dxd * cyd - dyd * (cxd - X));
     }
     const bool hit = fabsf(sC) <= snap;  // a snapped apex is a hit, not a near miss
     if (!hit && fabsf(sC) < near) w.st |= SG_ST_NEAR_VERTEX;
@@ -534,7 +647,7 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         // final truncated in-face segment (reading: stop once the length is used up)
         const float xe = fmaf(L, w.dx, x), ye = L * w.dy;
         w.Lh = 0.f; w.Ll = 0.f;
-        half_to_face(w, P, xe, ye);
+        half_to_face<MIX>(w, P, xe, ye);
         const FaceRec &F = w.R;
         float d0 = fabsf(w.py);
         float d1 = fabsf((F.x2x - F.l01) * (w.py) - F.x2y * (w.px - F.l01)) * F.il1;
@@ -549,14 +662,14 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         w.Lh = sum;
     }
     if (hit) {
-        half_to_face(w, P, cx, cy);
+        half_to_face<MIX>(w, P, cx, cy);
         const int c = prv(w.h - 3 * w.f);  // the apex is corner k+2 of the face
         hook.on_vertex(w, c);
         return !vertex_transport<HOLE>(w, c, P);
     }
-    const int link = right ? hlinkR(R) : hlinkL(R);
+    const int link = MIX ? (right ? __float_as_int(R.il1) : __float_as_int(R.il2)) : (right ? hlinkR(R) : hlinkL(R));
     if (link < 0) {  // boundary edge: original rule stops (Sec. 4), or hole avoidance
-        half_to_face(w, P, qx, qy);
+        half_to_face<MIX>(w, P, qx, qy);
         const int k = w.h - 3 * w.f;
         if (HOLE) {  // handled by hole_resolve on a later call
             w.mode = SG_MODE_HOLE_EDGE + (right ? nxt(k) : prv(k));
@@ -566,15 +679,30 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         return true;
     }
     const int hn = link >> 1, fl = link & 1;
-    const float ex = x1 - x0, ey = y1 - y0;
-    const float da = fmaf(w.dx, ex, w.dy * ey);   // |e| (d . e_hat)
-    const float dc = fmaf(w.dx, ey, -w.dy * ex);  // |e| (d . n_out)
-    const FaceRec G = load_rec<true>(P.half, hn);
-    // |(da, dc)| = |e|: one reciprocal square root normalises it (rsqrtf's error, a few 1e-7,
-    // does not accumulate: every step renormalises the direction it receives)
-    const float re = rsqrtf(fmaf(da, da, dc * dc));
-    const float ndx = (fl ? da : -da) * re, ndy = dc * re;
-    {
+    float ndx, ndy, re;
+    if (MIX) {
+        // the exit edge in double-float: B -> C = (cx - l, cy), C -> A = -(cx, cy)
+        const DF Ld{L0, __int_as_float(R.n1)}, cxd{cx, R.l01}, cyd{cy, R.x2y};
+        const DF dxd{w.dx, w.dxl}, dyd{w.dy, w.dyl};
+        const DF ex = right ? df_sub(cxd, Ld) : df_neg(cxd), ey = right ? cyd : df_neg(cyd);
+        const DF da = df_dot2(dxd, ex, dyd, ey);            // |e| (d . e_hat)
+        const DF dc = df_dot2(dxd, ey, df_neg(dyd), ex);    // |e| (d . n_out)
+        // one FP32 scale for both components keeps the angle to double-float precision
+        re = rsqrtf(fmaf(da.hi, da.hi, dc.hi * dc.hi));
+        const DF nx = df_mul_f(fl ? da : df_neg(da), re), ny = df_mul_f(dc, re);
+        ndx = nx.hi; ndy = ny.hi;
+        w.dxl = nx.lo; w.dyl = ny.lo;
+    } else {
+        const float ex = x1 - x0, ey = y1 - y0;
+        const float da = fmaf(w.dx, ex, w.dy * ey);   // |e| (d . e_hat)
+        const float dc = fmaf(w.dx, ey, -w.dy * ex);  // |e| (d . n_out)
+        // |(da, dc)| = |e|: one reciprocal square root normalises it (rsqrtf's error, a few 1e-7,
+        // does not accumulate: every step renormalises the direction it receives)
+        re = rsqrtf(fmaf(da, da, dc * dc));
+        ndx = (fl ? da : -da) * re; ndy = dc * re;
+    }
+    const FaceRec G = load_rec<true>(MIX ? P.half48 : P.half, hn);
+    if (!MIX) {
         const int k = w.h - 3 * (w.h / 3);
         const int g = hn / 3;
         hook.on_cross(w, Cross{right ? nxt(k) : prv(k), x0, y0, x1, y1, qx, qy, w.Lh + w.Ll, g, hn - 3 * g, fl,
@@ -592,26 +720,27 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     return false;
 }
 
-template <bool ESC, bool HOLE, class Hook>
+template <bool ESC, bool HOLE, bool MIX, class Hook>
 __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hook &hook);
 
 // One step of Alg. geodesic_step.  Returns true when the walk is finished.
-template <bool ESC, bool HOLE = false, class Hook = NoHook>
+template <bool ESC, bool HOLE = false, bool MIX = false, class Hook = NoHook>
 __device__ __forceinline__ bool walker_step(Walker &w, const WalkParams &P, Hook &&hook = Hook()) {
     if (HOLE && w.mode >= SG_MODE_HOLE_EDGE) return hole_resolve(w, P);  // a pending boundary event
     if (w.steps >= P.max_steps) {
-        if (w.mode == SG_MODE_HALF) half_to_face(w, P, w.px * hl(w.R), 0.f);
+        if (w.mode == SG_MODE_HALF)
+            half_to_face<MIX>(w, P, w.px * (MIX ? __int_as_float(w.R.n0) : hl(w.R)), 0.f);
         w.st |= SG_ST_MAX_STEPS;
         return true;
     }
     w.steps++;
-    if (w.mode == SG_MODE_HALF) return half_step<ESC, HOLE>(w, P, hook);
-    return general_step<ESC, HOLE>(w, P, hook);
+    if (w.mode == SG_MODE_HALF) return half_step<ESC, HOLE, MIX>(w, P, hook);
+    return general_step<ESC, HOLE, MIX>(w, P, hook);
 }
 
 // Step from a corner (after a vertex transport) or from a free start point (face frame); a
 // crossing moves the walker into the half-edge frame of the face it enters.
-template <bool ESC, bool HOLE, class Hook>
+template <bool ESC, bool HOLE, bool MIX, class Hook>
 __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hook &hook) {
     const FaceRec &R = w.R;
     const float near = P.tau_near * w.lref, snap = P.tau_snap * w.lref;
@@ -717,12 +846,16 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
     const float da = fmaf(w.dx, ex, w.dy * ey);
     const float dc = fmaf(w.dx, ey, -w.dy * ex);  // d . (ey, -ex)
     const int hn = 3 * g + kp;
-    const FaceRec G = load_rec<true>(P.half, hn);
+    const FaceRec G = load_rec<true>(MIX ? P.half48 : P.half, hn);
     float ndx = fl ? da : -da, ndy = dc;
     renorm(ndx, ndy);
-    hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, 0.f, 0.f, hl(G), 0.f, ndx, ndy,
-                           1.f, 0.f, hca(G), hsa(G), rsqrtf(fmaf(bx - ax, bx - ax, (by - ay) * (by - ay)))},
-                  G);
+    if (MIX) {  // a face-frame step (a start on an edge or vertex, a vertex transport) is FP32
+        w.dxl = 0.f; w.dyl = 0.f;
+    } else {
+        hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, 0.f, 0.f, hl(G), 0.f, ndx, ndy,
+                               1.f, 0.f, hca(G), hsa(G), rsqrtf(fmaf(bx - ax, bx - ax, (by - ay) * (by - ay)))},
+                      G);
+    }
     w.px = fl ? s : 1.f - s;
     w.py = 0.f;
     w.dx = ndx; w.dy = ndy;
@@ -758,11 +891,6 @@ struct SgFwdIO {
     uint64_t *out_hash;
     const int32_t *perm;
     int32_t *counter;
-    // Task lists of the mixed walk under the automatic precision (device counts, written by
-    // earlier kernels on the stream): tasks [0, n1) are perm[off1 + t], with n1 = *n1_dev, or
-    // nq - *off1_dev when n1_dev is NULL; tasks [n1, n1 + *n2_dev) are perm2[t - n1].  All NULL:
-    // tasks [0, nq) are perm[t] (or t).
-    const int32_t *off1_dev, *n1_dev, *perm2, *n2_dev;
 };
 sg_status sg_geom64_prepare(sg_mesh *m, cudaStream_t s, bool half48);
 // Length order of a batch (exp_map.cu): perm[0 .. nq) = the queries longest walk first, in
@@ -886,6 +1014,75 @@ __device__ bool walker_init(const WalkParams &P, const QueryIn &a, int64_t q, Wa
     return L > 0.f;
 }
 
+
+// The mixed walk's start, after walker_init placed a free start point: the start direction and
+// length in double-float from the FP64 face axes (an FP32 start direction would carry its rounding,
+// about 6e-8 rad, over the whole walk), and the walker placed on the edge through which its ray
+// enters the start face (behind the start point, the length extended by that distance), so that
+// the walk begins in the half-edge mode.  Declined (the FP32 start stays, with no low parts) for a
+// start on an edge or vertex, a zero or huge vector, or an entry-edge corner within the near band
+// of the ray line.
+__device__ __forceinline__ void walker_start_mix(const WalkParams &P, const QueryIn &in, int64_t q, Walker &w) {
+    w.dxl = 0.f; w.dyl = 0.f;
+    if (w.mode != 6) return;
+    const float b0 = __ldg(in.bary + 3 * q), b1 = __ldg(in.bary + 3 * q + 1), b2 = __ldg(in.bary + 3 * q + 2);
+    if (!(b0 > 0.f && b1 > 0.f && b2 > 0.f)) return;
+    int4 ra, rb;
+    ld_rec32<true>(P.half48 + 2 * (3 * w.f), ra, rb);  // half-edge 0 of the face: its frame is the face's
+    const DF l01{__int_as_float(ra.x), __int_as_float(ra.y)}, x2x{__int_as_float(ra.z), __int_as_float(ra.w)};
+    const DF x2y{__int_as_float(rb.x), __int_as_float(rb.y)};
+    const DF sb = df_add(two_sum(b0, b1), DF{b2, 0.f});
+    const DF rs = df_div(DF{1.f, 0.f}, sb);
+    const DF B1 = df_mul_f(rs, b1), B2 = df_mul_f(rs, b2);
+    const DF px = df_add_same_sign(df_mul(B1, l01), df_mul(B2, x2x)), py = df_mul(B2, x2y);
+    const double *fr = P.frm64 + 6 * w.f;
+    const double vx = __ldg(in.v + 3 * q), vy = __ldg(in.v + 3 * q + 1), vz = __ldg(in.v + 3 * q + 2);
+    const DF V1 = df_from(vx * __ldg(fr) + vy * __ldg(fr + 1) + vz * __ldg(fr + 2));
+    const DF V2 = df_from(vx * __ldg(fr + 3) + vy * __ldg(fr + 4) + vz * __ldg(fr + 5));
+    const DF n2 = df_add_same_sign(df_mul(V1, V1), df_mul(V2, V2));
+    if (!(n2.hi > 1e-30f && n2.hi < 1e30f)) return;
+    const DF rn = df_rsqrt(n2);
+    const DF dx = df_mul(V1, rn), dy = df_mul(V2, rn);
+    DF L = df_mul(n2, rn);
+    if (in.length) {
+        const float Li = __ldg(in.length + q);
+        if (!(Li > 0.f && Li < 1e30f)) return;
+        L = DF{Li, 0.f};
+    }
+    // corners' signed distances to the ray line; the ray enters through edge j (corner j on its
+    // left, corner j+1 on its right)
+    const DF zero{0.f, 0.f};
+    const DF s0 = df_sub(df_mul(dy, px), df_mul(dx, py));
+    const DF s1 = df_sub(df_mul(dx, df_neg(py)), df_mul(dy, df_sub(l01, px)));
+    const DF s2 = df_sub(df_mul(dx, df_sub(x2y, py)), df_mul(dy, df_sub(x2x, px)));
+    int j;
+    if (s0.hi > 0.f && s1.hi <= 0.f) j = 0;
+    else if (s1.hi > 0.f && s2.hi <= 0.f) j = 1;
+    else if (s2.hi > 0.f && s0.hi <= 0.f) j = 2;
+    else return;
+    const float nearf = P.tau_near * w.lref;
+    const DF sa = j == 0 ? s0 : (j == 1 ? s1 : s2), sbb = j == 0 ? s1 : (j == 1 ? s2 : s0);
+    if (fabsf(sa.hi) < nearf || fabsf(sbb.hi) < nearf) return;
+    const DF ax = j == 0 ? zero : (j == 1 ? l01 : x2x), ay = j == 2 ? x2y : zero;
+    const DF bx = j == 0 ? l01 : (j == 1 ? x2x : zero), by = j == 1 ? x2y : zero;
+    const DF ex = df_sub(bx, ax), ey = df_sub(by, ay);
+    const DF se = df_div(sa, df_add_same_sign(sa, df_neg(sbb)));
+    const DF qx = df_add(ax, df_mul(se, ex)), qy = df_add(ay, df_mul(se, ey));
+    DF tb = df_add(df_mul(df_sub(px, qx), dx), df_mul(df_sub(py, qy), dy));
+    if (tb.hi < 0.f) tb = zero;
+    const DF il = df_rsqrt(df_add_same_sign(df_mul(ex, ex), df_mul(ey, ey)));
+    const DF hx = df_mul(df_add(df_mul(dx, ex), df_mul(dy, ey)), il);
+    const DF hy = df_mul(df_sub(df_mul(ex, dy), df_mul(ey, dx)), il);
+    if (!(hy.hi > 0.f)) return;
+    const DF Lx = df_add_same_sign(L, tb);
+    w.h = 3 * w.f + j;
+    w.R = load_rec<true>(P.half48, w.h);
+    w.px = se.hi; w.py = 0.f;
+    w.dx = hx.hi; w.dxl = hx.lo;
+    w.dy = hy.hi; w.dyl = hy.lo;
+    w.Lh = Lx.hi; w.Ll = Lx.lo;
+    w.mode = SG_MODE_HALF;
+}
 
 // ------------------------------------------------------------------ persistent driver
 // warp-aggregated ticket: the calling lanes get consecutive queue positions

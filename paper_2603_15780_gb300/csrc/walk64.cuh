@@ -245,80 +245,6 @@ __device__ bool step64(W64 &w, const P64 &P) {
 }
 
 // ------------------------------------------------------------------ double-float walk
-// Error-free transformations: Knuth's two-sum (TAOCP vol. 2, sec. 4.2.2), Dekker's fast two-sum
-// (Dekker 1971, |a| >= |b|) and the exact product by one fused multiply-add.  Built on them, the
-// double-float sum, product and quotient keep about 2^-46 relative error.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ DF two_sum(float a, float b) {
-    const float s = a + b, bb = s - a;
-    return DF{s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {
-    const float s = a + b;
-    return DF{s, b - (s - a)};
-}
-__device__ __forceinline__ DF two_prod(float a, float b) {
-    const float p = a * b;
-    return DF{p, fmaf(a, b, -p)};
-}
-__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
-// the sum with both parts summed exactly: accurate under cancellation (c - x near a vertex)
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    DF s = two_sum(a.hi, b.hi);
-    const DF t = two_sum(a.lo, b.lo);
-    s.lo += t.hi;
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
-    return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
-// the sum of two terms of equal sign (no cancellation): one two-sum of the high parts suffices
-__device__ __forceinline__ DF df_add_same_sign(DF a, DF b) {
-    DF s = two_sum(a.hi, b.hi);
-    s.lo += a.lo + b.lo;
-    return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-    DF p = two_prod(a.hi, b.hi);
-    p.lo = fmaf(a.hi, b.lo, p.lo);
-    p.lo = fmaf(a.lo, b.hi, p.lo);
-    return fast_two_sum(p.hi, p.lo);
-}
-__device__ __forceinline__ DF df_mul_f(DF a, float b) {
-    DF p = two_prod(a.hi, b);
-    p.lo = fmaf(a.lo, b, p.lo);
-    return fast_two_sum(p.hi, p.lo);
-}
-// quotient by long division: two FP32 quotient digits (the second from the remainder, formed
-// in double-float) with one correctly rounded reciprocal of the divisor's high part
-__device__ __forceinline__ DF df_div(DF a, DF b) {
-    const float rb = __frcp_rn(b.hi);
-    const float q1 = a.hi * rb;
-    const DF r = df_sub(a, df_mul_f(b, q1));
-    return fast_two_sum(q1, r.hi * rb);
-}
-// 1/sqrt(n): the FP32 estimate refined by one Newton step r + r (1 - n r^2) / 2, which squares
-// its relative error
-__device__ __forceinline__ DF df_rsqrt(DF n) {
-    const float r = rsqrtf(n.hi);
-    const DF e = df_sub(DF{1.f, 0.f}, df_mul(n, two_prod(r, r)));
-    return fast_two_sum(r, 0.5f * r * e.hi);
-}
-__device__ __forceinline__ DF df_from(double x) {
-    const float hi = (float)x;
-    return DF{hi, (float)(x - (double)hi)};
-}
-__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ bool df_ge(DF a, DF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
-// a double-float pair in one double register pair (the low word holds hi), so the half-edge mode
-// reuses the FP64 state's registers
-__device__ __forceinline__ double dpack(DF a) { return __hiloint2double(__float_as_int(a.lo), __float_as_int(a.hi)); }
-__device__ __forceinline__ DF dunpack(double d) {
-    return DF{__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d))};
-}
-
 #define SG48_HALF 7
 // the walk ended inside a face in the half-edge mode: px, py hold the end point in the edge frame
 #define SG48_END 8
@@ -493,19 +419,6 @@ __device__ __forceinline__ bool step48(W64 &w, const P64 &P) {
 // Walker registers in the mixed half-edge mode: as in the double-float mode (px = the fraction s
 // along the entry edge, (dx, dy) the direction, L the remaining length, all packed pairs), with
 // only the high word of s and the pair L = Lh + Ll updated by FP32 steps.
-
-// a b + c d in double-float: the two exact products summed by one two-sum, all cross terms and
-// rounding errors gathered into the low part
-__device__ __forceinline__ DF df_dot2(DF a, DF b, DF c, DF d) {
-    const DF p = two_prod(a.hi, b.hi), q = two_prod(c.hi, d.hi);
-    DF s = two_sum(p.hi, q.hi);
-    float lo = s.lo + (p.lo + q.lo);
-    lo = fmaf(a.hi, b.lo, lo);
-    lo = fmaf(a.lo, b.hi, lo);
-    lo = fmaf(c.hi, d.lo, lo);
-    lo = fmaf(c.lo, d.hi, lo);
-    return fast_two_sum(s.hi, lo);
-}
 
 template <int NW>
 __device__ bool half40(W64 &w, const P64 &P) {

@@ -1,8 +1,11 @@
 """Precision of the double-float arithmetic the double-float walk (sg_opts.precision = 48) is
 built on, checked on the CPU: each value an unevaluated sum hi + lo of two float32 numbers,
 Knuth's two-sum, Dekker's fast two-sum and the exact product (an FMA on the GPU; here the
-float64 product of two float32 numbers, which is exact), and from them the sum, product,
-quotient and reciprocal square root in the forms the walk uses.  Their results are compared with
+float64 product of two float32 numbers, which is exact), and from them the sum, the sum of two
+terms of one sign, the two-term dot product, product, quotient and reciprocal square root in the
+forms the walks use.  Each function here restates, operation for operation, the device function
+of the same name in paper_2603_15780_gb300/csrc/walk.cuh (its FMA as a float64 multiply-add
+rounded once to float32).  Their results are compared with
 float64 references (whose own error, about 1e-16, is far below the bounds) over random operands
 spanning the magnitudes a walk meets."""
 import numpy as np
@@ -37,6 +40,24 @@ def df_add(a, b):
     s, e = fast_two_sum(s, e)
     e = f32(e + f)
     return fast_two_sum(s, e)
+
+
+def df_add_same_sign(a, b):
+    s, e = two_sum(a[0], b[0])
+    e = f32(e + f32(a[1] + b[1]))
+    return fast_two_sum(s, e)
+
+
+def df_dot2(a, b, c, d):
+    p, pe = two_prod(a[0], b[0])
+    q, qe = two_prod(c[0], d[0])
+    s, e = two_sum(p, q)
+    lo = f32(e + f32(pe + qe))
+    lo = fma(a[0], b[1], lo)
+    lo = fma(a[1], b[0], lo)
+    lo = fma(c[0], d[1], lo)
+    lo = fma(c[1], d[0], lo)
+    return fast_two_sum(s, lo)
 
 
 def df_mul(a, b):
@@ -124,3 +145,30 @@ def test_sum_is_accurate_under_cancellation():
         a, b = split(x), split(y)
         err = abs(val(df_add(a, b)) - (val(a) + val(b)))
         assert err <= 2.0 ** -46 * abs(x)
+
+
+def test_same_sign_sum_and_dot_product():
+    """The one-two-sum sum of two terms of one sign (norms, path lengths) within 2^-44 of the
+    exact sum; the two-term dot product a b + c d (the mixed walk's crossing test) within 2^-44
+    of |a b| + |c d| in absolute terms, including operands whose products cancel."""
+    rng = np.random.default_rng(6)
+    xs, ys = np.abs(operands(rng, 3000)), np.abs(operands(rng, 3000))
+    sg = rng.choice([-1.0, 1.0], 3000)
+    worst_s = 0.0
+    for x, y, g in zip(xs, ys, sg):
+        a, b = split(g * x), split(g * y)
+        A, B = val(a), val(b)
+        worst_s = max(worst_s, rel(val(df_add_same_sign(a, b)), A + B))
+    assert worst_s < 2.0 ** -44, worst_s
+    worst_d = 0.0
+    for k in range(3000):
+        a, b, c = (split(t) for t in operands(rng, 3))
+        if k % 2:
+            # c d close to -a b: the high parts cancel
+            d = split(-val(a) * val(b) / val(c) * (1.0 + rng.uniform(-1e-6, 1e-6)))
+        else:
+            d = split(operands(rng, 1)[0])
+        A, B, C, D = val(a), val(b), val(c), val(d)
+        err = abs(val(df_dot2(a, b, c, d)) - (A * B + C * D))
+        worst_d = max(worst_d, err / (abs(A * B) + abs(C * D)))
+    assert worst_d < 2.0 ** -44, worst_d
