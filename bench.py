@@ -45,7 +45,9 @@ def ncu_traffic(kernel: str, key: str = "dram_bytes_per_launch"):
     rec = json.load(open(path)).get(kernel)
     if not rec:
         return None
-    files = {"k_bwd_rewalk": ["walk.cuh", "backward.cu"], "k_walk_persistent": ["walk.cuh", "exp_map.cu"]}[kernel]
+    files = {"k_bwd_rewalk": ["walk.cuh", "backward.cu"], "k_walk_persistent": ["walk.cuh", "exp_map.cu"]}.get(kernel)
+    if files is None:
+        return None
     csrc = os.path.join(ROOT, "paper_2603_15780_gb300", "csrc")
     sha = hashlib.sha1(b"".join(open(os.path.join(csrc, f), "rb").read() for f in files)).hexdigest()
     return rec.get(key) if sha == rec["source_sha1"] else None
@@ -581,12 +583,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time the step as eager launches, not a CUDA graph")
     ap.add_argument("--no-probe", action="store_true", help="skip the 32-B gather ceilings measured after the timed steps")
-    ap.add_argument("--kernel", type=int, default=2)
-    ap.add_argument("--sort", type=int, default=-1, help="1 on, 0 off, -1 the library's automatic choice")
-    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=None,
+                    help="1 plain, 2 persistent; giving --kernel, --sort or --block skips the autotuner")
+    ap.add_argument("--sort", type=int, default=None, help="1 on, 0 off, -1 the library's automatic choice")
+    ap.add_argument("--block", type=int, default=None)
     ap.add_argument("--fp64", type=int, default=1)
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--no-autotune", action="store_true", help="multimesh: default persistent options")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="the library's default launch options instead of the autotuner's pick")
     ap.add_argument("--workload", default="fwdbwd",
                     choices=["fwdbwd", "multimesh", "icosphere-s3", "torus", "heightfield", "features"],
                     help="fwdbwd: the headline step; multimesh: 64 uneven meshes, plain per-mesh launches vs "
@@ -629,10 +633,28 @@ def main():
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32), device=dev)
     face = torch.tensor(q.face, device=dev)
     bary, v, g = f32(q.bary), f32(q.v), f32(q.g_pos)
+    # The forward's launch options: the autotuner's pick on this batch (kernel shape, block, queries
+    # per thread, query order; timed before and outside the timed region), unless options are given.
+    tuned = None
+    if args.kernel is None and args.sort is None and args.block is None and not args.no_autotune:
+        from paper_2603_15780_gb300 import autotune
+        best, table = autotune.tune(mesh, face, bary, v, reps=5, fp64_escalate=args.fp64)
+        args.kernel, args.sort, args.block = best.kernel, best.sort, best.block
+        tuned = {"pick": {k: getattr(best, k) for k in ("kernel", "block", "sort", "queries_per_thread")},
+                 "candidates": len(table), "pick_ms": min(t for _, t in table),
+                 "default_ms": next((t for c, t in table if c["kernel"] == 2 and c["block"] == 256 and c["sort"] == -1
+                                     and c["queries_per_thread"] == 0), None)}
+    # the backward's query order: the library's automatic choice unless --sort is given (the
+    # autotuner times the forward only)
+    bsort = -1 if (tuned is not None or args.sort is None) else args.sort
+    args.kernel = 2 if args.kernel is None else args.kernel
+    args.sort = -1 if args.sort is None else args.sort
+    args.block = 0 if args.block is None else args.block
+    qpt = tuned["pick"]["queries_per_thread"] if tuned else 0
     opts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
-                           block=args.block if args.block > 0 else None)
+                           block=args.block if args.block > 0 else None, queries_per_thread=qpt)
     ws = torch.empty(sg.workspace_size(mesh, nq, opts), dtype=torch.uint8, device=dev)
-    bopts = sg.default_opts(sort=args.sort)
+    bopts = sg.default_opts(sort=bsort)
     bws = torch.empty(sg.backward_workspace_size(mesh, "gfd", nq, True), dtype=torch.uint8, device=dev)
     # per-kernel events recorded by the library around its walk kernels (forward walk, GFD re-walk)
     kev = {k: [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for k in ("walk", "rewalk")}
@@ -642,9 +664,9 @@ def main():
     import ctypes
     kh = {k: (ctypes.c_void_p * 2)(pair[0].cuda_event, pair[1].cuda_event) for k, pair in kev.items()}
     popts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
-                            block=args.block if args.block > 0 else None)
+                            block=args.block if args.block > 0 else None, queries_per_thread=qpt)
     popts.prof_events = ctypes.addressof(kh["walk"])
-    pbopts = sg.default_opts(sort=args.sort)
+    pbopts = sg.default_opts(sort=bsort)
     pbopts.prof_events = ctypes.addressof(kh["rewalk"])
     out = {"face": torch.empty(nq, dtype=torch.int32, device=dev), "bary": torch.empty(nq, 3, device=dev),
            "pos": torch.empty(nq, 3, device=dev), "dir": torch.empty(nq, 3, device=dev),
@@ -884,7 +906,7 @@ def main():
     else:
         l2 = torch.cuda.get_device_properties(dev).L2_cache_size
         sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
-    bwd_lorder = args.sort == 2 or (args.sort < 0 and nq >= 65536)
+    bwd_lorder = bsort == 2 or (bsort < 0 and nq >= 65536)
     # the automatic precision adds the mixed walk over its escalation list (one launch, which finds
     # the list empty on this workload: every walk here stays within the FP32 walk's range)
     launches_per_step = 9 + {0: 0, 1: 5, 2: 2}[sort_mode] + (2 if bwd_lorder else 0)
@@ -902,7 +924,7 @@ def main():
     walk_bytes = ncross * RECORD_BYTES + nq * (28 + 2 * 48 + 48)
     rewalk_bytes = ncross * RECORD_BYTES + nq * 400
     rewalk_atomic_bytes = ncross * 8
-    kern = {"k_walk_persistent": (walk_bytes, float(np.mean(ktimes["walk"]))),
+    kern = {("k_walk_persistent" if args.kernel == 2 else "k_walk_plain"): (walk_bytes, float(np.mean(ktimes["walk"]))),
             "k_bwd_rewalk": (rewalk_bytes, float(np.mean(ktimes["rewalk"])))}
     dom = max(kern, key=lambda k: kern[k][1])
     achieved = kern[dom][0] / (kern[dom][1] * 1e-3) / 1e9
@@ -949,6 +971,7 @@ def main():
             "config": {"workload": "icosphere-s6-noisy 81920F 1Mq fwd+EP+GFD+gradV", "global_batch": world * nq,
                        "faces": int(len(F)), "queries_per_gpu": nq, "l2": "flushed between steps (512 MB write)",
                        "kernel": "persistent" if args.kernel == 2 else "plain",
+                       "autotuned": tuned,
                        "query_order": {0: "input", 1: "start face", 2: "walk length"}[sort_mode],
                        "bwd_query_order": "walk length" if bwd_lorder else "input",
                        "fp64_classification": bool(args.fp64),

@@ -210,9 +210,12 @@ __global__ void __launch_bounds__(256, SG_MIX_MINB) k_walk_mixed(FwdArgs a) {
 }
 
 // hole avoidance (boundary_mode 1): the boundary handling needs more registers than the
-// default walk, so it gets its own kernel with a lower residency bound instead of spilling
+// default walk, so it gets its own kernel and residency bound
+#ifndef SG_HOLE_MINB
+#define SG_HOLE_MINB 4
+#endif
 template <int NW>
-__global__ void __launch_bounds__(256, 4) k_walk_hole(FwdArgs a) {
+__global__ void __launch_bounds__(256, SG_HOLE_MINB) k_walk_hole(FwdArgs a) {
     FwdJob<NW, true, true> job;
     job.a = &a;
     run_persistent<FwdJob<NW, true, true>, SG_WALK_REFILL>(a.counter, a.nq, job);
