@@ -37,10 +37,12 @@
 // gradient parallel-transported back (gbar_i = a d_i + s_i b perp(d_i)), so one forward
 // re-walk accumulates everything (no stored path).  2-D corner gradients map to 3-D by the
 // face frame F (in-plane); start and end faces add b_k F gbar0 and b'_k (g.n) n, plus a
-// tilt term when v has a normal component.  Each crossing adds two scalars to its interior
-// edge's accumulator (one 8-byte atomic; GradHook below), k_gradv_edges expands them into
-// vertex gradients once per edge, the start and end terms go into a float4 accumulator per
-// vertex, and k_gradv_flush adds it to the caller's grad_V.
+// tilt term when v has a normal component.  Each crossing yields two scalars for its interior
+// edge.  Two consecutive crossings of a walk share a face, so they are added together with one
+// 16-byte atomic into that face's accumulator window for the pair of edges (GradHook below);
+// k_gradv_edges sums each edge's windows in its two faces and expands them into vertex
+// gradients once per edge, the start and end terms go into a float4 accumulator per vertex,
+// and k_gradv_flush adds it to the caller's grad_V.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,6 +68,11 @@
 #ifndef SG_LITERAL_MINB
 #define SG_LITERAL_MINB 7
 #endif
+// minimum resident blocks per SM of the re-walk (71 registers at 7 without spills, with the
+// straddle test's rare constants, the query id and the face offset in shared memory)
+#ifndef SG_REWALK_MINB
+#define SG_REWALK_MINB 7
+#endif
 // the same for the literal GFD walks
 #ifndef SG_LITERAL_REFILL
 #define SG_LITERAL_REFILL 24
@@ -88,8 +95,8 @@ struct BwdArgs {
     uint32_t *out_status;
     float eps_v, eps_p;
     float4 *gacc;       // [nV] vertex-gradient accumulator (scratch)
-    float2 *eacc;       // [nE] per interior edge (start, end) coefficients, canonical orientation (scratch)
-    const int2 *edges;  // [nE] (canonical half-edge, twin)
+    float4 *wacc;       // [3 nF] per face f, window k = the (start, end) coefficients of its edges k
+                        // and k+1, each in f's orientation of the edge (corner k -> k+1) (scratch)
     float *cols;        // [nq][4] column contractions: par, perp, u, v; until the chords are
                         // evaluated the par slot holds the re-walk's swept-column mask (scratch)
     int32_t *tasks;     // [3 nq] (q << 2 | k) columns recomputed by literal walks (scratch)
@@ -214,21 +221,38 @@ __global__ void __launch_bounds__(256) k_ep_backward(BwdArgs A) {
 // literal walks of a split query can restart on the entry edge of the face where the first such
 // corner was met; the hook stores the base walker's state there (bit 3 of `split`).
 #define SG_SPLIT_RESTART 8u
+// The constants of the full test are read only after the |sig| <= sbound rejection, about once
+// per hundred corners, so they live in shared memory (one column per thread of the re-walk's
+// 128-thread blocks), not in registers:
+//   Ltot, tphi   e_perp wedge: the walk's length, tan of its opening angle eps_v / L
+//   ub, vb       e_u / e_v offsets across d0 (start frame)
+//   uq, vq       offsets along d0 over those across (0 when ub, vb = 0)
+//   tol          tau_near l_ref (1 + tphi^2), at least tau_near l_ref / cos(phi)
+#define SG_STR_LTOT 0
+#define SG_STR_TPHI 1
+#define SG_STR_TOL 2
+#define SG_STR_UB 3
+#define SG_STR_VB 4
+#define SG_STR_UQ 5
+#define SG_STR_VQ 6
+__shared__ float s_straddle[7][128];
+// the re-walk's query and its mesh's face offset, read only when a swept corner is recorded and
+// at the end of the walk (shared memory, one slot per thread, instead of two registers)
+__shared__ int32_t s_rewalk_q[128], s_rewalk_foff[128];
 struct StraddleHook {
     const BwdArgs *A;
-    float Ltot, tphi;            // e_perp wedge: tan of its opening angle, eps_v / L
-    float ub, vb;                // e_u / e_v offsets across d0 (start frame)
-    float uq, vq;                // offsets along d0 over those across (0 when ub, vb = 0)
-    float tol;                   // tau_near l_ref (1 + tphi^2), at least tau_near l_ref / cos(phi)
     float sbound;                // every region below lies within |sig| <= sbound
     unsigned split;
     // RECORD: the walker sits on a half-edge (the apex test of the hot step), where a first
     // swept corner stores the restart state
     template <bool RECORD>
-    __device__ __forceinline__ void test_at(const Walker &w, int32_t q, float sig_loc, float cx, float cy, float px,
-                                            float py) {
+    __device__ __forceinline__ void test_at(const Walker &w, float sig_loc, float cx, float cy, float px, float py) {
         // nearly every vertex passed lies far from the eps-wide regions: reject on |sig| first
         if (fabsf(sig_loc) > sbound) return;
+        const int th = threadIdx.x;
+        const float Ltot = s_straddle[SG_STR_LTOT][th], tphi = s_straddle[SG_STR_TPHI][th];
+        const float tol = s_straddle[SG_STR_TOL][th], ub = s_straddle[SG_STR_UB][th], vb = s_straddle[SG_STR_VB][th];
+        const float uq = s_straddle[SG_STR_UQ][th], vq = s_straddle[SG_STR_VQ][th];
         float tau = (Ltot - (w.Lh + w.Ll)) + (cx - px) * w.dx + (cy - py) * w.dy;
         float sig = (w.st & SG_PARITY_BIT) ? -sig_loc : sig_loc;
         if (tau < -tol || tau > Ltot + tol) return;
@@ -245,26 +269,26 @@ struct StraddleHook {
         if (RECORD && nb && !split) {
             // first swept corner, met on a half-edge: the state on its entry edge
             const int hp = w.h | ((w.st & SG_PARITY_BIT) ? (1 << 30) : 0);
-            int4 *r = A->rst + 2 * (int64_t)q;
+            int4 *r = A->rst + 2 * (int64_t)s_rewalk_q[threadIdx.x];
             r[0] = make_int4(hp, __float_as_int(w.px), __float_as_int(w.dx), __float_as_int(w.dy));
             *reinterpret_cast<float2 *>(r + 1) = make_float2(w.Lh, w.Ll);
             nb |= SG_SPLIT_RESTART;
         }
         split |= nb;
     }
-    __device__ __forceinline__ void test(const Walker &w, int32_t q, float sig_loc, int k) {
-        test_at<false>(w, q, sig_loc, corner_x(w.R, k), corner_y(w.R, k), w.px, w.py);
+    __device__ __forceinline__ void test(const Walker &w, float sig_loc, int k) {
+        test_at<false>(w, sig_loc, corner_x(w.R, k), corner_y(w.R, k), w.px, w.py);
     }
-    __device__ __forceinline__ void on_face(const Walker &w, int32_t q, float s0, float s1, float s2, int mode) {
+    __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode) {
         if (mode < 3) {
             int a = prv(mode);
-            test(w, q, sel3(a, s0, s1, s2), a);
+            test(w, sel3(a, s0, s1, s2), a);
         } else if (mode < 6) {
             int c = mode - 3;
-            test(w, q, sel3(nxt(c), s0, s1, s2), nxt(c));
-            test(w, q, sel3(prv(c), s0, s1, s2), prv(c));
+            test(w, sel3(nxt(c), s0, s1, s2), nxt(c));
+            test(w, sel3(prv(c), s0, s1, s2), prv(c));
         } else {
-            test(w, q, s0, 0); test(w, q, s1, 1); test(w, q, s2, 2);
+            test(w, s0, 0); test(w, s1, 1); test(w, s2, 2);
         }
     }
 };
@@ -278,28 +302,51 @@ struct StraddleHook {
 //   g_B = (K / l) (N_old + N_new),   g_A = -(g_n + K / l) (N_old + N_new),
 // N_old / N_new = the in-plane unit normals of the edge pointing out of the old / new face.
 // N_old + N_new is a constant of the edge, so the walk only adds the two scalar
-// coefficients to the edge's accumulator (one atomic per crossing, in the edge's canonical
-// orientation, read from the twin half-edge record that the crossing loads anyway);
-// k_gradv_edges turns them into vertex gradients once.  For coplanar faces N_old + N_new = 0.
+// coefficients (kA, kB) to an accumulator of the edge; k_gradv_edges turns them into vertex
+// gradients once.  For coplanar faces N_old + N_new = 0.
+//
+// Accumulation: a crossing leaves face f through its edge j (A = corner j, B = corner j+1)
+// and enters g through g's edge kp.  The next crossing leaves g, so the two meet in g: the
+// first is held in registers (in g's orientation of edge kp) and the pair goes to g's window
+// for edges {kp, j'} as one 16-byte atomic.  Window k of a face holds edges k and k+1, so the
+// three windows cover the three pairs.  A crossing with no successor in its face (the walk
+// ends, or the next step is a vertex transport) is added alone to the first half of its
+// edge's window.  This halves the atomics, which share the L2 with the record reads.
 struct GradHook {
     float a, bs;        // gbar_i = a d_i + bs * s_i * perp(d_i)
-    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &G, float2 *eacc) {
-        const float exr = c.x1 - c.x0, eyr = c.y1 - c.y0;                // |e| e
-        const float il = c.il;
-        const float yx = fmaf(c.Lr, w.dx, c.qx) - c.x0, yy = fmaf(c.Lr, w.dy, c.qy) - c.y0;  // y - A
+    // The held crossing: its coefficients in g's orientation of edge kp (corner kp -> kp+1).
+    // Its half-edge 3g + kp is the walker's w.h from that crossing until the walk's next
+    // crossing, vertex transport or end (none of which happens without a flush or a pairing).
+    bool held;
+    float pa, pb;
+    __device__ __forceinline__ void flush(float4 *wacc, int h) {
+        if (held) atomicAdd(reinterpret_cast<float2 *>(wacc + h), make_float2(pa, pb));
+        held = false;
+    }
+    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, float4 *wacc) {
+        // With e = B - A, q - A = s e and y - A = s e + L_rem d, and g = a d + sb perp(d):
+        // g x e = a (d x e) - sb (d . e) = m, g x (y - A) = s m - sb L_rem, so
+        // K = -il (g x (y - A)) = il (sb L_rem - s m) and g_n = il m
         const float sb = (w.st & SG_PARITY_BIT) ? -bs : bs;             // old-frame parity
-        const float gx = a * w.dx - sb * w.dy, gy = a * w.dy + sb * w.dx;
-        // with n = (ey, -ex): (g.e)((y-A).n) - (g.n)((y-A).e) = -(g x (y-A)) for any unit e, so
-        // K = il (gy yx - gx yy); g_n = il (g x |e| e) needs no normalised e
-        const float kB = il * fmaf(gy, yx, -gx * yy);
-        const float gn = il * fmaf(gx, eyr, -gy * exr);
-        const float kA = -(gn + kB);
-        // the twin half-edge runs B -> A (A -> B when flipped); its record holds the edge id and
-        // whether it is the edge's canonical half-edge
-        const int ed = __float_as_int(G.il2);
-        // canonical orientation is A -> B unless the twin (running B -> A) is the canonical one
-        const bool same = ((ed & 1) != 0) || (c.fl != 0);
-        atomicAdd(eacc + (ed >> 1), same ? make_float2(kA, kB) : make_float2(kB, kA));
+        const float m = fmaf(a, c.dc, -sb * c.da);
+        const float sl = sb * c.Lr;
+        const float kB = c.il * fmaf(-c.s, m, sl);
+        const float kA = -c.il * (m + fmaf(-c.s, m, sl));               // -(g_n + K)
+        if (held && c.ke >= 0) {
+            // the held crossing entered this face through edge ke (a half-edge step, w.h = 3f +
+            // ke): window ke holds (ke, ke+1) when the walk leaves through j = ke+1, window j
+            // holds (j, ke) when it leaves through j = ke-1
+            if (c.j == nxt(c.ke)) atomicAdd(wacc + w.h, make_float4(pa, pb, kA, kB));
+            else atomicAdd(wacc + (w.h - c.ke + c.j), make_float4(kA, kB, pa, pb));
+            held = false;
+        } else {
+            flush(wacc, w.h);
+            // held in g's orientation of edge kp: corner kp of g is B, kp+1 is A, unless the
+            // adjacency is flipped (the two faces list the edge in the same direction)
+            held = true;
+            pa = c.fl ? kA : kB;
+            pb = c.fl ? kB : kA;
+        }
     }
 };
 
@@ -309,17 +356,18 @@ struct RewalkHook {
     StraddleHook S;
     GradHook G;
     bool gradv;
-    int32_t q;          // the query (nq < 2^29, checked at the entry point): one register
     __device__ __forceinline__ void on_face(const Walker &w, float s0, float s1, float s2, int mode, int) {
-        if (GFD) S.on_face(w, q, s0, s1, s2, mode);
+        if (GFD) S.on_face(w, s0, s1, s2, mode);
     }
     __device__ __forceinline__ void on_apex(const Walker &w, float sC, float cx, float cy, float px, float py) {
-        if (GFD) S.template test_at<true>(w, q, sC, cx, cy, px, py);
+        if (GFD) S.template test_at<true>(w, sC, cx, cy, px, py);
     }
-    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &R) {
-        if (GRADV && gradv) G.on_cross(w, c, R, A->eacc);
+    __device__ __forceinline__ void on_cross(const Walker &w, const Cross &c, const FaceRec &) {
+        if (GRADV && gradv) G.on_cross(w, c, A->wacc);
     }
-    __device__ __forceinline__ void on_vertex(const Walker &, int) {}
+    __device__ __forceinline__ void on_vertex(const Walker &w, int) {
+        if (GRADV && gradv) G.flush(A->wacc, w.h);
+    }
 };
 
 // ------------------------------------------------------------------ kernel 1: re-walk
@@ -331,33 +379,42 @@ struct RewalkJob {
     bool valid;
 
     __device__ __forceinline__ bool init(int64_t t) {
-        const int32_t q = H.q = A->perm ? __ldg(A->perm + t) : (int32_t)t;
+        // the query (nq < 2^29, checked at the entry point)
+        const int32_t q = A->perm ? __ldg(A->perm + t) : (int32_t)t;
+        s_rewalk_q[threadIdx.x] = q;
         H.A = A;
         const WalkParams &P = A->P;
         Carry<0> cw;
         bool live = walker_init<0>(P, A->in, q, w, cw);
         valid = live && !(w.st & SG_ST_INVALID);
         if (!valid) return false;
+        s_rewalk_foff[threadIdx.x] = w.foff;
         uint32_t fst = A->end_status ? __ldg(A->end_status + q) : 0u;
         H.gradv = GRADV && !(fst & (SG_ST_VERTEX_HIT | SG_ST_BOUNDARY | SG_ST_MAX_STEPS | SG_ST_INVALID | SG_ST_HOLE));
         if (GRADV && !H.gradv) w.st |= SG_ST_NO_GRADV;  // the walker never touches this bit
+        if (GRADV) H.G.held = false;
         const float L = w.Lh, d0x = w.dx, d0y = w.dy;
         if (GFD) {
             H.S.A = A;
-            H.S.tphi = A->eps_v / L;
-            H.S.Ltot = L;
-            H.S.tol = P.tau_near * w.lref * (1.f + H.S.tphi * H.S.tphi);
+            const float tphi = A->eps_v / L;
+            const float tol = P.tau_near * w.lref * (1.f + tphi * tphi);
             // a walk that slid along the boundary (hole avoidance) takes literal walks
             H.S.split = (fst & SG_ST_HOLE) ? 7u : 0u;
             float evx = w.R.x2x * w.R.il2, evy = w.R.x2y * w.R.il2;  // e_u = (1,0), e_v = P2/|P2|
             const float ua = A->eps_p * d0x, va = A->eps_p * (evx * d0x + evy * d0y);
-            H.S.ub = -A->eps_p * d0y;
-            H.S.vb = A->eps_p * (-evx * d0y + evy * d0x);
-            H.S.uq = H.S.ub != 0.f ? ua / H.S.ub : 0.f;
-            H.S.vq = H.S.vb != 0.f ? va / H.S.vb : 0.f;
+            const float ub = -A->eps_p * d0y;
+            const float vb = A->eps_p * (-evx * d0y + evy * d0x);
+            const int th = threadIdx.x;
+            s_straddle[SG_STR_LTOT][th] = L;
+            s_straddle[SG_STR_TPHI][th] = tphi;
+            s_straddle[SG_STR_TOL][th] = tol;
+            s_straddle[SG_STR_UB][th] = ub;
+            s_straddle[SG_STR_VB][th] = vb;
+            s_straddle[SG_STR_UQ][th] = ub != 0.f ? ua / ub : 0.f;
+            s_straddle[SG_STR_VQ][th] = vb != 0.f ? va / vb : 0.f;
             // the wedge needs sig < tau tphi + tol with tau <= Ltot + tol; the parallelograms
             // |sig| < |ub| + tol, |vb| + tol (with a margin for the bound's own rounding)
-            H.S.sbound = 1.0001f * (fmaxf(fmaxf(fabsf(H.S.ub), fabsf(H.S.vb)), (L + H.S.tol) * H.S.tphi) + H.S.tol);
+            H.S.sbound = 1.0001f * (fmaxf(fmaxf(fabsf(ub), fabsf(vb)), (L + tol) * tphi) + tol);
         }
         if (GRADV && H.gradv) {
             EndAdj E = end_adjoint(*A, q, w.foff);
@@ -384,13 +441,14 @@ struct RewalkJob {
     }
     __device__ __forceinline__ bool step() { return walker_step<true>(w, A->P, H); }
     __device__ __forceinline__ void finish() {
-        const int32_t q = H.q;
+        const int32_t q = s_rewalk_q[threadIdx.x];
         if (!valid) {
             if (A->out_status) A->out_status[q] = (w.st & ~SG_PARITY_BIT) | (GRADV ? SG_ST_NO_GRADV : 0u);
             return;
         }
         uint32_t st = w.st & ~SG_PARITY_BIT;
         if (GRADV && H.gradv) {
+            H.G.flush(A->wacc, w.h);
             // end face: grad x_j += b'_j (g . n) n
             const FaceRec &R = w.R;
             const int4 fve = __ldg(A->P.fv + w.f);
@@ -404,7 +462,7 @@ struct RewalkJob {
         // A forward walk beyond the FP32 walk's range ran in the mixed walk; this FP32 re-walk
         // may then pass a vertex on the other side: reported when it ends in another face.
         const bool mixed = A->end_status && (__ldg(A->end_status + q) & SG_ST_MIXED);
-        const bool diverged = mixed && w.f - w.foff != __ldg(A->end_face + q);
+        const bool diverged = mixed && w.f - s_rewalk_foff[threadIdx.x] != __ldg(A->end_face + q);
         if (diverged) st |= SG_ST_REWALK_DIVERGED;
         if (GFD) {
             // A walk that stopped at the boundary or at MAX_STEPS, or slid along the boundary
@@ -429,7 +487,7 @@ struct RewalkJob {
 };
 
 template <bool GFD, bool GRADV>
-__global__ void __launch_bounds__(128, 7) k_bwd_rewalk(BwdArgs A) {
+__global__ void __launch_bounds__(128, SG_REWALK_MINB) k_bwd_rewalk(BwdArgs A) {
     RewalkJob<GFD, GRADV> job;
     job.A = &A;
     run_persistent<RewalkJob<GFD, GRADV>, SG_REWALK_REFILL>(A.ntask + 1, A.nq, job);
@@ -879,17 +937,29 @@ __global__ void __launch_bounds__(256) k_bwd_transport(BwdArgs A) {
         for (int k = 0; k < A.n_w; ++k) st3(A.grad_w, (int64_t)A.n_w * q + k, gw[k]);
 }
 
-// per interior edge: its coefficients times N_a + N_b (the outward in-plane normals of the edge
+// the coefficients of edge k of face f in f's orientation: windows k (first half) and k-1
+// (second half)
+__device__ __forceinline__ float2 window_sum(const float4 *__restrict__ wacc, int f, int k) {
+    const float4 a = wacc[3 * f + k], b = wacc[3 * f + prv(k)];
+    return make_float2(a.x + b.z, a.y + b.w);
+}
+
+// per interior edge: its coefficients (summed over the windows of its two faces, in the
+// canonical half-edge's orientation) times N_a + N_b (the outward in-plane normals of the edge
 // in its two faces, N = F_f (sa, -ca) of each half-edge), added to the canonical half-edge's
 // start and end vertices
-__global__ void k_gradv_edges(int64_t nE, WalkParams P, const int2 *__restrict__ edges, const float2 *__restrict__ eacc,
+__global__ void k_gradv_edges(int64_t nE, WalkParams P, const int2 *__restrict__ edges, const float4 *__restrict__ wacc,
                               float4 *gacc) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nE) return;
-    const float2 c = eacc[e];
-    if (c.x == 0.f && c.y == 0.f) return;
     const int2 hh = __ldg(edges + e);
-    const int fa = hh.x / 3, ka = hh.x - 3 * fa, fb = hh.y / 3;
+    const int fa = hh.x / 3, ka = hh.x - 3 * fa, fb = hh.y / 3, kb = hh.y - 3 * fb;
+    const float2 ca = window_sum(wacc, fa, ka), cb = window_sum(wacc, fb, kb);
+    // fb lists the edge in the opposite direction unless the adjacency is flipped
+    const int4 na = __ldg(P.rec + 2 * fa);
+    const bool flip = (sel3(ka, na.x, na.y, na.z) >> 2) & 1;
+    const float2 c = flip ? make_float2(ca.x + cb.x, ca.y + cb.y) : make_float2(ca.x + cb.y, ca.y + cb.x);
+    if (c.x == 0.f && c.y == 0.f) return;
     const FaceRec Ha = load_rec(P.half, hh.x), Hb = load_rec(P.half, hh.y);
     const F3 N = lift(load_frm(P, fa), hsa(Ha), -hca(Ha)) + lift(load_frm(P, fb), hsa(Hb), -hca(Hb));
     const int4 t = __ldg(P.fv + fa);
@@ -921,14 +991,14 @@ unsigned persistent_grid(K kernel, int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per, 1), need));
 }
 struct BwdLayout {
-    size_t gacc, eacc, cols, tasks, tasks40, rst, ntask, gpos, lcounts, lkeys, perm, total;
+    size_t gacc, wacc, cols, tasks, tasks40, rst, ntask, gpos, lcounts, lkeys, perm, total;
 };
 // The re-walk takes its queries longest first (the forward's length order, rebuilt here) for
 // batches of at least this many queries, unless opts.sort is 0.
 #define SG_BWD_LORDER_MIN 65536
 bool bwd_lorder(const sg_opts &r, int64_t nq) { return r.sort == 2 || (r.sort < 0 && nq >= SG_BWD_LORDER_MIN); }
 
-BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool grad_V, bool lorder) {
+BwdLayout bwd_layout(int64_t nV, int64_t nF, int64_t nq, int32_t estimator, bool grad_V, bool lorder) {
     BwdLayout L{};
     size_t o = 0;
     L.ntask = o; o = align_up(o + 64, 256);
@@ -940,7 +1010,7 @@ BwdLayout bwd_layout(int64_t nV, int64_t nE, int64_t nq, int32_t estimator, bool
     }
     if (grad_V) {
         L.gacc = o; o = align_up(o + sizeof(float4) * (size_t)nV, 256);
-        L.eacc = o; o = align_up(o + sizeof(float2) * (size_t)std::max<int64_t>(nE, 1), 256);
+        L.wacc = o; o = align_up(o + sizeof(float4) * 3 * (size_t)std::max<int64_t>(nF, 1), 256);
     }
     if (estimator == SG_EST_GFD) {
         L.cols = o; o = align_up(o + sizeof(float) * 4 * (size_t)std::max<int64_t>(nq, 1), 256);
@@ -958,7 +1028,7 @@ extern "C" sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_
     if (!m || !bytes || nq < 0) return SG_ERR_INVALID_ARG;
     if (estimator != SG_EST_EP && estimator != SG_EST_GFD) return SG_ERR_INVALID_ARG;
     // room for the length order whatever the options (the layout without it is smaller)
-    *bytes = bwd_layout(m->nV, m->nE, nq, estimator, want_grad_V != 0, true).total;
+    *bytes = bwd_layout(m->nV, m->nF, nq, estimator, want_grad_V != 0, true).total;
     return SG_OK;
 }
 
@@ -1000,7 +1070,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.eps_v = eps_v; A.eps_p = eps_p;
 
     const bool lorder = (estimator == SG_EST_GFD || grad_V) && bwd_lorder(r, nq);  // only the re-walk uses it
-    BwdLayout Lw = bwd_layout(m->nV, m->nE, nq, estimator, grad_V != nullptr, lorder);
+    BwdLayout Lw = bwd_layout(m->nV, m->nF, nq, estimator, grad_V != nullptr, lorder);
     void *ws = nullptr;
     bool own = false;
     if (r.workspace) {
@@ -1014,7 +1084,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.ntask = (int32_t *)(base + Lw.ntask);
     if (grad_V) {
         A.gacc = (float4 *)(base + Lw.gacc);
-        A.eacc = (float2 *)(base + Lw.eacc);
+        A.wacc = (float4 *)(base + Lw.wacc);
     }
     if (estimator == SG_EST_GFD) {
         A.cols = (float *)(base + Lw.cols);
@@ -1047,7 +1117,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     }
     if (grad_V) {
         cudaMemsetAsync(A.gacc, 0, sizeof(float4) * (size_t)m->nV, s);
-        cudaMemsetAsync(A.eacc, 0, sizeof(float2) * (size_t)std::max<int64_t>(m->nE, 1), s);
+        cudaMemsetAsync(A.wacc, 0, sizeof(float4) * 3 * (size_t)std::max<int64_t>(m->nF, 1), s);
     }
     const unsigned g128 = (unsigned)((nq + 127) / 128), g256 = (unsigned)((nq + 255) / 256);
     if (estimator == SG_EST_EP) {
@@ -1078,7 +1148,7 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     if (grad_V) {
         if (g_bary) k_gradv_gbary<<<g256, 256, 0, s>>>(A);
         if (m->nE > 0)
-            k_gradv_edges<<<(unsigned)((m->nE + 255) / 256), 256, 0, s>>>(m->nE, A.P, m->d_edges, A.eacc, A.gacc);
+            k_gradv_edges<<<(unsigned)((m->nE + 255) / 256), 256, 0, s>>>(m->nE, A.P, m->d_edges, A.wacc, A.gacc);
         k_gradv_flush<<<(unsigned)((m->nV + 255) / 256), 256, 0, s>>>(m->nV, A.gacc, grad_V);
     }
     if (own) cudaFreeAsync(ws, s);

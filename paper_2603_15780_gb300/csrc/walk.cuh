@@ -553,6 +553,9 @@ struct Cross {
     float gax, gay, fx, fy, ndx, ndy;
     float ca0, sa0, ca1, sa1;  // rotations old frame -> old face frame, new frame -> new face frame
     float il;                  // 1 / |x1 - x0| (the crossed edge's inverse length)
+    int ke;                    // the old face's entry edge (half-edge step), -1 from a face-frame step
+    float s;                   // q = A + s (B - A)
+    float da, dc;              // d . (B - A) and d x (B - A) (old frame, old direction)
 };
 
 // Observer of a walk (the backward pass hooks into the same step code as the forward).
@@ -679,7 +682,7 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         return true;
     }
     const int hn = link >> 1, fl = link & 1;
-    float ndx, ndy, re;
+    float ndx, ndy, re, eda = 0.f, edc = 0.f;
     if (MIX) {
         // the exit edge in double-float: B -> C = (cx - l, cy), C -> A = -(cx, cy)
         const DF Ld{L0, __int_as_float(R.n1)}, cxd{cx, R.l01}, cyd{cy, R.x2y};
@@ -700,13 +703,14 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
         // does not accumulate: every step renormalises the direction it receives)
         re = rsqrtf(fmaf(da, da, dc * dc));
         ndx = (fl ? da : -da) * re; ndy = dc * re;
+        eda = da; edc = dc;
     }
     const FaceRec G = load_rec<true>(MIX ? P.half48 : P.half, hn);
     if (!MIX) {
         const int k = w.h - 3 * (w.h / 3);
         const int g = hn / 3;
         hook.on_cross(w, Cross{right ? nxt(k) : prv(k), x0, y0, x1, y1, qx, qy, w.Lh + w.Ll, g, hn - 3 * g, fl,
-                               0.f, 0.f, hl(G), 0.f, ndx, ndy, hca(R), hsa(R), hca(G), hsa(G), re},
+                               0.f, 0.f, hl(G), 0.f, ndx, ndy, hca(R), hsa(R), hca(G), hsa(G), re, k, s, eda, edc},
                       G);
     }
     w.px = fl ? s : 1.f - s;
@@ -853,7 +857,7 @@ __device__ __forceinline__ bool general_step(Walker &w, const WalkParams &P, Hoo
         w.dxl = 0.f; w.dyl = 0.f;
     } else {
         hook.on_cross(w, Cross{j, ax, ay, bx, by, qx, qy, w.Lh + w.Ll, g, kp, fl, 0.f, 0.f, hl(G), 0.f, ndx, ndy,
-                               1.f, 0.f, hca(G), hsa(G), rsqrtf(fmaf(bx - ax, bx - ax, (by - ay) * (by - ay)))},
+                               1.f, 0.f, hca(G), hsa(G), rsqrtf(fmaf(bx - ax, bx - ax, (by - ay) * (by - ay))), -1, s, da, dc},
                       G);
     }
     w.px = fl ? s : 1.f - s;
