@@ -93,7 +93,10 @@ typedef struct sg_opts {
     int32_t blocks_per_sm;  /* persistent kernel residency; <= 0: as many as fit */
     int32_t fp64_escalate;  /* 1: re-evaluate near-vertex classification in FP64 (persistent only) */
     float tau_near;         /* flag radius / l_ref for NEAR_VERTEX, NEAR_EDGE and the FP64 band; <= 0: 1e-4 */
-    float tau_snap;         /* vertex-snap radius / l_ref; <= 0: 1e-6 (precision 32), 1e-12 (48, 64) */
+    float tau_snap;         /* vertex-snap radius / l_ref; <= 0: 1e-6 (precision 0, 32, 40), 1e-12
+                               (48, 64), or tau_near if that is smaller; a value above tau_near is
+                               rejected (SG_ERR_INVALID_ARG): a snapped vertex lies inside the
+                               near band */
     void *workspace;        /* optional device scratch (see sg_exp_map_workspace_size); NULL: the
                                library allocates stream-ordered scratch itself */
     size_t workspace_bytes;

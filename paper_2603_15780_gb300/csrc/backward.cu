@@ -54,9 +54,9 @@
 
 #define SG_BWD_MAX_W 4
 // lanes of a warp that must be idle before the re-walk refills them together (swept under the
-// length order: 12 0.748, 16 0.756, 20 0.741, 24 0.723, 28 0.730, 32 0.745 ms)
+// length order with the paired grad_V reductions: 16 0.706, 20 0.686, 24 0.648, 28 0.631 ms)
 #ifndef SG_REWALK_REFILL
-#define SG_REWALK_REFILL 24
+#define SG_REWALK_REFILL 28
 #endif
 // minimum resident blocks per SM the assemble and literal kernels are compiled for (the assemble
 // pass holds no walk since its chord walks moved to a second pass)
@@ -1054,7 +1054,8 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     if (r.precision >= 40) return SG_ERR_UNSUPPORTED;
     if (r.max_steps <= 0) r.max_steps = 1 << 20;
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
-    if (r.tau_snap <= 0.f) r.tau_snap = 1e-6f;
+    if (r.tau_snap <= 0.f) r.tau_snap = fminf(1e-6f, r.tau_near);
+    if (r.tau_snap > r.tau_near) return SG_ERR_INVALID_ARG;  // a snapped vertex lies in the near band
     cudaStream_t s = (cudaStream_t)stream;
     BwdArgs A{};
     A.P.rec = m->d_rec; A.P.fv = m->d_fv; A.P.frm = m->d_frm; A.P.half = m->d_half; A.P.V = m->d_V; A.P.face_off = m->d_face_off;

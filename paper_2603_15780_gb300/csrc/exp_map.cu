@@ -634,7 +634,7 @@ sg_opts resolve(const sg_opts *o, int64_t nq, int64_t nF) {
     if (r.block <= 0) r.block = 256;
     if (r.precision < 0) r.precision = 0;  // 0: automatic (FP32, long walks in the mixed walk)
     if (r.tau_near <= 0.f) r.tau_near = 1e-4f;
-    if (r.tau_snap <= 0.f) r.tau_snap = r.precision >= 48 ? 1e-12f : 1e-6f;
+    if (r.tau_snap <= 0.f) r.tau_snap = fminf(r.precision >= 48 ? 1e-12f : 1e-6f, r.tau_near);
     if (r.kernel == SG_KERNEL_AUTO) r.kernel = SG_KERNEL_PERSISTENT;
     if (r.sort < 0)
         r.sort = nq < SG_SORT_MIN_BATCH ? 0 : (128 * nF > (int64_t)l2_bytes() / 2 ? 1 : 2);
@@ -997,6 +997,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
     if (n_w > 0 && !w) return SG_ERR_INVALID_ARG;
     const bool auto_kernel = !o || o->kernel == SG_KERNEL_AUTO;
     sg_opts r = resolve(o, nq, m->nF);
+    if (r.tau_snap > r.tau_near) return SG_ERR_INVALID_ARG;  // a snapped vertex lies in the near band
     if (r.kernel != SG_KERNEL_PLAIN && r.kernel != SG_KERNEL_PERSISTENT) return SG_ERR_INVALID_ARG;
     if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;
@@ -1102,6 +1103,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
         return SG_ERR_INVALID_ARG;
     if (path_cap > 0 && !out_path_face) return SG_ERR_INVALID_ARG;
     sg_opts r = resolve(o, nq, m->nF);
+    if (r.tau_snap > r.tau_near) return SG_ERR_INVALID_ARG;
     if (r.boundary_mode || r.precision >= 40) return SG_ERR_UNSUPPORTED;
     if (r.sort > 2) return SG_ERR_INVALID_ARG;
     if (r.block % 32 != 0 || r.block > 256) return SG_ERR_INVALID_ARG;

@@ -307,7 +307,8 @@ sg_status sg_exp_map_steps(const sg_mesh *m, int32_t K, float h, const float *U,
     if (o) r = *o;
     if (r.precision != 0 && r.precision != 32) return SG_ERR_UNSUPPORTED;  // the FP32 walk
     if (r.boundary_mode) return SG_ERR_UNSUPPORTED;
-    const float tau_near = r.tau_near > 0.f ? r.tau_near : 1e-4f, tau_snap = r.tau_snap > 0.f ? r.tau_snap : 1e-6f;
+    const float tau_near = r.tau_near > 0.f ? r.tau_near : 1e-4f, tau_snap = r.tau_snap > 0.f ? r.tau_snap : fminf(1e-6f, tau_near);
+    if (tau_snap > tau_near) return SG_ERR_INVALID_ARG;  // a snapped vertex lies in the near band
     cudaStream_t s = (cudaStream_t)stream;
     StepsArgs a{};
     a.P.rec = m->d_rec; a.P.fv = m->d_fv; a.P.frm = m->d_frm; a.P.half = m->d_half; a.P.V = m->d_V;

@@ -613,21 +613,24 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     float sA = w.dy * x;
     float sB = -w.dy * (L0 - x);
     float sC = fmaf(w.dx, cy, -w.dy * (cx - x));
-    if (ESC && fabsf(sC) < near) {
-        // FP64 re-evaluation of the classification (exact products of the walker's state)
-        w.st |= SG_ST_FP64;
-        const double Ld = MIX ? (double)L0 + (double)__int_as_float(R.n1) : (double)L0;
-        const double cxd = MIX ? (double)cx + (double)R.l01 : (double)cx;
-        const double cyd = MIX ? (double)cy + (double)R.x2y : (double)cy;
-        const double dxd = MIX ? (double)w.dx + (double)w.dxl : (double)w.dx;
-        const double dyd = MIX ? (double)w.dy + (double)w.dyl : (double)w.dy;
-        const double X = (double)w.px * Ld;
-        sA = f32_keep_sign(dyd * X);
-        sB = f32_keep_sign(-dyd * (Ld - X));
-        sC = f32_keep_sign(dxd * cyd - dyd * (cxd - X));
+    bool hit = false;
+    if (fabsf(sC) < near) {  // rare: the apex lies in the near band (the entry points require snap <= near)
+        if (ESC) {
+            // FP64 re-evaluation of the classification (exact products of the walker's state)
+            w.st |= SG_ST_FP64;
+            const double Ld = MIX ? (double)L0 + (double)__int_as_float(R.n1) : (double)L0;
+            const double cxd = MIX ? (double)cx + (double)R.l01 : (double)cx;
+            const double cyd = MIX ? (double)cy + (double)R.x2y : (double)cy;
+            const double dxd = MIX ? (double)w.dx + (double)w.dxl : (double)w.dx;
+            const double dyd = MIX ? (double)w.dy + (double)w.dyl : (double)w.dy;
+            const double X = (double)w.px * Ld;
+            sA = f32_keep_sign(dyd * X);
+            sB = f32_keep_sign(-dyd * (Ld - X));
+            sC = f32_keep_sign(dxd * cyd - dyd * (cxd - X));
+        }
+        hit = fabsf(sC) <= snap;  // a snapped apex is a hit, not a near miss
+        if (!hit && fabsf(sC) < near) w.st |= SG_ST_NEAR_VERTEX;
     }
-    const bool hit = fabsf(sC) <= snap;  // a snapped apex is a hit, not a near miss
-    if (!hit && fabsf(sC) < near) w.st |= SG_ST_NEAR_VERTEX;
     hook.on_apex(w, sC, cx, cy, x, 0.f);
     const bool right = sC > 0.f;
     const float x0 = right ? L0 : cx, y0 = right ? 0.f : cy;
@@ -639,8 +642,7 @@ __device__ __forceinline__ bool half_step(Walker &w, const WalkParams &P, Hook &
     } else {
         const float s0 = right ? sB : sC, s1 = right ? sC : sA;
         const float den = s0 - s1;
-        s = den != 0.f ? __fdividef(s0, den) : 0.5f;
-        s = fminf(fmaxf(s, 0.f), 1.f);
+        s = __saturatef(den != 0.f ? __fdividef(s0, den) : 0.5f);  // clamped to [0, 1], NaN to 0
         qx = fmaf(s, x1 - x0, x0);
         qy = fmaf(s, y1 - y0, y0);
     }

@@ -103,3 +103,17 @@ def test_bad_meshes_are_rejected_at_creation():
     Fn = np.concatenate([F, F[:1, [0, 2, 1]], F[:1]])   # an edge with three faces
     with pytest.raises(sg().SgError):
         sg().Mesh(X32, Fn)
+
+
+def test_snap_radius_beyond_the_near_band_is_rejected():
+    # the hot step tests the snap radius only inside the near band, so a snap radius larger than
+    # tau_near is an invalid option on every entry point that walks
+    X, F, q, _ = _bad_batch()
+    mesh = sg().Mesh(parity.as_f32(X), F)
+    f32 = parity.as_f32
+    with pytest.raises(sg().SgError, match="status 1"):
+        sg().exp_map(mesh, q.face, f32(q.bary), f32(q.v), tau_near=1e-4, tau_snap=1e-3)
+    out = sg().exp_map(mesh, q.face, f32(q.bary), f32(q.v), tau_near=1e-4, tau_snap=1e-4)  # equal: allowed
+    with pytest.raises(sg().SgError, match="status 1"):
+        sg().exp_map_backward(mesh, "gfd", q.face, f32(q.bary), f32(q.v), out["face"], out["bary"], out["dir"],
+                              out["status"], f32(q.g_pos), opts=sg().default_opts(tau_near=1e-5, tau_snap=1e-4))
