@@ -123,6 +123,15 @@ def gather_ceilings(ncross, ktimes):
         c32 = sg.probe_gather(sg.PROBE_CHAIN | W, tb, bps, thr, 256)
         out[k] = {"record_GBps": rec, "chain_GBps": {"2x16B": c16, "1x32B": c32},
                   "frac_of_chain": {"2x16B": rec / c16, "1x32B": rec / c32}}
+    # the re-walk's other L2 traffic: random reductions into the grad_V accumulator, 8 B (one
+    # crossing) or 16 B (a pair of crossings, the face windows: 48 B per face of the 81,920-face
+    # mesh), against the same 983,040-byte per-edge table held in a cluster's shared memory
+    wtab, etab = 48 * 81920, 8 * 122880
+    out["reduce_G_per_s"] = {"l2_8B": sg.probe_reduce(sg.PROBE_RED8, wtab, 400),
+                             "l2_16B": sg.probe_reduce(sg.PROBE_RED16, wtab, 400),
+                             "cluster5_dsmem_8B": sg.probe_reduce(sg.PROBE_RED_DSM, etab, 400, cluster=5),
+                             "cluster8_dsmem_8B": sg.probe_reduce(sg.PROBE_RED_DSM, etab, 400, cluster=8),
+                             "tables": {"l2_bytes": wtab, "dsmem_bytes": etab}}
     return out
 
 

@@ -1,10 +1,12 @@
-"""Measurement-only helpers of the benchmark: the 32-byte record gather probe.
+"""Measurement-only helpers of the benchmark: the 32-byte record gather probe and the reduction
+probe.
 
 ``probe.cu`` is built into its own library, ``measure/_build/libsgeo_probe.so`` (nvcc, sm_103a,
 in-tree), separate from the exponential-map library: it measures the memory ceilings a record
 walk can reach on the device (L2 streaming reads, independent and dependent 32-byte gathers) so
-that the benchmark can state the walk kernels' rates against them.  No part of the exponential
-map calls it.
+that the benchmark can state the walk kernels' rates against them, and the rate of random
+floating-point reductions into a gradient accumulator (in L2, or in a thread-block cluster's
+distributed shared memory).  No part of the exponential map calls it.
 """
 from __future__ import annotations
 
@@ -19,6 +21,7 @@ LIB = os.path.join(OUT_DIR, "libsgeo_probe.so")
 SRC = os.path.join(HERE, "probe.cu")
 
 PROBE_STREAM, PROBE_RANDOM, PROBE_CHAIN, PROBE_LD256 = 0, 1, 2, 4
+PROBE_RED8, PROBE_RED16, PROBE_RED_DSM = 0, 1, 2
 
 _lib = None
 
@@ -47,6 +50,9 @@ def lib():
         L.sg_probe_gather.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.sg_probe_gather.restype = C.c_int
+        L.sg_probe_reduce.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_int32,
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.sg_probe_reduce.restype = C.c_int
         _lib = L
     return _lib
 
@@ -64,3 +70,17 @@ def probe_gather(mode: int, table_bytes: int, blocks_per_sm: int, threads: int, 
     if rc != 0:
         raise RuntimeError(f"sg_probe_gather failed with status {rc}")
     return nb.value / sec.value / 1e9
+
+
+def probe_reduce(mode: int, table_bytes: int, iters: int, cluster: int = 0) -> float:
+    """Random reductions per second (in G/s) into an accumulator table of table_bytes: PROBE_RED8
+    (8-byte reductions into L2), PROBE_RED16 (16-byte reductions into L2) or PROBE_RED_DSM (the
+    table spread over the shared memory of clusters of `cluster` CTAs, one CTA of 896 threads per
+    SM, each reduction two 4-byte remote shared-memory reductions).  `iters` reductions per thread,
+    one untimed and one timed launch.  Synchronous on the legacy default stream; allocates and frees
+    its own device memory."""
+    sec, ops = C.c_double(), C.c_double()
+    rc = lib().sg_probe_reduce(mode, table_bytes, cluster, iters, C.byref(sec), C.byref(ops))
+    if rc != 0:
+        raise RuntimeError(f"sg_probe_reduce failed with status {rc}")
+    return ops.value / sec.value / 1e9

@@ -17,6 +17,16 @@
 // Records are 32 bytes, loaded through the read-only path either as the walk loads them (two
 // 16-byte loads) or, with SG_PROBE_LD256, as one 256-bit load (sm_100 and later), which the
 // L1 serves as one request instead of two.
+//
+// sg_probe_reduce measures the rate of random floating-point reductions into an accumulator table
+// of the size of a mesh's gradient accumulator, the other traffic of the backward re-walk:
+//
+//   SG_PROBE_RED8      8-byte reductions (two floats) into L2
+//   SG_PROBE_RED16     16-byte reductions (four floats) into L2
+//   SG_PROBE_RED_DSM   the table spread over the shared memory of a thread-block cluster (one CTA
+//                      of 896 threads per SM), each reduction two 4-byte red.shared::cluster on
+//                      the owning CTA, the table flushed to global memory at the end
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +39,9 @@
 #define SG_PROBE_RANDOM 1
 #define SG_PROBE_CHAIN 2
 #define SG_PROBE_LD256 4
+#define SG_PROBE_RED8 0
+#define SG_PROBE_RED16 1
+#define SG_PROBE_RED_DSM 2
 typedef int sg_probe_status;
 #define SG_OK 0
 #define SG_ERR_INVALID_ARG 1
@@ -98,6 +111,51 @@ __global__ void __launch_bounds__(1024) k_probe_chain(const int4 *__restrict__ t
         idx = (uint32_t)a.x;                  // in [0, nrec): written by the host below
     }
     if (acc == 0x9e3779b9u) sink[0] = acc ^ idx;
+}
+
+// an index in [0, n) from a linear congruential step (Numerical Recipes constants)
+__device__ __forceinline__ uint32_t next_index(uint32_t &x, uint32_t n) {
+    x = x * 1664525u + 1013904223u;
+    return (uint32_t)(((uint64_t)(x >> 8) * n) >> 24);
+}
+
+__global__ void __launch_bounds__(256) k_probe_red8(float2 *acc, uint32_t n, int32_t iters) {
+    uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+    for (int32_t i = 0; i < iters; ++i) atomicAdd(acc + next_index(x, n), make_float2(1.f, 2.f));
+}
+
+__global__ void __launch_bounds__(256) k_probe_red16(float4 *acc, uint32_t n, int32_t iters) {
+    uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+    for (int32_t i = 0; i < iters; ++i) atomicAdd(acc + next_index(x, n), make_float4(1.f, 2.f, 3.f, 4.f));
+}
+
+// entries [r slice, (r+1) slice) of the n-entry float2 table live in the shared memory of the
+// cluster's CTA r; magic = floor(2^32 / slice) gives r = e / slice with one correction
+__global__ void __launch_bounds__(896, 1) k_probe_red_dsm(float2 *acc, uint32_t n, uint32_t slice, uint32_t magic,
+                                                          int32_t iters) {
+    extern __shared__ float2 part[];
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    for (uint32_t i = threadIdx.x; i < slice; i += blockDim.x) part[i] = make_float2(0.f, 0.f);
+    cl.sync();  // every CTA of the cluster has zeroed its part before any remote reduction
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(part);
+    uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+    for (int32_t i = 0; i < iters; ++i) {
+        const uint32_t e = next_index(x, n);
+        uint32_t r = __umulhi(e, magic);
+        if (e - r * slice >= slice) ++r;  // r = e / slice < cluster size, since n <= cluster * slice
+        const uint32_t local = base + 8u * (e - r * slice);
+        asm volatile(
+            "{\n\t.reg .b32 ra;\n\tmapa.shared::cluster.u32 ra, %0, %1;\n\t"
+            "red.shared::cluster.add.f32 [ra], %2;\n\tred.shared::cluster.add.f32 [ra+4], %3;\n\t}" ::"r"(local),
+            "r"(r), "f"(1.f), "f"(2.f)
+            : "memory");
+    }
+    cl.sync();  // no CTA leaves while others may still reduce into its part
+    const uint32_t e0 = cl.block_rank() * slice;
+    for (uint32_t i = threadIdx.x; i < slice && e0 + i < n; i += blockDim.x) {
+        const float2 c = part[i];
+        if (c.x != 0.f || c.y != 0.f) atomicAdd(acc + e0 + i, c);
+    }
 }
 
 uint64_t splitmix64(uint64_t &s) {
@@ -184,5 +242,86 @@ extern "C" sg_probe_status sg_probe_gather(int32_t mode, int64_t table_bytes, in
     if (st == SG_OK && cudaGetLastError() != cudaSuccess) st = SG_ERR_CUDA;
     *out_seconds = st == SG_OK ? ms * 1e-3 : 0.0;
     *out_bytes = st == SG_OK ? moved : 0.0;
+    return st;
+}
+
+// Random reductions into an accumulator table of table_bytes: `iters` per thread, one untimed and
+// one timed launch.  SG_PROBE_RED8 / RED16: 8 blocks of 256 threads per SM.  SG_PROBE_RED_DSM: one
+// CTA of 896 threads per SM in clusters of `cluster` CTAs (2..16), as many clusters as fit at once;
+// SG_ERR_INVALID_ARG when the table's share per CTA exceeds the shared memory a block may use or
+// no cluster of that size fits.  out_ops = reductions performed (of 8 or 16 bytes).
+extern "C" sg_probe_status sg_probe_reduce(int32_t mode, int64_t table_bytes, int32_t cluster, int32_t iters,
+                                           double *out_seconds, double *out_ops) {
+    if (!out_seconds || !out_ops) return SG_ERR_INVALID_ARG;
+    if (mode < SG_PROBE_RED8 || mode > SG_PROBE_RED_DSM) return SG_ERR_INVALID_ARG;
+    if (table_bytes < 4096 || table_bytes > ((int64_t)1 << 28) || iters < 1 || iters > (1 << 16)) return SG_ERR_INVALID_ARG;
+    if (mode == SG_PROBE_RED_DSM && (cluster < 2 || cluster > 16)) return SG_ERR_INVALID_ARG;
+    int dev = 0, sms = 0, maxopt = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return SG_ERR_CUDA;
+    const uint32_t n = (uint32_t)(table_bytes / (mode == SG_PROBE_RED16 ? 16 : 8));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    uint32_t slice = 0, magic = 0;
+    int nclusters = 0;
+    if (mode == SG_PROBE_RED_DSM) {
+        slice = (n + (uint32_t)cluster - 1) / (uint32_t)cluster;
+        const size_t smem = (size_t)slice * sizeof(float2);
+        if (smem > (size_t)maxopt) return SG_ERR_INVALID_ARG;
+        if (cudaFuncSetAttribute(k_probe_red_dsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_probe_red_dsm, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            cudaGetLastError();
+            return SG_ERR_CUDA;
+        }
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.blockDim = dim3(896);
+        cfg.gridDim = dim3((unsigned)cluster);
+        cfg.dynamicSmemBytes = smem;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_probe_red_dsm, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return SG_ERR_CUDA;
+        }
+        if (nclusters < 1) return SG_ERR_INVALID_ARG;
+        cfg.gridDim = dim3((unsigned)(nclusters * cluster));
+        magic = (uint32_t)(0x100000000ull / slice);
+    }
+    void *acc = nullptr;
+    if (cudaMalloc(&acc, (size_t)table_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SG_ERR_OOM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sg_probe_status st = SG_OK;
+    float ms = 0.f;
+    double ops = 0.0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = SG_ERR_CUDA;
+    for (int rep = 0; rep < 2 && st == SG_OK; ++rep) {
+        if (cudaMemset(acc, 0, (size_t)table_bytes) != cudaSuccess) { st = SG_ERR_CUDA; break; }
+        if (rep == 1) cudaEventRecord(e0, 0);
+        if (mode == SG_PROBE_RED_DSM) {
+            if (cudaLaunchKernelEx(&cfg, k_probe_red_dsm, (float2 *)acc, n, slice, magic, iters) != cudaSuccess) st = SG_ERR_CUDA;
+            ops = (double)nclusters * cluster * 896.0 * iters;
+        } else {
+            const unsigned grid = (unsigned)sms * 8u;
+            if (mode == SG_PROBE_RED8) k_probe_red8<<<grid, 256>>>((float2 *)acc, n, iters);
+            else k_probe_red16<<<grid, 256>>>((float4 *)acc, n, iters);
+            ops = (double)grid * 256.0 * iters;
+        }
+        if (rep == 1) cudaEventRecord(e1, 0);
+    }
+    if (st == SG_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = SG_ERR_CUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(acc);
+    if (st == SG_OK && cudaGetLastError() != cudaSuccess) st = SG_ERR_CUDA;
+    *out_seconds = st == SG_OK ? ms * 1e-3 : 0.0;
+    *out_ops = st == SG_OK ? ops : 0.0;
     return st;
 }
