@@ -682,6 +682,9 @@ def main():
            "status": torch.empty(nq, dtype=torch.int32, device=dev),
            "ncross": torch.empty(nq, dtype=torch.int32, device=dev)}
     gV = torch.zeros(mesh.n_vertices, 3, device=dev)
+    # the forward writes the order it walked the queries in and the GFD backward's re-walk takes
+    # them in that order (sg_opts.order) instead of sorting them again
+    qorder = torch.empty(nq, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -695,7 +698,7 @@ def main():
         stream = torch.cuda.current_stream()  # the capture stream while the step is captured
         if ev is not None:
             ev[0].record(stream)
-        sg.exp_map(mesh, face, bary, v, out=out, workspace=ws, opts=popts if ev is not None else opts)
+        sg.exp_map(mesh, face, bary, v, out=out, workspace=ws, opts=popts if ev is not None else opts, order=qorder)
         if ev is not None:
             ev[1].record(stream)
         fdone = torch.cuda.Event()
@@ -717,7 +720,7 @@ def main():
             ev[3].record(stream)
         r = sg.exp_map_backward(mesh, "gfd", face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g,
                                 eps_v=EPS, eps_p=EPS, grad_V=gV, opts=pbopts if ev is not None else bopts,
-                                workspace=bws)
+                                workspace=bws, order=qorder)
         stream.wait_event(edone)
         if ev is not None:
             ev[4].record(stream)
@@ -818,7 +821,7 @@ def main():
 
         def compute(di):
             cs = torch.cuda.current_stream()
-            o = sg.exp_map(mesh, di["face"], di["bary"], di["v"], workspace=ws, opts=opts)
+            o = sg.exp_map(mesh, di["face"], di["bary"], di["v"], workspace=ws, opts=opts, order=qorder)
             fdone = torch.cuda.Event()
             fdone.record(cs)
             ep_stream.wait_event(fdone)
@@ -833,7 +836,7 @@ def main():
             gV.zero_()
             r = sg.exp_map_backward(mesh, "gfd", di["face"], di["bary"], di["v"], o["face"], o["bary"], o["dir"],
                                     o["status"], di["g"], eps_v=EPS, eps_p=EPS, grad_V=gV, opts=bopts,
-                                    workspace=bws)
+                                    workspace=bws, order=qorder)
             cs.wait_event(edone)
             return o, r
 
@@ -915,10 +918,13 @@ def main():
     else:
         l2 = torch.cuda.get_device_properties(dev).L2_cache_size
         sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
-    bwd_lorder = bsort == 2 or (bsort < 0 and nq >= 65536)
-    # the automatic precision adds the mixed walk over its escalation list (one launch, which finds
-    # the list empty on this workload: every walk here stays within the FP32 walk's range)
-    launches_per_step = 9 + {0: 0, 1: 5, 2: 2}[sort_mode] + (2 if bwd_lorder else 0)
+    # Library launches per step: the forward walk and the automatic precision's mixed walk over its
+    # escalation list (which finds the list empty on this workload: every walk here stays within
+    # the FP32 walk's range); EP; the GFD re-walk, literal walks (FP32 and mixed), the two assemble
+    # passes; the grad_V expansion and flush.  Plus the forward's order: its length order (two
+    # launches), start-face sort (five) or the identity written into the order buffer (one).  The
+    # backward takes the forward's order and sorts nothing.
+    launches_per_step = 10 + {0: 1, 1: 5, 2: 2}[sort_mode]
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     # Algorithmic bytes as the measurement plan defines them: the 32-B record of every face a walk
@@ -982,7 +988,7 @@ def main():
                        "kernel": "persistent" if args.kernel == 2 else "plain",
                        "autotuned": tuned,
                        "query_order": {0: "input", 1: "start face", 2: "walk length"}[sort_mode],
-                       "bwd_query_order": "walk length" if bwd_lorder else "input",
+                       "bwd_query_order": "the forward's (sg_opts.order)",
                        "fp64_classification": bool(args.fp64),
                        "launch": "eager" if graph is None else "CUDA graph of the step, captured once and replayed"},
             "crossings_per_s": world * ncross / (float(np.mean(ktimes["walk"])) * 1e-3),

@@ -137,6 +137,14 @@ typedef struct sg_opts {
                                this many queries from the queue on average (blocks per SM =
                                ceil(nq / (qpt * SMs * block)), at most the occupancy limit and the
                                blocks_per_sm given); the autotuner sweeps it. */
+    int32_t *order;         /* optional device int32[nq] buffer holding a query order.  sg_exp_map
+                               and sg_exp_map_trace write into it the order in which their kernel
+                               took the queries (its length or start-face order; the identity when
+                               they walk in input order).  sg_exp_map_backward reads it, when given,
+                               as the order of its re-walk instead of rebuilding the length order
+                               (two launches fewer): pass the buffer the forward call filled for
+                               the same queries.  It must be a permutation of 0..nq-1; an entry out
+                               of that range is skipped (no query is walked for it).  NULL: none. */
 } sg_opts;
 
 /* Fills `o` with the defaults described above. */

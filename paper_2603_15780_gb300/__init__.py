@@ -60,7 +60,7 @@ class Opts(C.Structure):
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("fp64_escalate", C.c_int32),
                 ("tau_near", C.c_float), ("tau_snap", C.c_float), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("prof_events", C.c_void_p), ("boundary_mode", C.c_int32),
-                ("precision", C.c_int32), ("queries_per_thread", C.c_int32)]
+                ("precision", C.c_int32), ("queries_per_thread", C.c_int32), ("order", C.c_void_p)]
 
 
 class MeshInfo(C.Structure):
@@ -250,10 +250,12 @@ def workspace_size(mesh: Mesh, nq: int, opts: Opts | None = None) -> int:
 
 
 def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, mesh_id=None, *, want_hash=False,
-            want_ncross=True, opts: Opts | None = None, workspace=None, out=None, stream=None, **opt_kw):
+            want_ncross=True, opts: Opts | None = None, workspace=None, out=None, stream=None, order=None,
+            **opt_kw):
     """sg_exp_map on torch CUDA tensors.  Returns dict(face, bary, pos, dir, w, status,
     ncross, hash).  `opts` (or keyword overrides such as kernel=KERNEL_PLAIN, sort=0,
-    fp64_escalate=0, block=128) map to sg_opts."""
+    fp64_escalate=0, block=128) map to sg_opts.  `order`: an int32 [nq] CUDA tensor that receives
+    the order the queries were walked in (sg_opts.order), for exp_map_backward(order=...)."""
     torch = _torch()
     face = _dev(face, torch.int32)
     nq = face.numel()
@@ -267,6 +269,8 @@ def exp_map(mesh: Mesh, face, bary, v, w=None, length=None, mesh_id=None, *, wan
     length = _dev(length, torch.float32, (nq,))
     mesh_id = _dev(mesh_id, torch.int32, (nq,))
     o = opts if opts is not None else default_opts(**opt_kw)
+    if order is not None:
+        o.order = _order_ptr(order, nq)
     if out is None:
         dev = face.device
         out = {"face": torch.empty(nq, dtype=torch.int32, device=dev),
@@ -345,9 +349,20 @@ def backward_workspace_size(mesh: Mesh, estimator, nq: int, want_grad_V: bool) -
     return n.value
 
 
+def _order_ptr(order, nq: int):
+    """Device pointer of a query-order buffer (int32 [nq], contiguous, CUDA), or None."""
+    if order is None:
+        return None
+    torch = _torch()
+    if order.dtype != torch.int32 or not order.is_cuda or not order.is_contiguous() or order.numel() != nq:
+        raise SgError(f"order: expected a contiguous int32 CUDA tensor of {nq} entries")
+    return order.data_ptr()
+
+
 def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_bary, end_dir, end_status, g_pos,
                      mesh_id=None, *, g_bary=None, g_dir=None, g_w=None, eps_v=1e-4, eps_p=1e-4,
-                     want_grad_V=False, grad_V=None, opts: Opts | None = None, workspace=None, stream=None):
+                     want_grad_V=False, grad_V=None, opts: Opts | None = None, workspace=None, stream=None,
+                     order=None):
     """sg_exp_map_backward.  estimator: "ep"/"gfd" or EST_*.  Upstream gradients: g_pos (end
     point), optional g_bary (end barycentrics), g_dir (end direction), g_w [nq, n_w, 3] (carried
     vectors).  Returns dict(grad_v, grad_p, grad_bary, grad_w (if g_w), grad_V (if requested;
@@ -382,6 +397,8 @@ def exp_map_backward(mesh: Mesh, estimator, face, bary, v, end_face, end_bary, e
             grad_V = torch.zeros(mesh.n_vertices, 3, device=dev)
         res["grad_V"] = grad_V
     o = opts if opts is not None else default_opts()
+    if order is not None:  # the forward call's order (else the one in opts, if any)
+        o.order = _order_ptr(order, nq)
     if workspace is None:
         workspace = torch.empty(backward_workspace_size(mesh, est, nq, "grad_V" in res), dtype=torch.uint8,
                                 device=dev)
@@ -513,10 +530,12 @@ def _autograd_function():
 
         @staticmethod
         def forward(ctx, mesh, face, bary, v, estimator="gfd", V=None, mesh_id=None, eps=1e-4):
-            out = exp_map(mesh, face, bary.detach(), v.detach(), mesh_id=mesh_id)
+            # the forward's query order is kept for the backward's re-walk (no second sort)
+            order = torch.empty(face.numel(), dtype=torch.int32, device=face.device)
+            out = exp_map(mesh, face, bary.detach(), v.detach(), mesh_id=mesh_id, order=order)
             ctx.mesh, ctx.estimator, ctx.eps = mesh, estimator, eps
             ctx.save_for_backward(face, bary.detach(), v.detach(), out["face"], out["bary"], out["dir"],
-                                  out["status"], mesh_id if mesh_id is not None else torch.empty(0))
+                                  out["status"], mesh_id if mesh_id is not None else torch.empty(0), order)
             ctx.has_V = V is not None
             ctx.mark_non_differentiable(out["face"], out["status"])
             ctx.set_materialize_grads(False)
@@ -524,7 +543,7 @@ def _autograd_function():
 
         @staticmethod
         def backward(ctx, g_pos, _gf, g_bary, g_dir, _gs):
-            face, bary, v, ef, eb, ed, es, mid = ctx.saved_tensors
+            face, bary, v, ef, eb, ed, es, mid, order = ctx.saved_tensors
             if g_pos is None:
                 g_pos = torch.zeros(face.numel(), 3, device=face.device)
             r = exp_map_backward(ctx.mesh, ctx.estimator, face, bary, v, ef, eb, ed, es, g_pos.contiguous(),
@@ -532,7 +551,7 @@ def _autograd_function():
                                  g_bary=None if g_bary is None else g_bary.contiguous(),
                                  g_dir=None if g_dir is None else g_dir.contiguous(),
                                  eps_v=ctx.eps, eps_p=ctx.eps,
-                                 want_grad_V=ctx.has_V and ctx.needs_input_grad[5])
+                                 want_grad_V=ctx.has_V and ctx.needs_input_grad[5], order=order)
             gV = r.get("grad_V")
             return None, None, r["grad_bary"], r["grad_v"], None, gV, None, None
 

@@ -379,8 +379,14 @@ struct RewalkJob {
     bool valid;
 
     __device__ __forceinline__ bool init(int64_t t) {
-        // the query (nq < 2^29, checked at the entry point)
+        // the query (nq < 2^29, checked at the entry point); an order entry out of range (a
+        // caller's order that is not a permutation) is skipped
         const int32_t q = A->perm ? __ldg(A->perm + t) : (int32_t)t;
+        if ((uint32_t)q >= (uint32_t)A->nq) {
+            s_rewalk_q[threadIdx.x] = -1;
+            valid = false;
+            return false;
+        }
         s_rewalk_q[threadIdx.x] = q;
         H.A = A;
         const WalkParams &P = A->P;
@@ -442,6 +448,7 @@ struct RewalkJob {
     __device__ __forceinline__ bool step() { return walker_step<true>(w, A->P, H); }
     __device__ __forceinline__ void finish() {
         const int32_t q = s_rewalk_q[threadIdx.x];
+        if (q < 0) return;
         if (!valid) {
             if (A->out_status) A->out_status[q] = (w.st & ~SG_PARITY_BIT) | (GRADV ? SG_ST_NO_GRADV : 0u);
             return;
@@ -1070,7 +1077,10 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
     A.out_status = out_status;
     A.eps_v = eps_v; A.eps_p = eps_p;
 
-    const bool lorder = (estimator == SG_EST_GFD || grad_V) && bwd_lorder(r, nq);  // only the re-walk uses it
+    // only the re-walk uses an order: the caller's (sg_opts.order, filled by the forward call), else
+    // the length order rebuilt here
+    const bool rewalk = estimator == SG_EST_GFD || grad_V;
+    const bool lorder = rewalk && !r.order && bwd_lorder(r, nq);
     BwdLayout Lw = bwd_layout(m->nV, m->nF, nq, estimator, grad_V != nullptr, lorder);
     void *ws = nullptr;
     bool own = false;
@@ -1105,7 +1115,9 @@ extern "C" sg_status sg_exp_map_backward(const sg_mesh *m, int32_t estimator, fl
         Q.lref = m->d_lref; Q.max_steps = r.max_steps; Q.want_hash = 0; Q.tau_near = r.tau_near; Q.tau_snap = r.tau_snap;
     }
     cudaMemsetAsync(A.ntask, 0, 64, s);
-    if (lorder) {
+    if (rewalk && r.order) {
+        A.perm = r.order;
+    } else if (lorder) {
         int32_t *perm = (int32_t *)(base + Lw.perm);
         sg_length_order(m, A.in, nq, (uint8_t *)(base + Lw.lkeys), (int32_t *)(base + Lw.lcounts), perm, s);
         A.perm = perm;

@@ -441,6 +441,12 @@ __device__ __forceinline__ int length_key(const QueryIn &in, const float *__rest
     return esc_lmax > 0.f ? max(k, 1) : k;
 }
 
+// the input order, for a caller's order buffer when the queries were walked unsorted
+__global__ void __launch_bounds__(256) k_iota(int64_t n, int32_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)i;
+}
+
 __global__ void __launch_bounds__(256) k_lorder_hist(int64_t nq, QueryIn in, const float *__restrict__ lref,
                                                      float esc_lmax, uint8_t *__restrict__ keys,
                                                      int32_t *__restrict__ counts) {
@@ -729,6 +735,7 @@ void sg_opts_default(sg_opts *o) {
     o->prof_events = nullptr;
     o->boundary_mode = 0;
     o->precision = 0;
+    o->order = nullptr;
 }
 
 const char *sg_status_string(sg_status s) {
@@ -939,8 +946,9 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
     // with the automatic precision the orders route the long queries to the mixed walk (the
     // length order's head, the start-face order's tail)
     const float lmax = esc ? SG_AUTO_FP32_LREF : 0.f;
+    // the order goes to the caller's buffer when one is given (sg_opts.order)
+    int32_t *perm = r.order ? r.order : (int32_t *)(base + L.perm);
     if (sort == 2) {
-        int32_t *perm = (int32_t *)(base + L.perm);
         int32_t *counts = (int32_t *)(base + L.counts);
         sg_length_order(m, a.in, nq, (uint8_t *)(base + L.keys), counts, perm, s, lmax);
         a.perm = perm;
@@ -948,7 +956,6 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
     } else if (sort == 1) {
         int32_t *counts = (int32_t *)(base + L.counts);
         int32_t *sums = (int32_t *)(base + L.sums);
-        int32_t *perm = (int32_t *)(base + L.perm);
         int64_t nk = esc ? 2 * m->nF + 1 : m->nF + 1;
         int64_t ntiles = (nk + SCAN_TILE - 1) / SCAN_TILE;
         cudaMemsetAsync(counts, 0, sizeof(int32_t) * nk, s);
@@ -1030,6 +1037,7 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
             return st;
         }
     }
+    if (r.order && !a.perm) k_iota<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, r.order);
     if (r.precision >= 40 || autoprec) {
         // the FP64 geometry and the double-float records (built with the mesh; re-derived here
         // after a vertex update)
@@ -1117,6 +1125,7 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
                (!t.pt || ((uintptr_t)t.pt % 16) == 0);
     void *own_ws = nullptr;
     sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.kernel != SG_KERNEL_PLAIN ? r.sort : 0, s, a, &own_ws);
+    if (st == SG_OK && r.order && !a.perm) k_iota<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, r.order);
     if (st != SG_OK) {
         if (own_ws) cudaFreeAsync(own_ws, s);
         return st;

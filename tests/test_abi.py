@@ -69,3 +69,25 @@ def test_header_is_plain_c_and_cxx():
         if shutil.which(cc) is None:
             pytest.skip(f"{cc} not available")
         subprocess.check_call([cc, "-fsyntax-only", std, "-Wall", "-Werror", "-x", lang, hdr])
+
+
+def test_opts_mirror_matches_the_header():
+    """The binding's ctypes mirror of sg_opts has the header's size and field offsets."""
+    import shutil
+    import subprocess
+    import tempfile
+    import paper_2603_15780_gb300 as sg
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    fields = [f for f, _ in sg.Opts._fields_]
+    src = '#include <stdio.h>\n#include <stddef.h>\n#include "sgeo.h"\nint main(void) {\n'
+    src += '    printf("%zu\\n", sizeof(sg_opts));\n'
+    src += "".join(f'    printf("%zu\\n", offsetof(sg_opts, {f}));\n' for f in fields) + "    return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "o.c"), os.path.join(d, "o")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert got[0] == C.sizeof(sg.Opts)
+    assert got[1:] == [getattr(sg.Opts, f).offset for f in fields]
+    assert not sg.default_opts().order   # no order buffer unless the caller gives one

@@ -61,3 +61,41 @@ def test_forward_and_backward_are_independent_of_the_query_order():
             assert torch.equal(base[2][k], res[sort][2][k]), f"sort {sort}: backward {k} differs"
         gV0, gV1 = base[2]["grad_V"], res[sort][2]["grad_V"]
         assert float((gV0 - gV1).abs().max()) <= 1e-5 * float(gV0.abs().max())
+
+
+def test_backward_reuses_the_forward_order():
+    """sg_opts.order: the forward writes the order it walked the queries in (a permutation; the
+    identity when it walks them in input order) and the backward's re-walk takes the queries in
+    that order instead of sorting them again.  Same gradients as the backward's own order."""
+    import torch
+    import paper_2603_15780_gb300 as sg
+    rng = np.random.default_rng(142)
+    n = 100_000
+    meshes, q, mid = _batch(n, rng)
+    mesh = sg.Mesh([(parity.as_f32(X), F) for X, F in meshes])
+    f32 = parity.as_f32
+    dev = "cuda"
+    face = torch.tensor(q.face, device=dev)
+    bary = torch.tensor(f32(q.bary), device=dev)
+    v = torch.tensor(f32(q.v), device=dev)
+    g = torch.tensor(f32(q.g_pos), device=dev)
+    midt = torch.tensor(mid, device=dev)
+    order = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    out = sg.exp_map(mesh, face, bary, v, mesh_id=midt, order=order)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(n))            # a permutation of the queries
+    assert not np.array_equal(o, np.arange(n))                 # the length order, not the input order
+    ident = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    out_plain = sg.exp_map(mesh, face, bary, v, mesh_id=midt, order=ident, sort=0)
+    assert np.array_equal(ident.cpu().numpy(), np.arange(n))   # walked in input order
+    assert torch.equal(out_plain["face"], out["face"]) and torch.equal(out_plain["pos"], out["pos"])
+    for est in ("gfd", "ep"):
+        args = (mesh, est, face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g)
+        a = sg.exp_map_backward(*args, mesh_id=midt, want_grad_V=True)
+        b = sg.exp_map_backward(*args, mesh_id=midt, want_grad_V=True, order=order)
+        torch.cuda.synchronize()
+        for k in ("grad_v", "grad_p", "grad_bary", "status"):
+            assert torch.equal(a[k], b[k]), (est, k)
+        gva, gvb = a["grad_V"].cpu().numpy(), b["grad_V"].cpu().numpy()
+        scale = np.abs(gva).max()
+        assert np.abs(gva - gvb).max() <= 1e-5 * scale, (est, np.abs(gva - gvb).max(), scale)
