@@ -340,6 +340,8 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
  *   grad_w     float32 [nq][n_w][3]  dL/dw = R^T g_w (parallel transport is a rotation of the
  *                               tangent planes for a fixed face sequence; exact)
  *   out_status uint32 [nq]      SG_ST_* of the extra walks (GFD) or of the re-walk
+ * The re-walk (GFD, or grad_V) takes the queries in the order o->order holds when it is given
+ * (the forward call's, see sg_opts.order), else in its own length order.
  * Asynchronous on `stream`.  Errors: SG_ERR_INVALID_ARG (bad estimator, eps <= 0 for GFD, a
  * required array NULL, nq above 536,869,887), SG_ERR_UNSUPPORTED (precision 40, 48 or 64), SG_ERR_OOM
  * (no workspace given and none could be allocated), SG_ERR_CUDA.
@@ -439,9 +441,11 @@ sg_status sg_transport_back(const sg_mesh *m, int64_t nq, const int32_t *mesh_id
  * nq queries with `estimator` (SG_EST_*) and, if want_grad_V != 0, the vertex gradient: for
  * GFD the column table (16 B per query), the literal-walk task list (12 B per query, reused for
  * the queries whose chords are walked) and the literal walks' restart records (32 B per query);
- * for grad_V a float4 accumulator per vertex and a float2 per interior edge; 12 B per query for
- * an end-barycentric upstream gradient; and the re-walk's length order (5 B per query).  Pass it
- * as o->workspace; without it the library allocates stream-ordered scratch itself.
+ * for grad_V a float4 accumulator per vertex and three float4 windows per face (the crossing
+ * coefficients of each pair of the face's edges); 12 B per query for an end-barycentric upstream
+ * gradient; and the re-walk's length order (5 B per query; not used when o->order carries the
+ * forward's order).  Pass it as o->workspace; without it the library allocates stream-ordered
+ * scratch itself.
  */
 sg_status sg_exp_map_backward_workspace_size(const sg_mesh *m, int32_t estimator, int64_t nq,
                                              int32_t want_grad_V, size_t *bytes);
