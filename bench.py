@@ -682,9 +682,20 @@ def main():
            "status": torch.empty(nq, dtype=torch.int32, device=dev),
            "ncross": torch.empty(nq, dtype=torch.int32, device=dev)}
     gV = torch.zeros(mesh.n_vertices, 3, device=dev)
-    # the forward writes the order it walked the queries in and the GFD backward's re-walk takes
-    # them in that order (sg_opts.order) instead of sorting them again
-    qorder = torch.empty(nq, dtype=torch.int32, device=dev)
+    # The query order the forward's options give, as the library decides it: by start face (5
+    # sort/scan kernels) when the mesh's records (128 B per face) exceed half of L2, else by walk
+    # length (2 kernels), input order for the plain kernel and small batches.  When the forward
+    # sorts, it writes its order into `qorder` and the GFD backward's re-walk takes the queries in
+    # that order (sg_opts.order) instead of sorting them again; after an unsorted forward the
+    # backward builds its own length order (batches of at least 65,536 queries).
+    if args.kernel == 1:
+        sort_mode = 0
+    elif args.sort >= 0:
+        sort_mode = args.sort
+    else:
+        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+        sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
+    qorder = torch.empty(nq, dtype=torch.int32, device=dev) if sort_mode else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -905,26 +916,7 @@ def main():
                "pipelined": "step k+1 uploads and step k-1 downloads overlap step k; L2 flush inside",
                "launch": "eager" if graphs is None else "one captured CUDA graph per buffer slot"}
 
-    # ---- kernels the library launches per step: the walk, EP, the GFD re-walk, literal walks,
-    # assemble (with the chords) and its chord-walk pass, and the grad_V edge expansion and
-    # flush; plus the query order, as the
-    # library decides it: by start face (5 sort/scan kernels) when the mesh's records (128 B per
-    # face) exceed half of L2, else by walk length (2 kernels), for the forward and again for the
-    # backward re-walk (which uses the length order whenever the batch is large enough).
-    if args.kernel == 1:
-        sort_mode = 0
-    elif args.sort >= 0:
-        sort_mode = args.sort
-    else:
-        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-        sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
-    # Library launches per step: the forward walk and the automatic precision's mixed walk over its
-    # escalation list (which finds the list empty on this workload: every walk here stays within
-    # the FP32 walk's range); EP; the GFD re-walk, literal walks (FP32 and mixed), the two assemble
-    # passes; the grad_V expansion and flush.  Plus the forward's order: its length order (two
-    # launches), start-face sort (five) or the identity written into the order buffer (one).  The
-    # backward takes the forward's order and sorts nothing.
-    launches_per_step = 10 + {0: 1, 1: 5, 2: 2}[sort_mode]
+    launches_per_step = 10 + {0: 2 if nq >= 65536 else 0, 1: 5, 2: 2}[sort_mode]
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     # Algorithmic bytes as the measurement plan defines them: the 32-B record of every face a walk
@@ -988,7 +980,7 @@ def main():
                        "kernel": "persistent" if args.kernel == 2 else "plain",
                        "autotuned": tuned,
                        "query_order": {0: "input", 1: "start face", 2: "walk length"}[sort_mode],
-                       "bwd_query_order": "the forward's (sg_opts.order)",
+                       "bwd_query_order": "the forward's (sg_opts.order)" if sort_mode else "walk length",
                        "fp64_classification": bool(args.fp64),
                        "launch": "eager" if graph is None else "CUDA graph of the step, captured once and replayed"},
             "crossings_per_s": world * ncross / (float(np.mean(ktimes["walk"])) * 1e-3),

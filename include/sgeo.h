@@ -143,8 +143,11 @@ typedef struct sg_opts {
                                they walk in input order).  sg_exp_map_backward reads it, when given,
                                as the order of its re-walk instead of rebuilding the length order
                                (two launches fewer): pass the buffer the forward call filled for
-                               the same queries.  It must be a permutation of 0..nq-1; an entry out
-                               of that range is skipped (no query is walked for it).  NULL: none. */
+                               the same queries, after a forward that sorted them (the default for
+                               batches of at least 65,536 queries; a re-walk of a large batch in
+                               input order is slower than in the length order).  It must be a
+                               permutation of 0..nq-1; an entry out of that range is skipped (no
+                               query is walked for it).  NULL: none. */
 } sg_opts;
 
 /* Fills `o` with the defaults described above. */
