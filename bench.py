@@ -565,7 +565,11 @@ def run_features(args):
         wsh = oh.pop("_workspace")
         th = timed(lambda: sg.exp_map(mh, fh, bh, vh, opts=o, workspace=wsh, out=oh))
         st = oh["status"].cpu().numpy()
+        nc = float(oh["ncross"].sum().item())
+        # the stopping walk ends at the first boundary it meets, hole avoidance walks the whole
+        # length: crossings per second compare the two per unit of work
         res[f"holey_sphere_{name}"] = {"ms": th, "geodesics_per_s": nq / (th * 1e-3),
+                                       "crossings_per_query": nc / nq, "crossings_per_s": nc / (th * 1e-3),
                                        "boundary_frac": float(((st & 1) != 0).mean()),
                                        "hole_frac": float(((st & 2048) != 0).mean())}
     line = {"metric": "feature throughput (see entries)", "value": res["trace"]["geodesics_per_s"],

@@ -145,6 +145,47 @@ def test_cone_apex_straightest_rule(theta):
     assert np.abs(gpu["pos"] - ref["pos"])[ok].max() < 2e-5
 
 
+def test_vertex_on_a_fold_matches_development():
+    """Rays aimed exactly at the vertices of a fold line (angle sum 2pi on a folded sheet): the
+    GPU walk and its carried vector equal the development's straight line and unchanged vector,
+    refolded, whether FP32 snaps the vertex or passes beside it; against the FP64 oracle the
+    walks snapped on both sides agree in face sequence and end point."""
+    from tests import test_oracle_pins as pins
+    nx, ny, c = 9, 7, 4
+    X, F, P = meshgen.folded_strip(nx, ny, 3.0, 2.0, [(c, 0.9)])
+    X32 = parity.as_f32(X)
+    rng = np.random.default_rng(62)
+    qs = pins.fold_vertex_queries(X, F, P, c, nx, ny, 300, rng)
+    n = len(qs)
+    q = meshgen.Queries(np.array([t[0] for t in qs], np.int32), np.array([t[1] for t in qs]),
+                        np.array([t[2] for t in qs]), np.array([[t[3]] for t in qs]), np.zeros((n, 3)))
+    mesh = sg().Mesh(X32, F)
+    gpu = parity.run_gpu(mesh, q, 1)
+    diag = meshgen.bbox_diag(X)
+    checked = 0
+    for i, (f, b, v3, w3, p0, d, L, wf) in enumerate(qs):
+        if gpu["status"][i] & (oracle.BOUNDARY | oracle.NEAR_EDGE):
+            continue
+        g, bg = pins.locate(P, F, p0 + L * d, tol=1e-9)
+        A, B, C = P[F[g]]
+        a, bb, cc = X[F[g]]
+        M2 = np.stack([B - A, C - A], 1)
+        to3 = lambda u: (lambda k: k[0] * (bb - a) + k[1] * (cc - a))(np.linalg.lstsq(M2, u, rcond=None)[0])
+        assert gpu["face"][i] == g, i
+        assert np.linalg.norm(gpu["pos"][i] - bg @ X[F[g]]) <= 1e-5 * diag, i
+        assert np.abs(gpu["dir"][i] - to3(d)).max() <= 2e-4, i
+        assert np.abs(gpu["w"][i, 0] - to3(wf)).max() <= 2e-4, i
+        checked += 1
+    assert checked > n // 2
+    # the oracle snaps at the GPU's radius: the float32 rays miss the vertex by ~1e-7 l_ref
+    ref, _ = parity.run_oracle(X32, F, q, 1, tau_snap=1e-6)
+    both = ((gpu["status"] & ref["status"]) & oracle.VERTEX_HIT) != 0
+    assert both.mean() > 0.5
+    ok = both & (((gpu["status"] | ref["status"]) & parity.FLAGS) == 0)
+    assert np.array_equal(gpu["hash"][ok], ref["hash"][ok]) and np.array_equal(gpu["face"][ok], ref["face"][ok])
+    assert np.linalg.norm(gpu["pos"] - ref["pos"], axis=1)[ok].max() <= 1e-5 * diag
+
+
 def test_torus_subset_two_carried_vectors():
     """Workload-1 mesh (noisy torus 262,144 faces), 50k of its queries, 2 carried vectors."""
     wl = meshgen.workload(1, scale=50000 / 4194304)

@@ -33,6 +33,13 @@ MUTATIONS = [
      "w[3 * q + i] = wl[q] * (cos(phi[q]) * dout[i] + sin(phi[q]) * c[i]);",
      "w[3 * q + i] = wl[q] * (cos(phi[q]) * dout[i] - sin(phi[q]) * c[i]);",
      [lambda: pins.test_cone_vertex_straightest_rule(1.8 * math.pi)]),
+    ("carried vector mirrored at a vertex, against the development at a vertex of angle sum 2pi",
+     "w[3 * q + i] = wl[q] * (cos(phi[q]) * dout[i] + sin(phi[q]) * c[i]);",
+     "w[3 * q + i] = wl[q] * (cos(phi[q]) * dout[i] - sin(phi[q]) * c[i]);",
+     [lambda: pins.test_vertex_on_a_fold_matches_development(0.9)]),
+    ("straightest rule splits theta unevenly, against the development at a vertex of angle sum 2pi",
+     "double half = 0.5 * m->theta[v0];", "double half = 0.45 * m->theta[v0];",
+     [lambda: pins.test_vertex_on_a_fold_matches_development(-1.7)]),
     ("barycentrics swapped on entering the neighbour",
      "s->b[gj] = sj; s->b[gk] = sk; s->b[gz] = 0.0;", "s->b[gj] = sk; s->b[gk] = sj; s->b[gz] = 0.0;",
      [pins.test_flat_mesh_endpoint_is_p_plus_v,

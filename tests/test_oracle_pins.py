@@ -87,6 +87,74 @@ def test_folded_strip_matches_development(folds):
     assert n_checked > 150
 
 
+def fold_vertex_queries(X, F, P, fold_col, nx, ny, n, rng):
+    """Rays of a folded strip aimed exactly at the interior vertices of the fold line
+    `fold_col`, from random points left of it, with a carried vector at a random angle.  Returns
+    per query the start face and barycentrics, the 3-D v and w, and the development's start
+    point, direction and length (in the flat strip P)."""
+    out = []
+    xs, ys = np.unique(P[:, 0]), np.unique(P[:, 1])
+    xc = xs[fold_col]
+    for _ in range(n):
+        V = np.array([xc, ys[int(rng.integers(1, ny - 1))], 0.0])
+        # a start point strictly inside a face left of the fold line
+        while True:
+            p0 = np.array([rng.uniform(0.05, xc - 0.05), rng.uniform(0.05, ys[-1] - 0.05), 0.0])
+            try:
+                f, b = locate(P, F, p0, tol=1e-12)
+            except AssertionError:
+                continue
+            break
+        d = V - p0
+        dist = np.linalg.norm(d)
+        d /= dist
+        L = dist + rng.uniform(0.1, 0.6)
+        beta = rng.uniform(-math.pi, math.pi)
+        wf = math.cos(beta) * d + math.sin(beta) * np.array([-d[1], d[0], 0.0])
+        # the face's flat -> 3-D isometry, written through its edge vectors
+        A, B, C = P[F[f]]
+        a, bb, c = X[F[f]]
+        M2 = np.stack([B - A, C - A], 1)
+        to3 = lambda u: (lambda k: k[0] * (bb - a) + k[1] * (c - a))(np.linalg.lstsq(M2, u, rcond=None)[0])
+        out.append((f, b, to3(d) * L, to3(wf), p0, d, L, wf))
+    return out
+
+
+@pytest.mark.parametrize("angle", [0.9, -1.7])
+def test_vertex_on_a_fold_matches_development(angle):
+    """Alg. transport_over_vertex at a vertex of angle sum 2pi on a folded (developable) sheet:
+    the straightest ray through it is the development's straight line, refolded, and the carried
+    vectors are the development's unchanged vectors, refolded -- whatever rule transports them
+    at vertices of other angle sums.  Rays are aimed exactly at the vertices of the fold line."""
+    nx, ny, c = 9, 7, 4
+    X, F, P = meshgen.folded_strip(nx, ny, 3.0, 2.0, [(c, angle)])
+    m = oracle.Mesh(X, F)
+    th, bnd = m.theta()
+    xs = np.unique(P[:, 0])
+    on_fold = np.where((np.abs(P[:, 0] - xs[c]) < 1e-12) & ~bnd)[0]
+    assert len(on_fold) == ny - 2 and np.abs(th[on_fold] - 2 * math.pi).max() < 1e-12
+    rng = np.random.default_rng(61)
+    qs = fold_vertex_queries(X, F, P, c, nx, ny, 120, rng)
+    out = oracle.exp_map(m, [q[0] for q in qs], [q[1] for q in qs], [q[2] for q in qs], [[q[3]] for q in qs])
+    checked = 0
+    for i, (f, b, v3, w3, p0, d, L, wf) in enumerate(qs):
+        st = out["status"][i]
+        assert st & oracle.VERTEX_HIT, i
+        if st & (oracle.BOUNDARY | oracle.NEAR_VERTEX | oracle.NEAR_EDGE):
+            continue
+        g, bg = locate(P, F, p0 + L * d, tol=1e-9)
+        A, B, C = P[F[g]]
+        a, bb, cc = X[F[g]]
+        M2 = np.stack([B - A, C - A], 1)
+        to3 = lambda u: (lambda k: k[0] * (bb - a) + k[1] * (cc - a))(np.linalg.lstsq(M2, u, rcond=None)[0])
+        assert out["face"][i] == g
+        assert np.abs(out["pos"][i] - bg @ X[F[g]]).max() < 1e-11
+        assert np.abs(out["dir"][i] - to3(d)).max() < 1e-11
+        assert np.abs(out["w"][i, 0] - to3(wf)).max() < 1e-11
+        checked += 1
+    assert checked > 60
+
+
 # --------------------------------------------------------------------------- exact brute force
 def _rational_queries(pc: Polycube, n, rng):
     qs = []
