@@ -54,7 +54,8 @@
 
 #define SG_BWD_MAX_W 4
 // lanes of a warp that must be idle before the re-walk refills them together (swept under the
-// length order with the paired grad_V reductions: 16 0.706, 20 0.686, 24 0.648, 28 0.631 ms)
+// length order with the paired grad_V reductions: 16 0.706, 20 0.686, 24 0.648, 28 0.631,
+// 32 0.633 ms)
 #ifndef SG_REWALK_REFILL
 #define SG_REWALK_REFILL 28
 #endif
@@ -68,8 +69,9 @@
 #ifndef SG_LITERAL_MINB
 #define SG_LITERAL_MINB 7
 #endif
-// minimum resident blocks per SM of the re-walk (71 registers at 7 without spills, with the
-// straddle test's rare constants, the query id and the face offset in shared memory)
+// minimum resident blocks per SM of the re-walk (69 registers at 7 without spills, with the
+// straddle test's rare constants, the query id and the face offset in shared memory; 6 blocks
+// time the same)
 #ifndef SG_REWALK_MINB
 #define SG_REWALK_MINB 7
 #endif
