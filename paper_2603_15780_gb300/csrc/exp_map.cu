@@ -7,8 +7,9 @@
 //                      counter as soon as their current walk ends, so lanes do not idle
 //                      behind the longest walk of their warp (the long tail of path
 //                      lengths the paper leaves to idle threads).  Queries can be taken in
-//                      start-face order (counting sort by global face id) so neighbouring
-//                      lanes gather the same records.
+//                      start-face order (counting sort by the start face's place on the
+//                      mesh's Z-order curve of face centroids) so that neighbouring lanes start
+//                      in one patch of the surface and gather nearby records.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -386,37 +387,39 @@ __device__ __forceinline__ float query_length(const QueryIn &in, int64_t i) {
     return sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
 }
 
-// Key of query i: its global start face; nF for an invalid query.  With the automatic precision
-// (esc_lmax > 0) the queries longer than esc_lmax l_ref, which the mixed walk takes, keep their
-// start face as key and form the permutation's head; the others get nF + their start face, and an
+// Key of query i: the spatial rank of its start face (its place on its mesh's Z-order curve of
+// face centroids, offset by the mesh's first face); nF for an invalid query.  With the automatic
+// precision (esc_lmax > 0) the queries longer than esc_lmax l_ref, which the mixed walk takes,
+// keep that rank as key and form the permutation's head; the others get nF + the rank, and an
 // invalid query 2 nF.
 __device__ __forceinline__ int face_key(const QueryIn &in, const int32_t *__restrict__ face_off,
-                                        const float *__restrict__ lref, int32_t nF, float esc_lmax, int64_t i) {
+                                        const int32_t *__restrict__ srank, const float *__restrict__ lref,
+                                        int32_t nF, float esc_lmax, int64_t i) {
     const int inval = esc_lmax > 0.f ? 2 * nF : nF;
     const int m = in.mesh_id ? __ldg(in.mesh_id + i) : 0;
     if (m < 0 || m >= in.n_mesh) return inval;
     const int lo = __ldg(face_off + m), hi = __ldg(face_off + m + 1);
     const int f = __ldg(in.face + i);
     if (f < 0 || f >= hi - lo) return inval;
-    int key = lo + f;
+    int key = __ldg(srank + lo + f);  // in [lo, hi): the face's place on the mesh's Z-order curve
     if (esc_lmax > 0.f && !(query_length(in, i) > esc_lmax * __ldg(lref + m))) key += nF;
     return key;
 }
 
 __global__ void k_sort_keys_hist(int64_t nq, QueryIn in, const int32_t *__restrict__ face_off,
-                                 const float *__restrict__ lref, int32_t nF, float esc_lmax,
-                                 int32_t *__restrict__ counts) {
+                                 const int32_t *__restrict__ srank, const float *__restrict__ lref, int32_t nF,
+                                 float esc_lmax, int32_t *__restrict__ counts) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(counts + face_key(in, face_off, lref, nF, esc_lmax, i), 1);
+        atomicAdd(counts + face_key(in, face_off, srank, lref, nF, esc_lmax, i), 1);
 }
 
 // after the scatter offsets[k] is the end of bucket k (with the automatic precision offsets[nF - 1]
 // is the number of routed queries at the head)
 __global__ void k_sort_scatter(int64_t nq, QueryIn in, const int32_t *__restrict__ face_off,
-                               const float *__restrict__ lref, int32_t nF, float esc_lmax,
-                               int32_t *__restrict__ offsets, int32_t *__restrict__ perm) {
+                               const int32_t *__restrict__ srank, const float *__restrict__ lref, int32_t nF,
+                               float esc_lmax, int32_t *__restrict__ offsets, int32_t *__restrict__ perm) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
-        const int pos = atomicAdd(offsets + face_key(in, face_off, lref, nF, esc_lmax, i), 1);
+        const int pos = atomicAdd(offsets + face_key(in, face_off, srank, lref, nF, esc_lmax, i), 1);
         perm[pos] = (int32_t)i;
     }
 }
@@ -824,6 +827,7 @@ sg_status sg_mesh_create_batched(const float *V, const int64_t *v_off, const int
               up((void **)&m->d_frm, H.frm.data(), sizeof(float4) * H.frm.size()) &&
               up((void **)&m->d_half, H.half.data(), sizeof(int4) * H.half.size()) &&
               up((void **)&m->d_edges, H.edges.data(), sizeof(int2) * std::max<size_t>(H.edges.size(), 1)) &&
+              up((void **)&m->d_srank, H.srank.data(), sizeof(int32_t) * H.srank.size()) &&
               up((void **)&m->d_V, H.V.data(), sizeof(float4) * H.V.size()) &&
               up((void **)&m->d_face_off, H.face_off.data(), sizeof(int32_t) * H.face_off.size()) &&
               up((void **)&m->d_lref, H.lref.data(), sizeof(float) * H.lref.size());
@@ -858,6 +862,7 @@ sg_status sg_mesh_destroy(sg_mesh *m) {
     cudaFree(m->d_frm);
     cudaFree(m->d_half);
     cudaFree(m->d_edges);
+    cudaFree(m->d_srank);
     cudaFree(m->d_V);
     cudaFree(m->d_face_off);
     cudaFree(m->d_lref);
@@ -963,11 +968,12 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         int g = (int)std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 8);
-        k_sort_keys_hist<<<g, 256, 0, s>>>(nq, a.in, m->d_face_off, m->d_lref, (int32_t)m->nF, lmax, counts);
+        k_sort_keys_hist<<<g, 256, 0, s>>>(nq, a.in, m->d_face_off, m->d_srank, m->d_lref, (int32_t)m->nF, lmax, counts);
         k_scan_tiles<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(counts, nk, sums);
         k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums, ntiles);
         k_scan_add<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(counts, nk, sums);
-        k_sort_scatter<<<g, 256, 0, s>>>(nq, a.in, m->d_face_off, m->d_lref, (int32_t)m->nF, lmax, counts, perm);
+        k_sort_scatter<<<g, 256, 0, s>>>(nq, a.in, m->d_face_off, m->d_srank, m->d_lref, (int32_t)m->nF, lmax, counts,
+                                         perm);
         a.perm = perm;
         if (esc) a.route_n = counts + m->nF - 1;  // the head: up to the end of bucket nF - 1
     }

@@ -32,6 +32,50 @@ inline int bits(float f) {
     return i;
 }
 
+// 21 bits of x spread to every third bit of a 63-bit Z-order (Morton) code
+inline uint64_t spread3(uint64_t x) {
+    x &= 0x1fffffULL;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+// The spatial rank of the faces of one mesh: their order along the Z-order curve of the face
+// centroids in the mesh's bounding cube (ties by face id), offset by the mesh's first face.  It
+// orders queries by start face so that a warp's walks start in one patch of the surface.
+void spatial_ranks(const float *V, const int32_t *Fm, int64_t v0, int64_t f0, int64_t nf, int32_t *rank) {
+    std::vector<double> c(3 * nf);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t f = 0; f < nf; ++f)
+        for (int k = 0; k < 3; ++k) {
+            const double x = ((double)V[3 * (v0 + Fm[3 * f]) + k] + (double)V[3 * (v0 + Fm[3 * f + 1]) + k] +
+                              (double)V[3 * (v0 + Fm[3 * f + 2]) + k]) / 3.0;
+            c[3 * f + k] = x;
+            lo[k] = std::min(lo[k], x);
+            hi[k] = std::max(hi[k], x);
+        }
+    // one scale for the three axes (the largest extent), so that a thin dimension (a heightfield's
+    // z) takes few of the curve's bits and the order follows the surface
+    const double span = std::max(std::max(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+    std::vector<uint64_t> key(nf);
+    for (int64_t f = 0; f < nf; ++f) {
+        uint64_t code = 0;
+        for (int k = 0; k < 3; ++k) {
+            const double t = span > 0.0 ? (c[3 * f + k] - lo[k]) / span : 0.0;
+            const uint64_t q = (uint64_t)std::min(std::max(t * 2097151.0, 0.0), 2097151.0);
+            code |= spread3(q) << k;
+        }
+        key[f] = code;
+    }
+    std::vector<int64_t> idx(nf);
+    std::iota(idx.begin(), idx.end(), (int64_t)0);
+    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return key[a] < key[b] || (key[a] == key[b] && a < b); });
+    for (int64_t r = 0; r < nf; ++r) rank[idx[r]] = (int32_t)(f0 + r);
+}
+
 struct EdgeKey {
     int32_t a, b;  // a < b, local vertex ids
     int32_t f;     // local face
@@ -55,6 +99,7 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
     out->half.assign(6 * nF, int4{0, 0, 0, 0});
     out->edges.clear();
     out->edges.reserve((size_t)(1.5 * nF) + 16);
+    out->srank.assign(nF, 0);
     out->V.assign(nV, float4{0, 0, 0, 0});
     out->face_off.assign(n_mesh + 1, 0);
     out->lref.assign(n_mesh, 0.f);
@@ -225,5 +270,7 @@ sg_status sg_build_host_mesh(const float *V, const int64_t *v_off, const int32_t
         float th = (float)theta[v];
         out->V[v] = float4{p[0], p[1], p[2], boundary[v] ? -th : th};
     }
+    for (int m = 0; m < n_mesh; ++m)
+        spatial_ranks(V, F + 3 * f_off[m], v_off[m], f_off[m], f_off[m + 1] - f_off[m], out->srank.data() + f_off[m]);
     return SG_OK;
 }

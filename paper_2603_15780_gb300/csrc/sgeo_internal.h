@@ -29,6 +29,9 @@
 //   edges int2[nE]     (canonical half-edge, twin half-edge) of each interior edge
 //   V     float4[nV]   vertex position (x,y,z); .w = total angle theta(x), negated for boundary
 //                      vertices (Sec. 4: theta = sum of incident corner angles)
+//   srank int32[nF]    spatial rank of each face: face_off[m] + its position in the Z-order
+//                      (Morton order) of the face centroids of mesh m, the key of the start-face
+//                      query order (queries of a warp then start in one patch of the surface)
 //   face_off int32[n_mesh+1], lref float[n_mesh] (mean edge length per mesh; -1 marks a mesh whose
 //                      vertices were moved to a degenerate face, every query on it is rejected)
 //
@@ -52,6 +55,7 @@ struct sg_mesh {
     int4 *d_half = nullptr;
     int2 *d_edges = nullptr;
     int64_t nE = 0;
+    int32_t *d_srank = nullptr;
     float4 *d_V = nullptr;
     int32_t *d_face_off = nullptr;
     float *d_lref = nullptr;
@@ -80,6 +84,7 @@ struct sg_mesh {
 struct sg_host_mesh {
     std::vector<int4> rec, fv, half;
     std::vector<int2> edges;
+    std::vector<int32_t> srank;
     std::vector<float4> frm;
     std::vector<float4> V;
     std::vector<int32_t> face_off;
