@@ -688,10 +688,10 @@ def main():
     gV = torch.zeros(mesh.n_vertices, 3, device=dev)
     # The query order the forward's options give, as the library decides it: by start face (5
     # sort/scan kernels) when the mesh's records (128 B per face) exceed half of L2, else by walk
-    # length (2 kernels), input order for the plain kernel and small batches.  When the forward
-    # sorts, it writes its order into `qorder` and the GFD backward's re-walk takes the queries in
-    # that order (sg_opts.order) instead of sorting them again; after an unsorted forward the
-    # backward builds its own length order (batches of at least 65,536 queries).
+    # length (2 kernels), input order for the plain kernel and small batches.  The forward writes
+    # the length order into `qorder` (its own queue's, or two more launches after another order)
+    # and the GFD backward's re-walk takes the queries in that order (sg_opts.order) instead of
+    # sorting them again.
     if args.kernel == 1:
         sort_mode = 0
     elif args.sort >= 0:
@@ -699,7 +699,7 @@ def main():
     else:
         l2 = torch.cuda.get_device_properties(dev).L2_cache_size
         sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
-    qorder = torch.empty(nq, dtype=torch.int32, device=dev) if sort_mode else None
+    qorder = torch.empty(nq, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -920,7 +920,7 @@ def main():
                "pipelined": "step k+1 uploads and step k-1 downloads overlap step k; L2 flush inside",
                "launch": "eager" if graphs is None else "one captured CUDA graph per buffer slot"}
 
-    launches_per_step = 10 + {0: 2 if nq >= 65536 else 0, 1: 5, 2: 2}[sort_mode]
+    launches_per_step = 10 + {0: 2, 1: 7, 2: 2}[sort_mode]
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / measured launch time)
     # Algorithmic bytes as the measurement plan defines them: the 32-B record of every face a walk
@@ -984,7 +984,7 @@ def main():
                        "kernel": "persistent" if args.kernel == 2 else "plain",
                        "autotuned": tuned,
                        "query_order": {0: "input", 1: "start face", 2: "walk length"}[sort_mode],
-                       "bwd_query_order": "the forward's (sg_opts.order)" if sort_mode else "walk length",
+                       "bwd_query_order": "walk length, written by the forward (sg_opts.order)",
                        "fp64_classification": bool(args.fp64),
                        "launch": "eager" if graph is None else "CUDA graph of the step, captured once and replayed"},
             "crossings_per_s": world * ncross / (float(np.mean(ktimes["walk"])) * 1e-3),

@@ -138,16 +138,16 @@ typedef struct sg_opts {
                                ceil(nq / (qpt * SMs * block)), at most the occupancy limit and the
                                blocks_per_sm given); the autotuner sweeps it. */
     int32_t *order;         /* optional device int32[nq] buffer holding a query order.  sg_exp_map
-                               and sg_exp_map_trace write into it the order in which their kernel
-                               took the queries (its length or start-face order; the identity when
-                               they walk in input order).  sg_exp_map_backward reads it, when given,
-                               as the order of its re-walk instead of rebuilding the length order
-                               (two launches fewer): pass the buffer the forward call filled for
-                               the same queries, after a forward that sorted them (the default for
-                               batches of at least 65,536 queries; a re-walk of a large batch in
-                               input order is slower than in the length order).  It must be a
-                               permutation of 0..nq-1; an entry out of that range is skipped (no
-                               query is walked for it).  NULL: none. */
+                               and sg_exp_map_trace write into it the walk-length order of the
+                               queries (longest first, the order sg_exp_map_backward's re-walk
+                               takes): their own queue's order when they took the queries in that
+                               order (no cost), else one built for the buffer (two launches, after
+                               a start-face or input-order walk).  sg_exp_map_backward reads it,
+                               when given, as the order of its re-walk instead of rebuilding the
+                               length order (two launches fewer): pass the buffer the forward call
+                               filled for the same queries.  It must be a permutation of
+                               0..nq-1; an entry out of that range is skipped (no query is walked
+                               for it).  NULL: none. */
 } sg_opts;
 
 /* Fills `o` with the defaults described above. */

@@ -444,12 +444,6 @@ __device__ __forceinline__ int length_key(const QueryIn &in, const float *__rest
     return esc_lmax > 0.f ? max(k, 1) : k;
 }
 
-// the input order, for a caller's order buffer when the queries were walked unsorted
-__global__ void __launch_bounds__(256) k_iota(int64_t n, int32_t *__restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (int32_t)i;
-}
-
 __global__ void __launch_bounds__(256) k_lorder_hist(int64_t nq, QueryIn in, const float *__restrict__ lref,
                                                      float esc_lmax, uint8_t *__restrict__ keys,
                                                      int32_t *__restrict__ counts) {
@@ -576,7 +570,7 @@ thread_local char g_err[256];
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-    size_t counter, counts, sums, keys, perm, esc, total;
+    size_t counter, counts, sums, keys, perm, esc, lkeys, lcounts, total;
 };
 
 // The 64-byte counter block (zeroed by every call): [0] the walk's tickets, [1] the mixed walk's
@@ -601,6 +595,10 @@ WsLayout ws_layout(int64_t nF, int64_t nq, int sort, bool esc = false) {
         L.counts = o; o = align_up(o + sizeof(int32_t) * 2 * SG_LBUCKETS, 256);
         L.keys = o; o = align_up(o + (size_t)std::max<int64_t>(nq, 1), 256);
         L.perm = o; o = align_up(o + sizeof(int32_t) * std::max<int64_t>(nq, 1), 256);
+    }
+    if (sort != 2) {  // the length order written into a caller's order buffer (sg_opts.order)
+        L.lcounts = o; o = align_up(o + sizeof(int32_t) * 2 * SG_LBUCKETS, 256);
+        L.lkeys = o; o = align_up(o + (size_t)std::max<int64_t>(nq, 1), 256);
     }
     L.total = o;
     return L;
@@ -951,8 +949,9 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
     // with the automatic precision the orders route the long queries to the mixed walk (the
     // length order's head, the start-face order's tail)
     const float lmax = esc ? SG_AUTO_FP32_LREF : 0.f;
-    // the order goes to the caller's buffer when one is given (sg_opts.order)
-    int32_t *perm = r.order ? r.order : (int32_t *)(base + L.perm);
+    // A caller's order buffer (sg_opts.order) receives the length order: the queue's own when it
+    // takes the queries in that order, else one built for the buffer after the queue's
+    int32_t *perm = (r.order && sort == 2) ? r.order : (int32_t *)(base + L.perm);
     if (sort == 2) {
         int32_t *counts = (int32_t *)(base + L.counts);
         sg_length_order(m, a.in, nq, (uint8_t *)(base + L.keys), counts, perm, s, lmax);
@@ -980,6 +979,8 @@ sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, co
     // the FP32 walk starts its tickets after the routed head
     if (a.route_n && cudaMemcpyAsync(a.counter, a.route_n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return SG_ERR_CUDA;
+    if (r.order && sort != 2)
+        sg_length_order(m, a.in, nq, (uint8_t *)(base + L.lkeys), (int32_t *)(base + L.lcounts), r.order, s, 0.f);
     return SG_OK;
 }
 
@@ -1036,14 +1037,13 @@ sg_status sg_exp_map(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const
 
     const bool persistent = r.kernel == SG_KERNEL_PERSISTENT;
     void *own_ws = nullptr;
-    if (persistent || autoprec) {
+    if (persistent || autoprec || r.order) {
         sg_status st = prepare_queue(m, nq, mesh_id, face, r, persistent ? r.sort : 0, s, a, &own_ws, autoprec);
         if (st != SG_OK) {
             if (own_ws) cudaFreeAsync(own_ws, s);
             return st;
         }
     }
-    if (r.order && !a.perm) k_iota<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, r.order);
     if (r.precision >= 40 || autoprec) {
         // the FP64 geometry and the double-float records (built with the mesh; re-derived here
         // after a vertex update)
@@ -1131,7 +1131,6 @@ sg_status sg_exp_map_trace(const sg_mesh *m, int64_t nq, const int32_t *mesh_id,
                (!t.pt || ((uintptr_t)t.pt % 16) == 0);
     void *own_ws = nullptr;
     sg_status st = prepare_queue(m, nq, mesh_id, face, r, r.kernel != SG_KERNEL_PLAIN ? r.sort : 0, s, a, &own_ws);
-    if (st == SG_OK && r.order && !a.perm) k_iota<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, r.order);
     if (st != SG_OK) {
         if (own_ws) cudaFreeAsync(own_ws, s);
         return st;

@@ -64,9 +64,10 @@ def test_forward_and_backward_are_independent_of_the_query_order():
 
 
 def test_backward_reuses_the_forward_order():
-    """sg_opts.order: the forward writes the order it walked the queries in (a permutation; the
-    identity when it walks them in input order) and the backward's re-walk takes the queries in
-    that order instead of sorting them again.  Same gradients as the backward's own order."""
+    """sg_opts.order: the forward writes the walk-length order of the queries (longest first) into
+    the buffer, whatever order its own kernel took them in, and the backward's re-walk takes the
+    queries in that order instead of sorting them again.  Same gradients as the backward's own
+    order."""
     import torch
     import paper_2603_15780_gb300 as sg
     rng = np.random.default_rng(142)
@@ -80,15 +81,28 @@ def test_backward_reuses_the_forward_order():
     v = torch.tensor(f32(q.v), device=dev)
     g = torch.tensor(f32(q.g_pos), device=dev)
     midt = torch.tensor(mid, device=dev)
-    order = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    # the length key: an eighth of an octave of |v| / l_ref per bucket (the meshes' mean edge lengths)
+    lref = np.array([np.linalg.norm(X[F[:, [1, 2, 0]]] - X[F], axis=2).mean() for X, F in meshes])
+    L = np.linalg.norm(f32(q.v).astype(np.float64), axis=1)
+    key = np.floor(8 * np.log2(L / lref[mid]))
+    ref = None
+    for kw in (dict(), dict(sort=0), dict(sort=1), dict(kernel=1, sort=0, precision=32)):
+        order = torch.full((n,), -7, dtype=torch.int32, device=dev)
+        out = sg.exp_map(mesh, face, bary, v, mesh_id=midt, order=order, **kw)
+        o = order.cpu().numpy()
+        assert np.array_equal(np.sort(o), np.arange(n)), kw             # a permutation of the queries
+        # longest first: bucket keys non-increasing along the order (one bucket of slack for the
+        # float32 rounding of the key on the device)
+        assert np.all(np.diff(key[o]) <= 1.0), kw
+        assert key[o[: n // 10]].mean() > key[o[-n // 10:]].mean() + 8, kw
+        if kw.get("kernel") == 1:
+            continue  # the plain kernel: another launch shape, results compared elsewhere
+        if ref is None:
+            ref = out
+        else:  # the persistent kernel gives the same results in every query order
+            assert torch.equal(out["face"], ref["face"]) and torch.equal(out["pos"], ref["pos"]), kw
+    order = torch.empty(n, dtype=torch.int32, device=dev)
     out = sg.exp_map(mesh, face, bary, v, mesh_id=midt, order=order)
-    o = order.cpu().numpy()
-    assert np.array_equal(np.sort(o), np.arange(n))            # a permutation of the queries
-    assert not np.array_equal(o, np.arange(n))                 # the length order, not the input order
-    ident = torch.full((n,), -7, dtype=torch.int32, device=dev)
-    out_plain = sg.exp_map(mesh, face, bary, v, mesh_id=midt, order=ident, sort=0)
-    assert np.array_equal(ident.cpu().numpy(), np.arange(n))   # walked in input order
-    assert torch.equal(out_plain["face"], out["face"]) and torch.equal(out_plain["pos"], out["pos"])
     for est in ("gfd", "ep"):
         args = (mesh, est, face, bary, v, out["face"], out["bary"], out["dir"], out["status"], g)
         a = sg.exp_map_backward(*args, mesh_id=midt, want_grad_V=True)
