@@ -114,12 +114,19 @@ def test_gfd_matches_oracle_gfd(sphere6):
     assert unsplit.mean() > 0.6
     assert rel(gpu["grad_v"], ref["grad_v"])[unsplit].max() < 1e-3
     assert rel(gpu["grad_p"], ref["grad_p"])[unsplit].max() < 1e-3
+    # Queries with a swept vertex: the GPU's FP32 literal walks (restarted at the first swept
+    # corner) against the oracle's FP64 literal walks from the start, element-wise.  A literal
+    # column is (p'' - p') / eps with float32 end points: their rounding, about 6e-8 on this unit
+    # sphere, over eps = 1e-4 is about 1e-3 of a unit column, and grad_p solves a 2x2 system of two
+    # such columns.  Bar: grad_v within 1e-3; grad_p within 1e-3 at the 99th percentile, 2e-3 at
+    # most.
     split = quiet & ((gpu["status"] & 256) != 0)
-    if split.sum() > 10:
-        # literal FP32 walks on both sides of a swept vertex: agree in direction
-        cs = np.einsum("ij,ij->i", gpu["grad_v"][split], ref["grad_v"][split]) / (
-            np.linalg.norm(gpu["grad_v"][split], axis=1) * np.linalg.norm(ref["grad_v"][split], axis=1))
-        assert np.median(cs) > 0.99
+    assert split.sum() > 100, split.sum()
+    s_v, s_p = rel(gpu["grad_v"], ref["grad_v"])[split], rel(gpu["grad_p"], ref["grad_p"])[split]
+    print("split queries", split.sum(), "grad_v max", s_v.max(), "grad_p p99", np.quantile(s_p, 0.99),
+          "max", s_p.max())
+    assert s_v.max() < 1e-3
+    assert np.quantile(s_p, 0.99) < 1e-3 and s_p.max() < 2e-3
 
 
 def test_flat_mesh_gradients_closed_form():
