@@ -81,7 +81,9 @@ typedef struct sg_opts {
                                persistent kernel's arithmetic (FP64 classification kept): such a
                                batch fills the persistent grid once, so the queue gains nothing */
     int32_t sort;           /* order in which the persistent kernels take the queries:
-                               0: input order; 1: by (mesh, start face); 2: by walk length,
+                               0: input order; 1: by (mesh, start face), the faces taken along
+                               the mesh's Z-order curve of face centroids so that neighbouring
+                               queries start in one patch of the surface; 2: by walk length,
                                longest first (L or |v| over l_ref, an eighth of an octave per
                                bucket: lanes of a warp then finish together and idle less);
                                <0: auto -- for batches of >= 65536 queries, 1 on meshes whose
@@ -218,7 +220,9 @@ sg_status sg_mesh_get_info(const sg_mesh *m, sg_mesh_info *info);
  * before the call by the caller.  The arithmetic is that of sg_mesh_create (FP64, no
  * multiply-add contraction), so an updated mesh walks like one created from the new positions;
  * the FP64 sums (theta, l_ref) are accumulated in a different order, which can move their FP32
- * values by one unit in the last place.
+ * values by one unit in the last place.  The faces' places on the Z-order curve that keys the
+ * start-face query order keep the creation positions (an order, not a result: walks give the same
+ * outputs in any order).
  * A face that the new positions make zero-area or non-finite marks its mesh (its member of a
  * batch) unusable: every query on it returns SG_ST_INVALID until a later update makes all of
  * its faces valid again; sg_mesh_get_info reports the count.
