@@ -69,6 +69,15 @@
 #ifndef SG_LITERAL_MINB
 #define SG_LITERAL_MINB 7
 #endif
+// walk steps between the re-walk's and the literal walks' refill checks (re-walk: 1 step 0.600 ms,
+// 2 steps 0.619, 3 steps 0.651; refill at 28 idle lanes with one step: 20 0.665, 24 0.619,
+// 30 0.601, 32 0.610 ms; the forward walk keeps 2: 0.389 ms against 0.522 with one)
+#ifndef SG_REWALK_STEPS
+#define SG_REWALK_STEPS 1
+#endif
+#ifndef SG_LITERAL_STEPS
+#define SG_LITERAL_STEPS 2
+#endif
 // minimum resident blocks per SM of the re-walk (69 registers at 7 without spills, with the
 // straddle test's rare constants, the query id and the face offset in shared memory; 6 blocks
 // time the same)
@@ -499,7 +508,7 @@ template <bool GFD, bool GRADV>
 __global__ void __launch_bounds__(128, SG_REWALK_MINB) k_bwd_rewalk(BwdArgs A) {
     RewalkJob<GFD, GRADV> job;
     job.A = &A;
-    run_persistent<RewalkJob<GFD, GRADV>, SG_REWALK_REFILL>(A.ntask + 1, A.nq, job);
+    run_persistent<RewalkJob<GFD, GRADV>, SG_REWALK_REFILL, SG_REWALK_STEPS>(A.ntask + 1, A.nq, job);
 }
 
 // ------------------------------------------------------------------ chord / literal walks
@@ -679,7 +688,7 @@ template <bool HOLE>
 __global__ void __launch_bounds__(128, SG_LITERAL_MINB) k_bwd_literal(BwdArgs A) {
     LiteralJob<HOLE> job;
     job.A = &A;
-    run_persistent<LiteralJob<HOLE>, SG_LITERAL_REFILL>(A.ntask + 2, (int64_t)*A.ntask, job);
+    run_persistent<LiteralJob<HOLE>, SG_LITERAL_REFILL, SG_LITERAL_STEPS>(A.ntask + 2, (int64_t)*A.ntask, job);
 }
 
 // The literal walks of the swept columns of a query whose forward walk was the mixed walk (a walk

@@ -1110,13 +1110,14 @@ __device__ __forceinline__ int64_t fetch_ticket(int32_t *counter) {
 // Once the counter passes n, lanes finish as soon as they are done and the warp leaves when
 // all of its lanes are idle.  Every lane of the warp stays in the loop until then (the
 // ballots use the full mask).  Job: bool init(t) (true: a walk to step), bool step()
-// (true: done), void finish().
+// (true: done), void finish().  STEPS walk steps run between refill checks (each kernel sets
+// its own count).
 #define SG_REFILL_LANES 8
 #ifndef SG_STEPS_PER_CHECK
 #define SG_STEPS_PER_CHECK 2
 #endif
 
-template <class Job, int REFILL = SG_REFILL_LANES>
+template <class Job, int REFILL = SG_REFILL_LANES, int STEPS = SG_STEPS_PER_CHECK>
 __device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job &job) {
     if (n <= 0) return;  // an empty list (a count read from device memory): no ticket to take
     bool live = false, pending = false, exhausted = false;
@@ -1143,7 +1144,7 @@ __device__ __forceinline__ void run_persistent(int32_t *counter, int64_t n, Job 
         }
         // several steps per refill check divide the loop overhead
 #pragma unroll
-        for (int k = 0; k < SG_STEPS_PER_CHECK; ++k) {
+        for (int k = 0; k < STEPS; ++k) {
             if (live && job.step()) {
                 live = false;
                 pending = true;
