@@ -197,6 +197,10 @@ struct MixJob {
 #ifndef SG_MIX_MINB
 #define SG_MIX_MINB 4
 #endif
+// walk steps between the mixed walk's refill checks (64-mesh batch: 2 steps 17.2 ms, 1 step 17.8 ms)
+#ifndef SG_MIX_STEPS
+#define SG_MIX_STEPS 2
+#endif
 template <int NW, bool ESC>
 __global__ void __launch_bounds__(256, SG_MIX_MINB) k_walk_mixed(FwdArgs a) {
     MixJob<NW, ESC> job;
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(256, SG_MIX_MINB) k_walk_mixed(FwdArgs a) {
         job.n1 = a.route_n ? __ldg(a.route_n) : 0;
         n = job.n1 + __ldg(a.esc_count);
     }
-    run_persistent<MixJob<NW, ESC>, SG_WALK_REFILL>(a.counter, n, job);
+    run_persistent<MixJob<NW, ESC>, SG_WALK_REFILL, SG_MIX_STEPS>(a.counter, n, job);
 }
 
 // hole avoidance (boundary_mode 1): the boundary handling needs more registers than the
@@ -215,11 +219,17 @@ __global__ void __launch_bounds__(256, SG_MIX_MINB) k_walk_mixed(FwdArgs a) {
 #ifndef SG_HOLE_MINB
 #define SG_HOLE_MINB 4
 #endif
+// walk steps between the hole-avoidance walk's refill checks: one (the boundary handling makes
+// the loop body large; the sphere with 8% of its faces removed, 1M queries: 2.41 ms, against
+// 4.63 ms with two steps per check)
+#ifndef SG_HOLE_STEPS
+#define SG_HOLE_STEPS 1
+#endif
 template <int NW>
 __global__ void __launch_bounds__(256, SG_HOLE_MINB) k_walk_hole(FwdArgs a) {
     FwdJob<NW, true, true> job;
     job.a = &a;
-    run_persistent<FwdJob<NW, true, true>, SG_WALK_REFILL>(a.counter, a.nq, job);
+    run_persistent<FwdJob<NW, true, true>, SG_WALK_REFILL, SG_HOLE_STEPS>(a.counter, a.nq, job);
 }
 
 // ------------------------------------------------------------------ geodesic tracing
