@@ -25,6 +25,14 @@
 // lanes of a warp that must be idle before the forward walk refills them together (walk on 1M
 // queries of the 81,920-face sphere, length order, 256-bit record loads: 8 lanes 0.412 ms, 12
 // 0.403, 16 0.424, 20 0.432)
+// walk steps between refill checks of the forward walk (one: 0.522 ms against 0.389 ms with two)
+// and of the trace
+#ifndef SG_WALK_STEPS
+#define SG_WALK_STEPS 2
+#endif
+#ifndef SG_TRACE_STEPS
+#define SG_TRACE_STEPS 2
+#endif
 #ifndef SG_WALK_REFILL
 #define SG_WALK_REFILL 12
 #endif
@@ -167,7 +175,7 @@ template <int NW, bool ESC, bool AUTO = false>
 __global__ void __launch_bounds__(256, 4) k_walk_persistent(FwdArgs a) {
     FwdJob<NW, ESC, false, AUTO> job;
     job.a = &a;
-    run_persistent<FwdJob<NW, ESC, false, AUTO>, SG_WALK_REFILL>(a.counter, a.nq, job);
+    run_persistent<FwdJob<NW, ESC, false, AUTO>, SG_WALK_REFILL, SG_WALK_STEPS>(a.counter, a.nq, job);
 }
 
 // The mixed walk (precision 40; walk.cuh, MIX): the FP32 walker with the direction in
@@ -385,7 +393,7 @@ __global__ void __launch_bounds__(256, 4) k_trace_persistent(FwdArgs a, TraceOut
     job.a = &a;
     job.t = &t;
     job.sg = &stage;
-    run_persistent<TraceJob<ESC>, SG_WALK_REFILL>(a.counter, a.nq, job);
+    run_persistent<TraceJob<ESC>, SG_WALK_REFILL, SG_TRACE_STEPS>(a.counter, a.nq, job);
 }
 
 // ------------------------------------------------------------------ start-face counting sort
