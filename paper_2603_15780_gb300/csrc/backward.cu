@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(256) k_ep_backward(BwdArgs A) {
 #define SG_STR_VQ 6
 __shared__ float s_straddle[7][128];
 // the re-walk's query and its mesh's face offset, read only when a swept corner is recorded and
-// at the end of the walk (shared memory, one slot per thread, instead of two registers)
+// at the end of the walk (shared memory, one slot per thread, instead of two registers).  These
+// arrays are sized for the re-walk's 128-thread blocks: its __launch_bounds__(128, ...) makes a
+// launch with larger blocks fail instead of indexing past them.
 __shared__ int32_t s_rewalk_q[128], s_rewalk_foff[128];
 struct StraddleHook {
     const BwdArgs *A;
