@@ -14,7 +14,6 @@ from __future__ import annotations
 
 import numpy as np
 
-import meshgen
 import oracle
 
 FLAGS = oracle.NEAR_VERTEX | oracle.NEAR_EDGE

@@ -12,7 +12,6 @@ import numpy as np
 import pytest
 
 import meshgen
-import oracle
 from tests import parity
 
 pytestmark = pytest.mark.gpu

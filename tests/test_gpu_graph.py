@@ -60,7 +60,6 @@ def test_tuned_and_swept_launches_match_the_oracle(pick):
     """The launch the autotuner picks on the multi-mesh batch, and the two ends of its
     queries-per-thread axis, at the full parity bar against the oracle mesh by mesh (face
     sequences bit-exact on unflagged queries, end points within 1e-5 of each mesh's diagonal)."""
-    import oracle
     sg, mesh, q, face, bary, v, mid = _batch()
     from paper_2603_15780_gb300 import autotune
     if pick == "tuned":
