@@ -26,3 +26,14 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "geodesics/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["crossings_per_s"] > 0
+
+
+def test_traffic_record_matches_the_kernel_sources():
+    """profiles/ncu_traffic.json holds the DRAM bytes and L2 requests of the walk and re-walk
+    kernels as captured by ncu, keyed by the hash of their sources: the benchmark reports them
+    only while the sources are those that were captured."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("k_walk_persistent", "k_bwd_rewalk"):
+        assert bench.ncu_traffic(k) is not None, k
+        assert bench.ncu_traffic(k, "lts_requests_per_launch") is not None, k
