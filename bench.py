@@ -664,8 +664,23 @@ def main():
     args.sort = -1 if args.sort is None else args.sort
     args.block = 0 if args.block is None else args.block
     qpt = tuned["pick"]["queries_per_thread"] if tuned else 0
+    # The query order the forward's options give, as the library decides it: by start face (5
+    # sort/scan kernels) when the mesh's records (128 B per face) exceed half of L2, else by walk
+    # length (2 kernels), input order for the plain kernel and small batches.  The forward writes
+    # the length order into `qorder` (its own queue's, or two more launches after another order)
+    # and the GFD backward's re-walk takes the queries in that order (sg_opts.order) instead of
+    # sorting them again.
+    if args.kernel == 1:
+        sort_mode = 0
+    elif args.sort >= 0:
+        sort_mode = args.sort
+    else:
+        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+        sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
+    qorder = torch.empty(nq, dtype=torch.int32, device=dev)
     opts = sg.default_opts(kernel=args.kernel, sort=args.sort, fp64_escalate=args.fp64,
                            block=args.block if args.block > 0 else None, queries_per_thread=qpt)
+    opts.order = qorder.data_ptr()   # the workspace is sized with the order buffer in use
     ws = torch.empty(sg.workspace_size(mesh, nq, opts), dtype=torch.uint8, device=dev)
     bopts = sg.default_opts(sort=bsort)
     bws = torch.empty(sg.backward_workspace_size(mesh, "gfd", nq, True), dtype=torch.uint8, device=dev)
@@ -686,20 +701,6 @@ def main():
            "status": torch.empty(nq, dtype=torch.int32, device=dev),
            "ncross": torch.empty(nq, dtype=torch.int32, device=dev)}
     gV = torch.zeros(mesh.n_vertices, 3, device=dev)
-    # The query order the forward's options give, as the library decides it: by start face (5
-    # sort/scan kernels) when the mesh's records (128 B per face) exceed half of L2, else by walk
-    # length (2 kernels), input order for the plain kernel and small batches.  The forward writes
-    # the length order into `qorder` (its own queue's, or two more launches after another order)
-    # and the GFD backward's re-walk takes the queries in that order (sg_opts.order) instead of
-    # sorting them again.
-    if args.kernel == 1:
-        sort_mode = 0
-    elif args.sort >= 0:
-        sort_mode = args.sort
-    else:
-        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-        sort_mode = 0 if nq < 65536 else (1 if 128 * mesh.n_faces > l2 // 2 else 2)
-    qorder = torch.empty(nq, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 

@@ -232,7 +232,9 @@ sg_status sg_mesh_update_vertices(sg_mesh *m, const float *V, void *stream);
 
 /*
  * sg_exp_map_workspace_size -- bytes of device scratch sg_exp_map needs for nq queries
- * with options `o` (the start-face sort and the work-queue counter).
+ * with options `o` (the query order, the work-queue counter, the automatic precision's
+ * escalation list, and, when o->order is set and the walk takes another order than the length
+ * order, the length order's keys: 1 byte per query and 2 KiB).  Set o->order before asking.
  */
 sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts *o, size_t *bytes);
 

@@ -597,8 +597,9 @@ struct WsLayout {
 #define SG_CTR_ESC 2
 
 // sort: 0 none, 1 by (mesh, start face), 2 by walk length; esc: room for the escalation list of
-// the automatic precision
-WsLayout ws_layout(int64_t nF, int64_t nq, int sort, bool esc = false) {
+// the automatic precision; order: room to build the length order for a caller's order buffer
+// (sg_opts.order) when the walk takes another order
+WsLayout ws_layout(int64_t nF, int64_t nq, int sort, bool esc = false, bool order = false) {
     WsLayout L{};
     size_t o = 0;
     L.counter = o; o = align_up(o + 64, 256);
@@ -614,7 +615,7 @@ WsLayout ws_layout(int64_t nF, int64_t nq, int sort, bool esc = false) {
         L.keys = o; o = align_up(o + (size_t)std::max<int64_t>(nq, 1), 256);
         L.perm = o; o = align_up(o + sizeof(int32_t) * std::max<int64_t>(nq, 1), 256);
     }
-    if (sort != 2) {  // the length order written into a caller's order buffer (sg_opts.order)
+    if (order && sort != 2) {  // the length order written into a caller's order buffer
         L.lcounts = o; o = align_up(o + sizeof(int32_t) * 2 * SG_LBUCKETS, 256);
         L.lkeys = o; o = align_up(o + (size_t)std::max<int64_t>(nq, 1), 256);
     }
@@ -922,7 +923,7 @@ sg_status sg_exp_map_workspace_size(const sg_mesh *m, int64_t nq, const sg_opts 
     sg_opts r = resolve(o, nq, m->nF);
     if (r.sort < 0 || r.sort > 2) return SG_ERR_INVALID_ARG;
     *bytes = ws_layout(m->nF, nq, r.kernel == SG_KERNEL_PERSISTENT ? r.sort : 0,
-                       r.precision == 0 && r.boundary_mode == 0).total;
+                       r.precision == 0 && r.boundary_mode == 0, r.order != nullptr).total;
     return SG_OK;
 }
 
@@ -948,7 +949,7 @@ FwdArgs fwd_args(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int
 sg_status prepare_queue(const sg_mesh *m, int64_t nq, const int32_t *mesh_id, const int32_t *face, const sg_opts &r,
                         int sort, cudaStream_t s, FwdArgs &a, void **own_ws, bool esc = false) {
     *own_ws = nullptr;
-    WsLayout L = ws_layout(m->nF, nq, sort, esc);
+    WsLayout L = ws_layout(m->nF, nq, sort, esc, r.order != nullptr);
     void *ws = nullptr;
     if (r.workspace) {
         if (r.workspace_bytes < L.total) return SG_ERR_OOM;
